@@ -1,0 +1,159 @@
+/*
+ * lbgb.h -- C ABI of the GB300 (sm_103a) colloidal two-component Shan-Chen
+ * lattice-Boltzmann library (method of Bonaccorso et al., "LBsoft: a parallel
+ * open-source software for simulation of colloidal systems",
+ * arXiv:2004.04080).
+ *
+ * One library context owns one D3Q19 lattice of nx*ny*nz sites on one GPU,
+ * with two fluid components and up to max_colloids rigid spheres.  Each call
+ * of lb_step advances the whole coupled system by the paper's time step
+ * (Sec. 3.1, particle sequence): moments (Eqs. 6, 7, 14), fluid-node
+ * destruction and creation under moving particles (Eqs. 24, 25), particle
+ * pair forces (Eqs. 26, 27), wetting virtual densities and Shan-Chen forces
+ * (Eqs. 11, 20, 21), collision with the exact-difference source (Eqs. 13-16),
+ * halfway bounce-back on particles and walls with the link forces
+ * (Eqs. 8, 9, 17-19, 22, 23), Svanberg rotational leap-frog (Eqs. 28-35) and
+ * streaming (Eq. 3).
+ *
+ * Conventions shared by every entry point:
+ *  - Site index s = x + nx*(y + ny*z); fields are flat arrays of length
+ *    N = nx*ny*nz; vector fields are structure-of-arrays [3][N].
+ *  - Particle arrays are [n][3] (quaternions [n][4] as q0,q1,q2,q3, scalar
+ *    first), double precision, in lattice units.
+ *  - Host pointers are owned by the caller; the library copies from or into
+ *    them before the call returns (synchronously on the context stream).
+ *  - Device memory: the library allocates nothing.  The caller allocates one
+ *    device workspace of lb_workspace_bytes() bytes (256-byte aligned) and
+ *    keeps it alive until lb_destroy; all kernels run on the CUDA stream
+ *    given to lb_create (NULL = legacy default stream).
+ *  - Errors: every call returns LB_OK (0) or a negative LB_ERR_* code; no
+ *    exception crosses the ABI.  lb_last_error() gives a text for the last
+ *    failure of a context.  Device-detected conditions (non-finite or
+ *    negative density, overlapping particles) are read back once at the end
+ *    of lb_step.
+ */
+#ifndef LBGB_H
+#define LBGB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx; /* opaque; created by lb_create */
+
+enum {
+    LB_OK = 0,
+    LB_ERR_ARG = -1,       /* invalid argument                               */
+    LB_ERR_STATE = -2,     /* call out of order or capacity exceeded         */
+    LB_ERR_CUDA = -3,      /* a CUDA runtime call failed                      */
+    LB_ERR_NOMEM = -4,     /* workspace too small                             */
+    LB_ERR_NONFINITE = -5, /* a density became non-finite or negative         */
+    LB_ERR_OVERLAP = -6,   /* two particles claimed the same lattice node     */
+    LB_ERR_TIMEOUT = -7    /* reserved: a bounded device wait gave up          */
+};
+
+/* Storage precision of the populations.  LB_FP64 and LB_FP32 compute in the
+ * storage type; LB_FP16 stores each population as the half-precision
+ * deviation f_i - w_i rho0^k and computes in FP32.  Particle state, particle
+ * force/torque sums and the global reductions are FP64 in every mode. */
+enum { LB_FP64 = 0, LB_FP32 = 1, LB_FP16 = 2 };
+
+/* Physical parameters (paper App. A "LB" and "MD" rooms; lattice units). */
+typedef struct {
+    double tau[2];          /* BGK relaxation time per component (Eq. 4), > 1/2   */
+    double G;               /* Shan-Chen coupling G_C (Eq. 11); repulsive for G>0 */
+    double zeta[2];         /* wetting constant per component (Eq. 20)            */
+    double rho0[2];         /* reference density: FP16 deviation shift, and the  */
+                            /* refill density of a node with no fluid neighbour  */
+    int bc[3];              /* 1 periodic, 0 wall; walls only along z (bc[2])    */
+    double wall_u_lo[3];    /* velocity of the wall at z = -1/2 (Eq. 9)          */
+    double wall_u_hi[3];    /* velocity of the wall at z = nz - 1/2              */
+    double body_force[3];   /* force per unit mass on the fluid ("force ext")    */
+    double hertz_K;         /* Hertz constant K (Eq. 26); 0 disables              */
+    double hertz_sigma;     /* contact distance: force acts for r < sigma         */
+    double hertz_rcap;      /* r is floored at rcap in the force magnitude       */
+    int lub_on;             /* lubrication (Eq. 27) on/off                        */
+    double lub_hn, lub_hmin, lub_scale; /* cut-off gap, gap floor, prefactor    */
+    double side_wall_k;     /* soft harmonic particle-wall spring; 0 disables    */
+    double side_wall_d;     /* it pushes when a centre is closer than d to a wall */
+    int rotate;             /* integrate angular velocity and orientation        */
+} lb_params;
+
+/* Device workspace size for a lattice; *bytes receives the size.
+ * Returns LB_ERR_ARG for a non-positive size or unknown precision. */
+int lb_workspace_bytes(int nx, int ny, int nz, int prec, int max_colloids, size_t *bytes);
+
+/* Create a context on the calling thread's current CUDA device.
+ * d_workspace: device pointer, 256-byte aligned, >= lb_workspace_bytes bytes,
+ * owned by the caller.  cuda_stream: a cudaStream_t or NULL.
+ * Lattice sides must be >= 4; nx must be a multiple of 4. */
+int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void *d_workspace,
+              size_t bytes, void *cuda_stream, lb_ctx **out);
+
+/* Set the parameters (copied).  Must precede lb_init_fields. */
+int lb_set_params(lb_ctx *ctx, const lb_params *p);
+
+/* Initialise populations to f^eq(rho^k, u) (Eq. 5) on every site.
+ * rhoA, rhoB: [N] host arrays; u: [3][N] host array or NULL for rest.
+ * Removes any particles (their node map is cleared). */
+int lb_init_fields(lb_ctx *ctx, const double *rhoA, const double *rhoB, const double *u);
+
+/* Append n particles (total <= max_colloids) and map their solid nodes
+ * (Sec. 2.4: node solid iff |x - r_p|^2 < R_p^2, minimum image); fluid on the
+ * newly solid nodes is removed without momentum bookkeeping.
+ * pos, radius, mass required; vel = v(-1/2), omega, quat may be NULL (zero,
+ * zero, identity).  A mass of +inf makes a particle immobile.
+ * Positions are wrapped into the box along periodic axes; along a wall axis
+ * they must lie in [0, n-1].  2R+5 must be smaller than each periodic side. */
+int lb_add_colloids(lb_ctx *ctx, int n, const double *pos, const double *vel,
+                    const double *omega, const double *quat, const double *radius,
+                    const double *mass);
+
+/* Advance nsteps time steps.  Returns LB_ERR_NONFINITE / LB_ERR_OVERLAP if the
+ * device flagged the condition during these steps (state then undefined). */
+int lb_step(lb_ctx *ctx, int nsteps);
+
+/* Densities rho^k and the half-force-corrected mixture velocity
+ * u = sum_k (j^k + F^k/2) / rho (Sec. 2.3) of the current state, with the
+ * forces evaluated on the current node map.  Solid nodes read zero.
+ * Any output pointer may be NULL. */
+int lb_get_fields(lb_ctx *ctx, double *rhoA, double *rhoB, double *u);
+
+/* Particle state: position r(t), velocity v(t-1/2), angular velocity
+ * omega(t-1/2), orientation q(t), and the total force / torque of Eq. 35 used
+ * by the last step.  Any pointer may be NULL.  Returns the particle count. */
+int lb_get_colloids(lb_ctx *ctx, double *pos, double *vel, double *omega, double *quat,
+                    double *force, double *torque);
+
+/* One per-particle force term of the last step, [n][3]:
+ * 0 F_liq(t+1/2) (Eq. 22), 1 T_liq (Eq. 23), 2 F_d, 3 T_d (Eq. 24),
+ * 4 F_c, 5 T_c (Eq. 25), 6 F_s, 7 T_s (Eq. 21 summed over the frontier),
+ * 8 pair + side-wall force (Eqs. 26-27), 9 total force, 10 total torque. */
+int lb_get_colloid_terms(lb_ctx *ctx, int which, double *out);
+
+/* Global FP64 sums over fluid nodes: out[0..1] mass of A and B,
+ * out[2..4] sum_k j^k, out[5..7] sum_k (j^k + F^k/2). */
+int lb_get_totals(lb_ctx *ctx, double *out);
+
+/* Raw populations of component k as FP64, [19][N] (for tests). */
+int lb_get_populations(lb_ctx *ctx, int k, double *out);
+
+/* Node map: -1 fluid, else the index of the owning particle, [N]. */
+int lb_get_owner(lb_ctx *ctx, int *out);
+
+/* Number of kernel launches issued by this context since creation. */
+long long lb_launch_count(const lb_ctx *ctx);
+
+/* Release the context (not the caller's workspace). */
+int lb_destroy(lb_ctx *ctx);
+
+/* Text of the last error of ctx ("" if none); valid until the next call. */
+const char *lb_last_error(const lb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBGB_H */

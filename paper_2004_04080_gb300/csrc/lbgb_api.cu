@@ -1,0 +1,418 @@
+// lbgb_api.cu -- host side of the C ABI declared in include/lbgb.h:
+// argument validation, workspace carving, the per-step launch sequence and
+// the host<->device copies of the read-out calls.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "lbgb_internal.cuh"
+
+using namespace lbgb;
+
+struct lb_ctx {
+    Lattice L;
+    int prec;
+    int maxc;
+    cudaStream_t stream;
+    char* ws;
+    size_t ws_bytes;
+    int have_params, have_fields, stepped;
+    long long launches;
+    double* totals_dev;
+    char err[512];
+};
+
+namespace {
+
+const size_t ALIGN = 256;
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+size_t storage_bytes(int prec) { return prec == LB_FP64 ? 8 : (prec == LB_FP32 ? 4 : 2); }
+size_t compute_bytes(int prec) { return prec == LB_FP64 ? 8 : 4; }
+
+const int DOUBLES_PER_PARTICLE = 57;  // pos..Ttot, see carve()
+const int RED_BLOCKS = 1024;
+
+struct Layout {
+    size_t f0, f1, psi, psi_wall, mask, owner, evt, flags, col, prev, red, totals, total;
+    long long pstride;
+};
+
+Layout layout(int nx, int ny, int nz, int prec, int maxc) {
+    Layout l;
+    long long N = (long long)nx * ny * nz;
+    l.pstride = (N + 63) / 64 * 64;
+    size_t off = 0;
+    size_t fb = (size_t)2 * Q * l.pstride * storage_bytes(prec);
+    // the second population buffer doubles as the FP64 staging area of the
+    // read-out calls (5 doubles per site), so it is at least that large
+    size_t fb1 = fb > (size_t)5 * N * 8 ? fb : (size_t)5 * N * 8;
+    l.f0 = off; off = align_up(off + fb);
+    l.f1 = off; off = align_up(off + fb1);
+    l.psi = off; off = align_up(off + (size_t)2 * N * compute_bytes(prec));
+    l.psi_wall = off; off = align_up(off + (size_t)4 * nx * ny * compute_bytes(prec));
+    l.mask = off; off = align_up(off + (size_t)N);
+    l.owner = off; off = align_up(off + (size_t)N * 4);
+    l.evt = off; off = align_up(off + (size_t)N * 4);
+    l.flags = off; off = align_up(off + 64);
+    int mc = maxc > 0 ? maxc : 1;
+    l.col = off; off = align_up(off + (size_t)mc * DOUBLES_PER_PARTICLE * 8);
+    l.prev = off; off = align_up(off + (size_t)mc * 4);
+    l.red = off; off = align_up(off + (size_t)RED_BLOCKS * 16 * 8);
+    l.totals = off; off = align_up(off + 8 * 8);
+    l.total = off;
+    return l;
+}
+
+int set_err(lb_ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_check(lb_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return LB_OK;
+    return set_err(c, LB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        int rc_ = cuda_check(ctx, (call), what);         \
+        if (rc_) return rc_;                             \
+    } while (0)
+
+int launched(lb_ctx* ctx, int n, const char* what) {
+    ctx->launches += n;
+    return cuda_check(ctx, cudaGetLastError(), what);
+}
+
+double* stage_ptr(lb_ctx* ctx) { return (double*)ctx->L.f_nxt; }
+
+}  // namespace
+
+extern "C" {
+
+int lb_workspace_bytes(int nx, int ny, int nz, int prec, int max_colloids, size_t* bytes) {
+    if (!bytes || nx < 4 || ny < 4 || nz < 4 || max_colloids < 0) return LB_ERR_ARG;
+    if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_FP16) return LB_ERR_ARG;
+    *bytes = layout(nx, ny, nz, prec, max_colloids).total;
+    return LB_OK;
+}
+
+int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_workspace, size_t bytes,
+              void* cuda_stream, lb_ctx** out) {
+    if (!out) return LB_ERR_ARG;
+    *out = NULL;
+    if (nx < 4 || ny < 4 || nz < 4 || (nx % 4) != 0 || max_colloids < 0) return LB_ERR_ARG;
+    if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_FP16) return LB_ERR_ARG;
+    if (!d_workspace || ((uintptr_t)d_workspace % ALIGN) != 0) return LB_ERR_ARG;
+    Layout l = layout(nx, ny, nz, prec, max_colloids);
+    if (bytes < l.total) return LB_ERR_NOMEM;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, d_workspace) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return LB_ERR_ARG;
+    }
+    lb_ctx* ctx = new (std::nothrow) lb_ctx;
+    if (!ctx) return LB_ERR_NOMEM;
+    memset(ctx, 0, sizeof(*ctx));
+    ctx->prec = prec;
+    ctx->maxc = max_colloids;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->ws = (char*)d_workspace;
+    ctx->ws_bytes = bytes;
+    Lattice& L = ctx->L;
+    L.nx = nx; L.ny = ny; L.nz = nz;
+    L.N = (long long)nx * ny * nz;
+    L.pstride = l.pstride;
+    L.per[0] = L.per[1] = L.per[2] = 1;
+    L.f_cur = ctx->ws + l.f0;
+    L.f_nxt = ctx->ws + l.f1;
+    L.psi = ctx->ws + l.psi;
+    L.psi_wall = ctx->ws + l.psi_wall;
+    L.mask = (uint8_t*)(ctx->ws + l.mask);
+    L.owner = (int*)(ctx->ws + l.owner);
+    L.evt = (int*)(ctx->ws + l.evt);
+    L.flags = (int*)(ctx->ws + l.flags);
+    int mc = max_colloids > 0 ? max_colloids : 1;
+    double* c = (double*)(ctx->ws + l.col);
+    double** slots3[] = {&L.pos, &L.vel, &L.omg};
+    for (int a = 0; a < 3; a++) { *slots3[a] = c; c += 3 * mc; }
+    L.quat = c; c += 4 * mc;
+    L.rad = c; c += mc;
+    L.mass = c; c += mc;
+    double** more[] = {&L.Fliq, &L.Tliq, &L.Fliq_prev, &L.Tliq_prev, &L.Fd, &L.Td, &L.Fc,
+                       &L.Tc, &L.Fs, &L.Ts, &L.Fpair, &L.Ftot, &L.Ttot};
+    for (int a = 0; a < 13; a++) { *more[a] = c; c += 3 * mc; }
+    L.prev_valid = (int*)(ctx->ws + l.prev);
+    L.red = (double*)(ctx->ws + l.red);
+    L.red_blocks = RED_BLOCKS;
+    ctx->totals_dev = (double*)(ctx->ws + l.totals);
+    L.nc = 0;
+    // empty node map, no particles, no error flags
+    cudaError_t e = cudaMemsetAsync(ctx->ws + l.mask, 0, (size_t)L.N, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.owner, 0xff, (size_t)L.N * 4, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.evt, 0, (size_t)L.N * 4, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.flags, 0, 64, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.col, 0, (size_t)mc * DOUBLES_PER_PARTICLE * 8, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.prev, 0, (size_t)mc * 4, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return LB_ERR_CUDA;
+    }
+    *out = ctx;
+    return LB_OK;
+}
+
+int lb_set_params(lb_ctx* ctx, const lb_params* p) {
+    if (!ctx || !p) return LB_ERR_ARG;
+    if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5) || !isfinite(p->tau[0]) || !isfinite(p->tau[1]))
+        return set_err(ctx, LB_ERR_ARG, "tau must be finite and > 1/2");
+    if (p->bc[0] != 1 || p->bc[1] != 1 || (p->bc[2] != 0 && p->bc[2] != 1))
+        return set_err(ctx, LB_ERR_ARG, "walls are supported only along z (bc = {1,1,0|1})");
+    const double* vals[] = {&p->G, &p->zeta[0], &p->zeta[1], &p->rho0[0], &p->rho0[1], &p->hertz_K,
+                            &p->hertz_sigma, &p->hertz_rcap, &p->side_wall_k, &p->side_wall_d};
+    for (unsigned a = 0; a < sizeof(vals) / sizeof(vals[0]); a++)
+        if (!isfinite(*vals[a])) return set_err(ctx, LB_ERR_ARG, "non-finite parameter");
+    for (int d = 0; d < 3; d++)
+        if (!isfinite(p->wall_u_lo[d]) || !isfinite(p->wall_u_hi[d]) || !isfinite(p->body_force[d]))
+            return set_err(ctx, LB_ERR_ARG, "non-finite wall velocity or body force");
+    if (p->lub_on && !(p->lub_hmin > 0.0 && p->lub_hn > p->lub_hmin))
+        return set_err(ctx, LB_ERR_ARG, "lubrication needs 0 < lub_hmin < lub_hn");
+    if (ctx->stepped && p->bc[2] != ctx->L.P.bc[2])
+        return set_err(ctx, LB_ERR_STATE, "boundary conditions cannot change after stepping");
+    ctx->L.P = *p;
+    ctx->L.per[0] = 1;
+    ctx->L.per[1] = 1;
+    ctx->L.per[2] = p->bc[2];
+    ctx->have_params = 1;
+    return LB_OK;
+}
+
+int lb_init_fields(lb_ctx* ctx, const double* rhoA, const double* rhoB, const double* u) {
+    if (!ctx || !rhoA || !rhoB) return LB_ERR_ARG;
+    if (!ctx->have_params) return set_err(ctx, LB_ERR_STATE, "lb_set_params must come first");
+    Lattice& L = ctx->L;
+    size_t nb = (size_t)L.N * 8;
+    double* st = stage_ptr(ctx);
+    CK(cudaMemcpyAsync(st, rhoA, nb, cudaMemcpyHostToDevice, ctx->stream), "copy rhoA");
+    CK(cudaMemcpyAsync(st + L.N, rhoB, nb, cudaMemcpyHostToDevice, ctx->stream), "copy rhoB");
+    if (u) CK(cudaMemcpyAsync(st + 2 * L.N, u, 3 * nb, cudaMemcpyHostToDevice, ctx->stream), "copy u");
+    else CK(cudaMemsetAsync(st + 2 * L.N, 0, 3 * nb, ctx->stream), "zero u");
+    L.nc = 0;
+    int n = launch_clear_map(L, ctx->stream);
+    n += launch_init_fields(L, ctx->prec, st, ctx->stream);
+    int rc = launched(ctx, n, "init kernels");
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(ctx->stream), "init sync");
+    ctx->have_fields = 1;
+    ctx->stepped = 0;
+    return LB_OK;
+}
+
+int lb_add_colloids(lb_ctx* ctx, int n, const double* pos, const double* vel, const double* omega,
+                    const double* quat, const double* radius, const double* mass) {
+    if (!ctx || n < 0 || (n > 0 && (!pos || !radius || !mass))) return LB_ERR_ARG;
+    if (!ctx->have_fields) return set_err(ctx, LB_ERR_STATE, "lb_init_fields must come first");
+    if (ctx->stepped) return set_err(ctx, LB_ERR_STATE, "particles must be added before the first step");
+    Lattice& L = ctx->L;
+    if (L.nc + n > ctx->maxc) return set_err(ctx, LB_ERR_STATE, "more than max_colloids particles");
+    if (n == 0) return LB_OK;
+    int Ls[3] = {L.nx, L.ny, L.nz};
+    double* h = new (std::nothrow) double[(size_t)n * 17];
+    if (!h) return LB_ERR_NOMEM;
+    double *hp = h, *hv = h + 3 * n, *hw = h + 6 * n, *hq = h + 9 * n, *hr = h + 13 * n, *hm = h + 14 * n;
+    double rmax = L.rmax;
+    for (int p = 0; p < n; p++) {
+        double R = radius[p];
+        if (!(R > 0.0) || !isfinite(R) || !(mass[p] > 0.0) || isnan(mass[p])) {
+            delete[] h;
+            return set_err(ctx, LB_ERR_ARG, "particle %d: radius must be finite > 0, mass > 0", p);
+        }
+        for (int d = 0; d < 3; d++) {
+            double x = pos[3 * p + d];
+            if (!isfinite(x)) { delete[] h; return set_err(ctx, LB_ERR_ARG, "non-finite position"); }
+            if (L.per[d]) {
+                if (2.0 * R + 5.0 >= (double)Ls[d]) {
+                    delete[] h;
+                    return set_err(ctx, LB_ERR_ARG, "particle %d too large for the box", p);
+                }
+                x = x - (double)Ls[d] * floor(x / (double)Ls[d]);
+            } else if (x < 0.0 || x > (double)Ls[d] - 1.0) {
+                delete[] h;
+                return set_err(ctx, LB_ERR_ARG, "particle %d outside the walls", p);
+            }
+            hp[3 * p + d] = x;
+            hv[3 * p + d] = vel ? vel[3 * p + d] : 0.0;
+            hw[3 * p + d] = omega ? omega[3 * p + d] : 0.0;
+        }
+        for (int d = 0; d < 4; d++) hq[4 * p + d] = quat ? quat[4 * p + d] : (d == 0 ? 1.0 : 0.0);
+        hr[p] = R;
+        hm[p] = mass[p];
+        if (R > rmax) rmax = R;
+    }
+    int first = L.nc;
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMemcpyAsync(L.pos + 3 * first, hp, 24 * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(L.vel + 3 * first, hv, 24 * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(L.omg + 3 * first, hw, 24 * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(L.quat + 4 * first, hq, 32 * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(L.rad + first, hr, 8 * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(L.mass + first, hm, 8 * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemsetAsync(L.prev_valid + first, 0, 4 * (size_t)n, s);
+    if (!e) e = cudaMemsetAsync(L.flags, 0, 4, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    delete[] h;
+    if (e) return cuda_check(ctx, e, "copy particles");
+    L.nc = first + n;
+    L.rmax = rmax;
+    int rc = launched(ctx, launch_map_initial(L, first, n, s), "map kernel");
+    if (rc) return rc;
+    int flags = 0;
+    CK(cudaMemcpyAsync(&flags, L.flags, 4, cudaMemcpyDeviceToHost, s), "read flags");
+    CK(cudaStreamSynchronize(s), "map sync");
+    if (flags & FLAG_OVERLAP) return set_err(ctx, LB_ERR_OVERLAP, "particles overlap on the lattice");
+    return LB_OK;
+}
+
+int lb_step(lb_ctx* ctx, int nsteps) {
+    if (!ctx || nsteps < 0) return LB_ERR_ARG;
+    if (!ctx->have_fields) return set_err(ctx, LB_ERR_STATE, "lb_init_fields must come first");
+    Lattice& L = ctx->L;
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemsetAsync(L.flags, 0, 4, s), "clear flags");
+    for (int t = 0; t < nsteps; t++) {
+        int n = 0;
+        n += launch_remap(L, ctx->prec, s);           // destroy / create (Eqs. 24, 25)
+        n += launch_density(L, ctx->prec, s);          // rho^k (Eq. 6)
+        n += launch_wall_psi(L, ctx->prec, s);         // wall densities
+        n += launch_virtual(L, ctx->prec, 1, s);       // Eqs. 20, 21
+        n += launch_fluid_step(L, ctx->prec, s);       // Eqs. 11, 14, 16, 3, 9, 17
+        n += launch_links(L, ctx->prec, s);            // Eqs. 19, 22, 23
+        n += launch_pairs_integrate(L, s);             // Eqs. 26-27, 32-35
+        int rc = launched(ctx, n, "step kernels");
+        if (rc) return rc;
+        void* tmp = L.f_cur;
+        L.f_cur = L.f_nxt;
+        L.f_nxt = tmp;
+        ctx->stepped = 1;
+    }
+    int flags = 0;
+    CK(cudaMemcpyAsync(&flags, L.flags, 4, cudaMemcpyDeviceToHost, s), "read flags");
+    CK(cudaStreamSynchronize(s), "step sync");
+    if (flags & FLAG_OVERLAP) return set_err(ctx, LB_ERR_OVERLAP, "two particles claimed one node");
+    if (flags & FLAG_NONFINITE) return set_err(ctx, LB_ERR_NONFINITE, "non-finite or negative density");
+    return LB_OK;
+}
+
+// density, wetting and wall fields of the current state (no particle terms)
+static int current_forces(lb_ctx* ctx) {
+    Lattice& L = ctx->L;
+    int n = launch_density(L, ctx->prec, ctx->stream);
+    n += launch_wall_psi(L, ctx->prec, ctx->stream);
+    n += launch_virtual(L, ctx->prec, 0, ctx->stream);
+    return launched(ctx, n, "density kernels");
+}
+
+int lb_get_fields(lb_ctx* ctx, double* rhoA, double* rhoB, double* u) {
+    if (!ctx) return LB_ERR_ARG;
+    if (!ctx->have_fields) return set_err(ctx, LB_ERR_STATE, "no fields");
+    Lattice& L = ctx->L;
+    int rc = current_forces(ctx);
+    if (rc) return rc;
+    double* st = stage_ptr(ctx);
+    rc = launched(ctx, launch_fields_out(L, ctx->prec, st, ctx->stream), "fields kernel");
+    if (rc) return rc;
+    size_t nb = (size_t)L.N * 8;
+    if (rhoA) CK(cudaMemcpyAsync(rhoA, st, nb, cudaMemcpyDeviceToHost, ctx->stream), "copy rhoA");
+    if (rhoB) CK(cudaMemcpyAsync(rhoB, st + L.N, nb, cudaMemcpyDeviceToHost, ctx->stream), "copy rhoB");
+    if (u) CK(cudaMemcpyAsync(u, st + 2 * L.N, 3 * nb, cudaMemcpyDeviceToHost, ctx->stream), "copy u");
+    CK(cudaStreamSynchronize(ctx->stream), "fields sync");
+    return LB_OK;
+}
+
+int lb_get_totals(lb_ctx* ctx, double* out) {
+    if (!ctx || !out) return LB_ERR_ARG;
+    if (!ctx->have_fields) return set_err(ctx, LB_ERR_STATE, "no fields");
+    int rc = current_forces(ctx);
+    if (rc) return rc;
+    rc = launched(ctx, launch_totals(ctx->L, ctx->prec, ctx->totals_dev, ctx->stream), "totals kernels");
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(out, ctx->totals_dev, 64, cudaMemcpyDeviceToHost, ctx->stream), "copy totals");
+    CK(cudaStreamSynchronize(ctx->stream), "totals sync");
+    return LB_OK;
+}
+
+int lb_get_populations(lb_ctx* ctx, int k, double* out) {
+    if (!ctx || !out || k < 0 || k > 1) return LB_ERR_ARG;
+    if (!ctx->have_fields) return set_err(ctx, LB_ERR_STATE, "no fields");
+    Lattice& L = ctx->L;
+    // one population plane at a time through the staging area
+    double* st = stage_ptr(ctx);
+    for (int i = 0; i < Q; i++) {
+        int rc = launched(ctx, launch_populations_out(L, ctx->prec, k, i, st, ctx->stream), "pops kernel");
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(out + (size_t)i * L.N, st, (size_t)L.N * 8, cudaMemcpyDeviceToHost, ctx->stream),
+           "copy pops");
+        CK(cudaStreamSynchronize(ctx->stream), "pops sync");
+    }
+    return LB_OK;
+}
+
+int lb_get_owner(lb_ctx* ctx, int* out) {
+    if (!ctx || !out) return LB_ERR_ARG;
+    CK(cudaMemcpyAsync(out, ctx->L.owner, (size_t)ctx->L.N * 4, cudaMemcpyDeviceToHost, ctx->stream), "copy owner");
+    CK(cudaStreamSynchronize(ctx->stream), "owner sync");
+    return LB_OK;
+}
+
+int lb_get_colloids(lb_ctx* ctx, double* pos, double* vel, double* omega, double* quat, double* force,
+                    double* torque) {
+    if (!ctx) return LB_ERR_ARG;
+    Lattice& L = ctx->L;
+    size_t n = (size_t)L.nc;
+    cudaStream_t s = ctx->stream;
+    if (n) {
+        if (pos) CK(cudaMemcpyAsync(pos, L.pos, 24 * n, cudaMemcpyDeviceToHost, s), "copy pos");
+        if (vel) CK(cudaMemcpyAsync(vel, L.vel, 24 * n, cudaMemcpyDeviceToHost, s), "copy vel");
+        if (omega) CK(cudaMemcpyAsync(omega, L.omg, 24 * n, cudaMemcpyDeviceToHost, s), "copy omega");
+        if (quat) CK(cudaMemcpyAsync(quat, L.quat, 32 * n, cudaMemcpyDeviceToHost, s), "copy quat");
+        if (force) CK(cudaMemcpyAsync(force, L.Ftot, 24 * n, cudaMemcpyDeviceToHost, s), "copy force");
+        if (torque) CK(cudaMemcpyAsync(torque, L.Ttot, 24 * n, cudaMemcpyDeviceToHost, s), "copy torque");
+        CK(cudaStreamSynchronize(s), "colloid sync");
+    }
+    return (int)n;
+}
+
+int lb_get_colloid_terms(lb_ctx* ctx, int which, double* out) {
+    if (!ctx || !out || which < 0 || which > 10) return LB_ERR_ARG;
+    Lattice& L = ctx->L;
+    const double* src[11] = {L.Fliq, L.Tliq, L.Fd, L.Td, L.Fc, L.Tc, L.Fs, L.Ts, L.Fpair, L.Ftot, L.Ttot};
+    if (L.nc) {
+        CK(cudaMemcpyAsync(out, src[which], 24 * (size_t)L.nc, cudaMemcpyDeviceToHost, ctx->stream), "copy term");
+        CK(cudaStreamSynchronize(ctx->stream), "term sync");
+    }
+    return LB_OK;
+}
+
+long long lb_launch_count(const lb_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int lb_destroy(lb_ctx* ctx) {
+    if (!ctx) return LB_ERR_ARG;
+    cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+    return LB_OK;
+}
+
+const char* lb_last_error(const lb_ctx* ctx) { return ctx ? ctx->err : ""; }
+
+}  // extern "C"

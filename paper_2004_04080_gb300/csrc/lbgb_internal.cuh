@@ -1,0 +1,245 @@
+// lbgb_internal.cuh -- device-side definitions shared by the library's
+// translation units: the D3Q19 lattice as compile-time functions, storage
+// conversions, the context layout and the kernel entry points.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lbgb.h"
+
+namespace lbgb {
+
+// ---------------------------------------------------------------- lattice
+// D3Q19 (Sec. 2.1).  Link 0 rests; 1-6 are the axis links +x,-x,+y,-y,+z,-z;
+// 7-18 the face diagonals, ordered so that link i (odd) and i+1 are opposite.
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+// lattice weights w0 = 1/3, w1-6 = 1/18, w7-18 = 1/36
+template <typename C>
+__host__ __device__ constexpr C wgt(int i) {
+    return i == 0 ? C(1) / C(3) : (i <= 6 ? C(1) / C(18) : C(1) / C(36));
+}
+constexpr int Q = 19;
+
+// ---------------------------------------------------------- precisions
+// Storage type S and compute type C of the populations.
+template <int PREC> struct Prec;
+template <> struct Prec<LB_FP64> { typedef double S; typedef double C; };
+template <> struct Prec<LB_FP32> { typedef float S; typedef float C; };
+template <> struct Prec<LB_FP16> { typedef __half S; typedef float C; };
+
+// load / store one population; FP16 stores the deviation f - w_i rho0^k
+__device__ __forceinline__ double ld_pop(const double* p, double) { return *p; }
+__device__ __forceinline__ float ld_pop(const float* p, float) { return *p; }
+__device__ __forceinline__ float ld_pop(const __half* p, float shift) {
+    return __half2float(*p) + shift;
+}
+__device__ __forceinline__ void st_pop(double* p, double v, double) { *p = v; }
+__device__ __forceinline__ void st_pop(float* p, float v, float) { *p = v; }
+__device__ __forceinline__ void st_pop(__half* p, float v, float shift) {
+    *p = __float2half_rn(v - shift);
+}
+
+// ------------------------------------------------------------- context
+// Device-visible view of one lattice (passed by value to every kernel).
+struct Lattice {
+    int nx, ny, nz;
+    long long N;       // nx*ny*nz
+    long long pstride; // elements between two population planes (>= N, padded)
+    int per[3];        // periodic flags
+    void* f_cur;       // populations at time t: [2][19][pstride] of S
+    void* f_nxt;       // populations at time t+1
+    void* psi;         // [2][N] of C: rho^k on fluid, virtual density on frontier
+    void* psi_wall;    // [2 walls][2 comps][nx*ny] of C
+    uint8_t* mask;     // 1 on particle nodes
+    int* owner;        // -1 fluid, else particle index
+    int* evt;          // remap events: 4 (p+1) + 1 destroy, 4 (p+1) + 2 create
+    int* flags;        // [0] error bits
+    // particles (FP64, [n][3] / [n][4] / [n])
+    int nc;
+    double *pos, *vel, *omg, *quat, *rad, *mass;
+    double *Fliq, *Tliq, *Fliq_prev, *Tliq_prev;
+    int* prev_valid;
+    double *Fd, *Td, *Fc, *Tc, *Fs, *Ts, *Fpair, *Ftot, *Ttot;
+    double rmax;       // largest particle radius
+    double* red;       // reduction partials
+    int red_blocks;
+    lb_params P;
+};
+
+enum { FLAG_NONFINITE = 1, FLAG_OVERLAP = 2 };
+
+// ------------------------------------------------- compensated FP64 sums
+struct NSum {
+    double s, c;
+    __device__ __forceinline__ void add(double x) {
+        double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ void merge(const NSum& o) {
+        add(o.s);
+        c += o.c;
+    }
+    __device__ __forceinline__ double value() const { return s + c; }
+};
+
+// ----------------------------------------------------------- site helpers
+struct SiteNbr {
+    int x, y, z;
+    int xm, xp, ym, yp, zm, zp;  // wrapped neighbour coordinates
+    bool wall_lo, wall_hi;        // z-1 / z+1 lies beyond a wall
+};
+
+__device__ __forceinline__ SiteNbr site_nbr(const Lattice& L, int x, int y, int z) {
+    SiteNbr n;
+    n.x = x; n.y = y; n.z = z;
+    n.xm = x == 0 ? L.nx - 1 : x - 1;
+    n.xp = x == L.nx - 1 ? 0 : x + 1;
+    n.ym = y == 0 ? L.ny - 1 : y - 1;
+    n.yp = y == L.ny - 1 ? 0 : y + 1;
+    n.zm = z == 0 ? L.nz - 1 : z - 1;
+    n.zp = z == L.nz - 1 ? 0 : z + 1;
+    n.wall_lo = (z == 0) && !L.per[2];
+    n.wall_hi = (z == L.nz - 1) && !L.per[2];
+    return n;
+}
+
+// site index of the neighbour along link i (caller checks walls first)
+__device__ __forceinline__ long long nbr_index(const Lattice& L, const SiteNbr& n, int i) {
+    int X = cx(i) == 0 ? n.x : (cx(i) > 0 ? n.xp : n.xm);
+    int Y = cy(i) == 0 ? n.y : (cy(i) > 0 ? n.yp : n.ym);
+    int Z = cz(i) == 0 ? n.z : (cz(i) > 0 ? n.zp : n.zm);
+    return (long long)X + (long long)L.nx * ((long long)Y + (long long)L.ny * Z);
+}
+
+__device__ __forceinline__ bool nbr_is_wall(const SiteNbr& n, int i) {
+    return (cz(i) < 0 && n.wall_lo) || (cz(i) > 0 && n.wall_hi);
+}
+
+// Eq. 5: f_i^eq = w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u)   (cs^2 = 1/3)
+template <typename C>
+__device__ __forceinline__ C feq(int i, C rho, C ux, C uy, C uz, C uu) {
+    C cu = C(cx(i)) * ux + C(cy(i)) * uy + C(cz(i)) * uz;
+    return wgt<C>(i) * rho * (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ C pop_shift(const Lattice& L, int k, int i) {
+    return (sizeof(S) == 2) ? wgt<C>(i) * C(L.P.rho0[k]) : C(0);
+}
+
+// Load the 2 x 19 populations of one site and form rho^k and j^k
+// (Eqs. 6, 7).  The summation order is fixed (i = 0..18) so that every
+// kernel obtains bit-identical densities for the same site.
+template <int PREC>
+__device__ __forceinline__ void load_site(const Lattice& L, const typename Prec<PREC>::S* f,
+                                          long long s, typename Prec<PREC>::C (&fv)[2][Q],
+                                          typename Prec<PREC>::C (&rho)[2],
+                                          typename Prec<PREC>::C (&j)[2][3]) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        C r = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            C v = ld_pop(f + ((long long)(k * Q + i)) * L.pstride + s, pop_shift<S, C>(L, k, i));
+            fv[k][i] = v;
+            r += v;
+            if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
+            if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
+            if (cz(i) > 0) jz += v; else if (cz(i) < 0) jz -= v;
+        }
+        rho[k] = r;
+        j[k][0] = jx; j[k][1] = jy; j[k][2] = jz;
+    }
+}
+
+// Eq. 11 (repulsive sign) plus the body force: F^k = -G rho^k sum_i w_i
+// psi^kbar(x + c_i) c_i + rho^k g.  psi is rho on fluid nodes, the virtual
+// density (Eq. 20) on particle frontier nodes and the wall density beyond a
+// wall.
+template <typename C>
+__device__ __forceinline__ void sc_force(const Lattice& L, const SiteNbr& n, const C (&rho)[2],
+                                         C (&F)[2][3]) {
+    const C* psi = (const C*)L.psi;
+    const C* pw = (const C*)L.psi_wall;
+    long long nxy = (long long)L.nx * L.ny;
+    C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};  // sums of w psi^A c and w psi^B c
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        C pa, pb;
+        if (nbr_is_wall(n, i)) {
+            int X = cx(i) == 0 ? n.x : (cx(i) > 0 ? n.xp : n.xm);
+            int Y = cy(i) == 0 ? n.y : (cy(i) > 0 ? n.yp : n.ym);
+            int side = cz(i) < 0 ? 0 : 1;
+            long long w = (long long)X + (long long)L.nx * Y;
+            pa = pw[(side * 2 + 0) * nxy + w];
+            pb = pw[(side * 2 + 1) * nxy + w];
+        } else {
+            long long m = nbr_index(L, n, i);
+            pa = __ldg(psi + m);
+            pb = __ldg(psi + L.N + m);
+        }
+        C w = wgt<C>(i);
+        if (cx(i)) { sA[0] += C(cx(i)) * w * pa; sB[0] += C(cx(i)) * w * pb; }
+        if (cy(i)) { sA[1] += C(cy(i)) * w * pa; sB[1] += C(cy(i)) * w * pb; }
+        if (cz(i)) { sA[2] += C(cz(i)) * w * pa; sB[2] += C(cz(i)) * w * pb; }
+    }
+    C G = C(L.P.G);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        C g = C(L.P.body_force[d]);
+        F[0][d] = -G * rho[0] * sB[d] + rho[0] * g;  // component A feels B
+        F[1][d] = -G * rho[1] * sA[d] + rho[1] * g;  // component B feels A
+    }
+}
+
+// Eq. 14 mixture velocity with omega^k = 1/tau_k, and the relaxation
+// frequency of the mixture 1/(nubar/cs^2 + 1/2), 1/nubar = sum_k (rho^k/rho)/nu_k.
+template <typename C>
+__device__ __forceinline__ void mixture(const Lattice& L, const C (&rho)[2], const C (&j)[2][3],
+                                        C (&u)[3], C& om) {
+    C w0 = C(1) / C(L.P.tau[0]), w1 = C(1) / C(L.P.tau[1]);
+    C den = w0 * rho[0] + w1 * rho[1];
+#pragma unroll
+    for (int d = 0; d < 3; d++) u[d] = (w0 * j[0][d] + w1 * j[1][d]) / den;
+    C nu0 = (C(L.P.tau[0]) - C(0.5)) / C(3), nu1 = (C(L.P.tau[1]) - C(0.5)) / C(3);
+    C rt = rho[0] + rho[1];
+    C inv_nu = (rho[0] / rt) / nu0 + (rho[1] / rt) / nu1;
+    C nubar = C(1) / inv_nu;
+    om = C(1) / (C(3) * nubar + C(0.5));
+}
+
+// kernel launchers (each returns the number of kernels it launched)
+int launch_init_fields(const Lattice& L, int prec, const double* stage, cudaStream_t st);
+int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st);
+int launch_density(const Lattice& L, int prec, cudaStream_t st);
+int launch_wall_psi(const Lattice& L, int prec, cudaStream_t st);
+int launch_fields_out(const Lattice& L, int prec, double* stage, cudaStream_t st);
+int launch_totals(const Lattice& L, int prec, double* out_dev, cudaStream_t st);
+int launch_populations_out(const Lattice& L, int prec, int k, int i, double* stage, cudaStream_t st);
+int launch_clear_map(const Lattice& L, cudaStream_t st);
+
+int launch_map_initial(const Lattice& L, int first, int count, cudaStream_t st);
+int launch_remap(const Lattice& L, int prec, cudaStream_t st);
+int launch_virtual(const Lattice& L, int prec, int store_terms, cudaStream_t st);
+int launch_links(const Lattice& L, int prec, cudaStream_t st);
+int launch_pairs_integrate(const Lattice& L, cudaStream_t st);
+
+}  // namespace lbgb

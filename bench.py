@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the colloidal Shan-Chen lattice-Boltzmann step.
+
+One step = one pass of the whole coupled update (remap, densities, wetting,
+fused collide/stream with bounce-back, link forces, pair forces, integrator)
+over the confined sheared bijel workload: 512x512x256 sites, walls normal to z
+moving at +-0.05, radius-5.5 spheres at volume fraction 0.15 (14,444), 50/50
+mixture with +-1 % seeded noise, G = 0.65, tau = 1, FP32 storage.
+
+Prints one JSON line (rank 0).  ``value`` is MLUPS = sites x steps / time
+(Eqs. 36-37, all sites), summed over ranks; every rank runs an independent
+replica (the method is not sharded here).  ``--impl reference`` times the
+plain FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % HBM roofline, FP32 vs FP16-store vs FP64 at stated error; adjoint/fwd time"
+# algorithmic bytes per site update: read + write of 2 x 19 populations + 1 mask byte
+ALG_BYTES = {"fp64": 2 * 38 * 8 + 1, "fp32": 2 * 38 * 4 + 1, "fp16": 2 * 38 * 2 + 1}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32-math"}
+# stated parity bounds against the FP64 oracle (relative, fields after 100 steps), as tested
+STATED_ERROR = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 1e-3}
+FUSED_KERNEL_SRC = os.path.join(ROOT, "paper_2004_04080_gb300", "csrc", "lbgb_fluid.cu")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash():
+    with open(FUSED_KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(prec):
+    """ncu DRAM bytes per launch of the fused kernel, if the committed record
+    was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d.get(prec)
+        if e and e.get("kernel_sha") == kernel_hash():
+            return float(e["bytes_per_launch_full_workload"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.uuid, "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(name, target_seconds=20.0):
+    """The FP64 oracle (as it stands, one host thread) on a bounded sample of
+    the workload: a 128x128x64 sub-box with the same physics and particle
+    volume fraction, stepped until about target_seconds have passed."""
+    from oracle import Oracle
+    from paper_2004_04080_gb300.workloads import workload
+
+    sub = (128, 128, 64)
+    w = workload(name, scale=sub)
+    a, b = w.densities()
+    c = w.colloids()
+    o = Oracle(*w.shape, max(w.n_colloids, 1))
+    o.set_params(**w.params)
+    o.init_fields(a, b)
+    if c is not None:
+        o.add_colloids(c["pos"], c["radius"], c["mass"])
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > target_seconds or steps >= 50:
+            break
+    mlups = w.n_sites * steps / el / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%s sub-box %dx%dx%d, %d particles, %d steps, %.1f s" % (
+                name, *sub, w.n_colloids, steps, el)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    base = cpu_baseline(args.workload, target_seconds=max(5.0, min(60.0, 2.0 * (args.steps + args.warmup))))
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "prec": "fp64 oracle", "parallelism": "single host thread"},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_steps(lat, steps, torch):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    lat.step(steps)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="shear512")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "fp64"])
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP16/FP64 side measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2004_04080_gb300.lbgb import LBLattice
+    from paper_2004_04080_gb300.workloads import workload
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = workload(args.workload)
+    a, b = w.densities()
+    col = w.colloids()
+    lat = LBLattice(w.shape, args.prec, max_colloids=w.n_colloids, device=dev)
+    lat.set_params(**w.params)
+    lat.init_fields(a, b)
+    lat.add_colloids(col["pos"], col["radius"], col["mass"])
+    lat.step(args.warmup)
+    barrier()
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    launches0 = lat.launch_count()
+    lat.profile(True)
+    with ClockSampler(uuid) as clk:
+        barrier()
+        ms = time_steps(lat, args.steps, torch)
+        barrier()
+    launches = lat.launch_count() - launches0
+    kern_ms, kern_n = lat.profile_read()
+    lat.profile(False)
+    ms = max_over_ranks(ms)
+    ms_step = ms / args.steps
+    value = world * w.n_sites * args.steps / (ms / 1e3) / 1e6
+    peak, peak_kind = peaks()
+    alg = ALG_BYTES[args.prec] * w.n_sites
+    kavg = kern_ms / max(kern_n, 1)
+    achieved = alg / (kavg / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.prec),
+                "kernel": "k_collide_push", "kernel_ms": round(kavg, 4),
+                "alg_bytes_per_launch": alg, "peak_kind": peak_kind,
+                "step_frac": round(alg / (ms_step / 1e3) / 1e9 / peak, 4)}
+
+    # end to end through the public API with pinned host buffers
+    N = w.n_sites
+    pin = lambda n: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    ha, hb = pin(N), pin(N)
+    ha[:] = a
+    hb[:] = b
+    oa, ob, ou = pin(N), pin(N), pin(3 * N)
+    n = w.n_colloids
+    hp = pin(3 * n)
+    hp[:] = col["pos"].ravel()
+    hr, hm = pin(n), pin(n)
+    hr[:] = col["radius"]
+    hm[:] = col["mass"]
+    cpos, cvel = pin(3 * n), pin(3 * n)
+    barrier()
+    t0 = time.perf_counter()
+    from paper_2004_04080_gb300 import lbgb as api
+
+    api.lb_init_fields(lat.h, ha, hb)
+    api.lb_add_colloids(lat.h, hp, hr, hm)
+    api.lb_step(lat.h, args.steps)
+    api.lb_get_fields(lat.h, oa, ob, ou)
+    api.lb_get_colloids(lat.h, cpos, cvel, None, None, None, None)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": round(world * N * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": int((2 * N * 8 + n * 5 * 8) / args.steps),
+           "d2h_bytes_per_step": int((5 * N * 8 + n * 6 * 8) / args.steps)}
+    del lat
+    torch.cuda.empty_cache()
+
+    forms = {}
+    if not args.no_forms:
+        for prec, steps in (("fp16", max(20, min(args.steps, 200))), ("fp64", 10)):
+            if prec == args.prec:
+                continue
+            L2 = LBLattice(w.shape, prec, max_colloids=n, device=dev)
+            L2.set_params(**w.params)
+            L2.init_fields(a, b)
+            L2.add_colloids(col["pos"], col["radius"], col["mass"])
+            L2.step(3)
+            L2.profile(True)
+            barrier()
+            m2 = max_over_ranks(time_steps(L2, steps, torch))
+            km, kn = L2.profile_read()
+            kk = km / max(kn, 1)
+            forms[prec] = {"mlups": round(world * N * steps / (m2 / 1e3) / 1e6, 1), "steps": steps,
+                           "kernel_frac": round(ALG_BYTES[prec] * N / (kk / 1e3) / 1e9 / peak, 4),
+                           "stated_rel_error_vs_fp64_oracle": STATED_ERROR[prec]}
+            del L2
+            torch.cuda.empty_cache()
+        forms[args.prec] = {"mlups": round(value, 1), "stated_rel_error_vs_fp64_oracle": STATED_ERROR[args.prec]}
+        if "fp16" in forms and args.prec == "fp32":
+            forms["fp16_speedup_over_fp32"] = round(forms["fp16"]["mlups"] / value, 3)
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec],
+            "data": "synthetic",
+            "config": {"workload": "%s: %dx%dx%d sites, walls z +-0.05, R=5.5 phi=0.15 (%d particles), "
+                                   "G=0.65, tau=1" % (args.workload, *w.shape, n),
+                       "prec": args.prec, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (%.1f GB of populations)" % (
+                           2 * 38 * N * {"fp64": 8, "fp32": 4, "fp16": 2}[args.prec] / 1e9)},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+            "forms": forms, "adjoint": None}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -143,6 +143,16 @@ int lb_get_populations(lb_ctx *ctx, int k, double *out);
 /* Node map: -1 fluid, else the index of the owning particle, [N]. */
 int lb_get_owner(lb_ctx *ctx, int *out);
 
+/* Kernel timing.  While enabled, lb_step records a CUDA event pair on the
+ * context stream around every launch of the fused lattice kernel (the
+ * collide + Shan-Chen + bounce-back + stream kernel, the dominant one).
+ * lb_profile(ctx, 1) enables and clears the record, lb_profile(ctx, 0)
+ * disables it; lb_profile_read waits for the recorded events and returns the
+ * summed kernel time (ms) and the number of timed launches (at most 16384 are
+ * kept per record). */
+int lb_profile(lb_ctx *ctx, int enable);
+int lb_profile_read(lb_ctx *ctx, double *total_ms, long long *launches);
+
 /* Number of kernel launches issued by this context since creation. */
 long long lb_launch_count(const lb_ctx *ctx);
 

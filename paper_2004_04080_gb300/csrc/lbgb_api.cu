@@ -22,6 +22,11 @@ struct lb_ctx {
     int have_params, have_fields, stepped;
     long long launches;
     double* totals_dev;
+    void* cells;
+    size_t cells_bytes;
+    int prof_on;
+    int prof_n;                 // recorded event pairs
+    cudaEvent_t* prof_ev;       // 2 * PROF_MAX events, created on first use
     char err[512];
 };
 
@@ -36,9 +41,11 @@ size_t compute_bytes(int prec) { return prec == LB_FP64 ? 8 : 4; }
 
 const int DOUBLES_PER_PARTICLE = 57;  // pos..Ttot, see carve()
 const int RED_BLOCKS = 1024;
+const int PROF_MAX = 16384;
 
 struct Layout {
-    size_t f0, f1, psi, psi_wall, mask, owner, evt, flags, col, prev, red, totals, total;
+    size_t f0, f1, psi, psi_wall, mask, owner, evt, flags, col, prev, ipos, fsnap, cells, cells_bytes, red,
+        totals, total;
     long long pstride;
 };
 
@@ -62,6 +69,11 @@ Layout layout(int nx, int ny, int nz, int prec, int maxc) {
     int mc = maxc > 0 ? maxc : 1;
     l.col = off; off = align_up(off + (size_t)mc * DOUBLES_PER_PARTICLE * 8);
     l.prev = off; off = align_up(off + (size_t)mc * 4);
+    l.ipos = off; off = align_up(off + (size_t)mc * 12);
+    l.fsnap = off; off = align_up(off + (size_t)mc * 36);
+    // particle cell list: counts and starts of up to 64^3 cells, then the items
+    l.cells_bytes = ((size_t)2 * 64 * 64 * 64 + 1 + (size_t)mc) * 4;
+    l.cells = off; off = align_up(off + l.cells_bytes);
     l.red = off; off = align_up(off + (size_t)RED_BLOCKS * 16 * 8);
     l.totals = off; off = align_up(off + 8 * 8);
     l.total = off;
@@ -153,9 +165,13 @@ int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_worksp
                        &L.Tc, &L.Fs, &L.Ts, &L.Fpair, &L.Ftot, &L.Ttot};
     for (int a = 0; a < 13; a++) { *more[a] = c; c += 3 * mc; }
     L.prev_valid = (int*)(ctx->ws + l.prev);
+    L.ipos = (int*)(ctx->ws + l.ipos);
+    L.fsnap = (float*)(ctx->ws + l.fsnap);
     L.red = (double*)(ctx->ws + l.red);
     L.red_blocks = RED_BLOCKS;
     ctx->totals_dev = (double*)(ctx->ws + l.totals);
+    ctx->cells = ctx->ws + l.cells;
+    ctx->cells_bytes = l.cells_bytes;
     L.nc = 0;
     // empty node map, no particles, no error flags
     cudaError_t e = cudaMemsetAsync(ctx->ws + l.mask, 0, (size_t)L.N, ctx->stream);
@@ -275,7 +291,10 @@ int lb_add_colloids(lb_ctx* ctx, int n, const double* pos, const double* vel, co
     if (e) return cuda_check(ctx, e, "copy particles");
     L.nc = first + n;
     L.rmax = rmax;
-    int rc = launched(ctx, launch_map_initial(L, first, n, s), "map kernel");
+    // the FP32 snapshot first: the map kernel of the FP32 forms reads it
+    int nl = launch_snapshot(L, s);
+    nl += launch_map_initial(L, ctx->prec, first, n, s);
+    int rc = launched(ctx, nl, "map kernel");
     if (rc) return rc;
     int flags = 0;
     CK(cudaMemcpyAsync(&flags, L.flags, 4, cudaMemcpyDeviceToHost, s), "read flags");
@@ -293,12 +312,18 @@ int lb_step(lb_ctx* ctx, int nsteps) {
     for (int t = 0; t < nsteps; t++) {
         int n = 0;
         n += launch_remap(L, ctx->prec, s);           // destroy / create (Eqs. 24, 25)
-        n += launch_density(L, ctx->prec, s);          // rho^k (Eq. 6)
+        n += launch_shell_density(L, ctx->prec, s);    // rho^k near particles / walls (Eq. 6)
         n += launch_wall_psi(L, ctx->prec, s);         // wall densities
         n += launch_virtual(L, ctx->prec, 1, s);       // Eqs. 20, 21
+        bool timed = ctx->prof_on && ctx->prof_n < PROF_MAX;
+        if (timed) CK(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], s), "profile event");
         n += launch_fluid_step(L, ctx->prec, s);       // Eqs. 11, 14, 16, 3, 9, 17
+        if (timed) {
+            CK(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], s), "profile event");
+            ctx->prof_n++;
+        }
         n += launch_links(L, ctx->prec, s);            // Eqs. 19, 22, 23
-        n += launch_pairs_integrate(L, s);             // Eqs. 26-27, 32-35
+        n += launch_pairs_integrate(L, ctx->cells, ctx->cells_bytes, s);  // Eqs. 26-27, 32-35
         int rc = launched(ctx, n, "step kernels");
         if (rc) return rc;
         void* tmp = L.f_cur;
@@ -406,9 +431,47 @@ int lb_get_colloid_terms(lb_ctx* ctx, int which, double* out) {
 
 long long lb_launch_count(const lb_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
+int lb_profile(lb_ctx* ctx, int enable) {
+    if (!ctx) return LB_ERR_ARG;
+    if (enable && !ctx->prof_ev) {
+        cudaEvent_t* ev = new (std::nothrow) cudaEvent_t[2 * PROF_MAX];
+        if (!ev) return LB_ERR_NOMEM;
+        for (int i = 0; i < 2 * PROF_MAX; i++) {
+            cudaError_t e = cudaEventCreate(&ev[i]);
+            if (e != cudaSuccess) {
+                for (int j = 0; j < i; j++) cudaEventDestroy(ev[j]);
+                delete[] ev;
+                return cuda_check(ctx, e, "create profile events");
+            }
+        }
+        ctx->prof_ev = ev;
+    }
+    ctx->prof_on = enable ? 1 : 0;
+    if (enable) ctx->prof_n = 0;
+    return LB_OK;
+}
+
+int lb_profile_read(lb_ctx* ctx, double* total_ms, long long* launches) {
+    if (!ctx || !total_ms || !launches) return LB_ERR_ARG;
+    double t = 0.0;
+    for (int i = 0; i < ctx->prof_n; i++) {
+        float ms = 0.f;
+        CK(cudaEventSynchronize(ctx->prof_ev[2 * i + 1]), "profile sync");
+        CK(cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]), "profile elapsed");
+        t += ms;
+    }
+    *total_ms = t;
+    *launches = ctx->prof_n;
+    return LB_OK;
+}
+
 int lb_destroy(lb_ctx* ctx) {
     if (!ctx) return LB_ERR_ARG;
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->prof_ev) {
+        for (int i = 0; i < 2 * PROF_MAX; i++) cudaEventDestroy(ctx->prof_ev[i]);
+        delete[] ctx->prof_ev;
+    }
     delete ctx;
     return LB_OK;
 }

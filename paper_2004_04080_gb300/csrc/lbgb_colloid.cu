@@ -1,109 +1,172 @@
 // lbgb_colloid.cu -- particle kernels: node map and remap (destroy / create),
 // wetting virtual densities with the solid-node Shan-Chen force, Ladd link
-// forces, pair forces and the rotational leap-frog integrator.
+// forces, pair forces (cell list) and the rotational leap-frog integrator.
 //
-// Per-particle work runs one thread block per particle over a box around the
-// sphere; every per-particle sum is a Neumaier-compensated FP64 sum, reduced
-// in a fixed order (each thread's fixed share of the box, then warp shuffles,
-// then warps in order), so the result does not depend on scheduling.
+// Per-particle lattice work runs one 16x8 thread block per particle over the
+// box of lattice points around its sphere.  Geometry is evaluated in the
+// compute type of the populations (FP32 for the FP32 / FP16 forms): FP64
+// arithmetic on GB300 runs at a small fraction of the FP32 rate and costs a
+// whole warp even in a divergent branch, so it is kept out of per-link code.
+// Node membership |x - r_p|^2 < R^2 is nevertheless decided exactly: points
+// whose FP32 distance is within a safe margin of the sphere are re-tested in
+// FP64.  Each thread accumulates its share of a per-particle sum with a
+// compensated (Neumaier) sum in the compute type; the thread partials are
+// merged in FP64 in a fixed order (warp shuffles, then warps in order), so
+// the per-particle totals are FP64 and independent of scheduling.
 #include "lbgb_internal.cuh"
 
 namespace lbgb {
 
-constexpr int PB = 128;  // threads per particle block
+constexpr int BXP = 16, BYP = 8, PB = BXP * BYP;  // particle block
 
-// box of lattice points around particle p, padded by `pad`
-struct PBox {
-    int lo[3], ext[3], total;
-    double r[3], R;
+// geometry of particle p in compute type C
+template <typename C>
+struct PGeo {
+    int lo[3], ext[3];  // box of lattice points
+    int ip[3];          // floor(r_p)
+    C fr[3];            // r_p - floor(r_p)
+    C v[3], w[3];       // v(t-1/2), omega(t-1/2)
+    double R;
+    C R2;
 };
 
-__device__ __forceinline__ PBox make_box(const Lattice& L, int p, double pad) {
-    PBox b;
-    b.R = L.rad[p];
-    b.total = 1;
+template <typename C>
+__device__ __forceinline__ PGeo<C> pgeo(const Lattice& L, int p, double pad) {
+    PGeo<C> g;
+    g.R = L.rad[p];
+    g.R2 = C(g.R) * C(g.R);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        b.r[d] = L.pos[3 * p + d];
-        int lo = (int)floor(b.r[d] - b.R - pad);
-        int hi = (int)ceil(b.r[d] + b.R + pad);
-        b.lo[d] = lo;
-        b.ext[d] = hi - lo + 1;
-        b.total *= b.ext[d];
+        if (sizeof(C) == 8) {
+            double r = L.pos[3 * p + d];
+            g.lo[d] = (int)floor(r - g.R - pad);
+            g.ext[d] = (int)ceil(r + g.R + pad) - g.lo[d] + 1;
+            g.ip[d] = (int)floor(r);
+            g.fr[d] = C(r - (double)g.ip[d]);
+            g.v[d] = C(L.vel[3 * p + d]);
+            g.w[d] = C(L.omg[3 * p + d]);
+        } else {
+            // box from the snapshot: r = ip + fr with fr in [0, 1) (the box only
+            // has to cover the working shell, which it does with a wide margin)
+            g.ip[d] = L.ipos[3 * p + d];
+            g.fr[d] = C(L.fsnap[9 * p + d]);
+            g.v[d] = C(L.fsnap[9 * p + 3 + d]);
+            g.w[d] = C(L.fsnap[9 * p + 6 + d]);
+            float Rp = float(g.R) + float(pad);
+            g.lo[d] = g.ip[d] + (int)floorf(float(g.fr[d]) - Rp);
+            g.ext[d] = g.ip[d] + (int)ceilf(float(g.fr[d]) + Rp) - g.lo[d] + 1;
+        }
     }
-    return b;
+    return g;
 }
 
-// t-th point of the box: wrapped site (X,Y,Z), offset d = point - r_p (no
-// wrap needed: the box is smaller than half of every periodic side).
-// Returns false for points beyond a wall.
-__device__ __forceinline__ bool box_point(const Lattice& L, const PBox& b, int t, int& X, int& Y,
-                                          int& Z, double (&d)[3]) {
-    int a = b.lo[0] + t % b.ext[0];
-    int c = b.lo[1] + (t / b.ext[0]) % b.ext[1];
-    int e = b.lo[2] + t / (b.ext[0] * b.ext[1]);
-    d[0] = (double)a - b.r[0];
-    d[1] = (double)c - b.r[1];
-    d[2] = (double)e - b.r[2];
-    if (!L.per[2] && (e < 0 || e >= L.nz)) return false;
-    X = ((a % L.nx) + L.nx) % L.nx;
-    Y = ((c % L.ny) + L.ny) % L.ny;
-    Z = ((e % L.nz) + L.nz) % L.nz;
-    return true;
+// exact membership |a - r_p|^2 < R^2 (FP64 without contraction, as a plain
+// double evaluation would decide it)
+__device__ __noinline__ bool inside_exact(const Lattice& L, int p, int a, int b, int c) {
+    double dx = (double)a - L.pos[3 * p], dy = (double)b - L.pos[3 * p + 1], dz = (double)c - L.pos[3 * p + 2];
+    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    double R = L.rad[p];
+    return d2 < __dmul_rn(R, R);
 }
 
-// |d|^2 without fused multiply-add, so that node membership (|d|^2 < R^2) is
-// decided with the same rounding as a plain double evaluation
-__device__ __forceinline__ double dist2(const double (&d)[3]) {
-    return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+template <typename C>
+__device__ __forceinline__ bool inside(const Lattice& L, int p, const PGeo<C>& g, const C (&d)[3], int a, int b,
+                                       int c) {
+    if (sizeof(C) == 8) return inside_exact(L, p, a, b, c);
+    C d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    C gap = d2 - g.R2;
+    if (gap > C(1e-2) || gap < C(-1e-2)) return gap < C(0);
+    return inside_exact(L, p, a, b, c);
 }
 
-__device__ __forceinline__ void crossd(const double (&a)[3], const double (&b)[3], double (&o)[3]) {
+// |d| within [R + lo, R + hi) (in the compute type, with the margins chosen
+// by the callers well beyond its rounding): the shell where a kernel can have
+// work, so that the rest of the box is skipped without memory traffic
+template <typename C>
+__device__ __forceinline__ bool in_shell(const PGeo<C>& g, const C (&d)[3], float lo, float hi) {
+    float d2 = float(d[0]) * float(d[0]) + float(d[1]) * float(d[1]) + float(d[2]) * float(d[2]);
+    float a = float(g.R) + lo, b = float(g.R) + hi;
+    return (a <= 0.f || d2 >= a * a) && d2 < b * b;
+}
+
+// Visit the box points of particle p; f(X, Y, Z, s, a, b, c, d) gets the
+// wrapped site, its index, the unwrapped point and its offset from r_p.
+template <typename C, typename Fn>
+__device__ __forceinline__ void for_box(const Lattice& L, const PGeo<C>& g, Fn&& fn) {
+    for (int zz = 0; zz < g.ext[2]; zz++) {
+        int c = g.lo[2] + zz;
+        if (!L.per[2] && (c < 0 || c >= L.nz)) continue;
+        int Z = c < 0 ? c + L.nz : (c >= L.nz ? c - L.nz : c);
+        for (int yy = threadIdx.y; yy < g.ext[1]; yy += BYP) {
+            int b = g.lo[1] + yy;
+            int Y = b < 0 ? b + L.ny : (b >= L.ny ? b - L.ny : b);
+            for (int xx = threadIdx.x; xx < g.ext[0]; xx += BXP) {
+                int a = g.lo[0] + xx;
+                int X = a < 0 ? a + L.nx : (a >= L.nx ? a - L.nx : a);
+                long long s = (long long)X + (long long)L.nx * ((long long)Y + (long long)L.ny * Z);
+                C d[3] = {C(a - g.ip[0]) - g.fr[0], C(b - g.ip[1]) - g.fr[1], C(c - g.ip[2]) - g.fr[2]};
+                fn(X, Y, Z, s, a, b, c, d);
+            }
+        }
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ void crs(const C (&a)[3], const C (&b)[3], C (&o)[3]) {
     o[0] = a[1] * b[2] - a[2] * b[1];
     o[1] = a[2] * b[0] - a[0] * b[2];
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-__device__ __forceinline__ long long sidx(const Lattice& L, int X, int Y, int Z) {
-    return (long long)X + (long long)L.nx * ((long long)Y + (long long)L.ny * Z);
-}
-
-// Block-wide deterministic reduction of M compensated sums; thread 0 gets
-// the results in out[0..M-1].
-template <int M>
-__device__ void block_reduce(NSum (&acc)[M], double* out) {
-    __shared__ double sh_s[PB / 32][M], sh_c[PB / 32][M];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Deterministic block reduction of M per-thread compensated partials into
+// FP64 totals (thread 0 receives them in out).  Within a warp the (s, c)
+// pairs are merged in the compute type with the same compensated rule (a
+// fixed butterfly); lane m < M of warp 0 then converts the warp partials of
+// value m to FP64 and merges them in warp order, so the FP64 work is a few
+// instructions per block rather than per thread.
+template <int M, typename C>
+__device__ void block_reduce(CSum<C> (&part)[M], double* out) {
+    __shared__ C sh_s[PB / 32][M], sh_c[PB / 32][M];
+    __shared__ double sh_out[M];
+    int tid = threadIdx.y * BXP + threadIdx.x;
+    int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int m = 0; m < M; m++) {
+        CSum<C> acc = part[m];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            NSum o;
-            o.s = __shfl_down_sync(0xffffffffu, acc[m].s, off);
-            o.c = __shfl_down_sync(0xffffffffu, acc[m].c, off);
-            if (lane < off) acc[m].merge(o);
+            C os = __shfl_down_sync(0xffffffffu, acc.s, off);
+            C oc = __shfl_down_sync(0xffffffffu, acc.c, off);
+            if (lane < off) {
+                acc.add(os);
+                acc.c += oc;
+            }
         }
         if (lane == 0) {
-            sh_s[warp][m] = acc[m].s;
-            sh_c[warp][m] = acc[m].c;
+            sh_s[warp][m] = acc.s;
+            sh_c[warp][m] = acc.c;
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int m = 0; m < M; m++) {
-            NSum t = {sh_s[0][m], sh_c[0][m]};
-            for (int w = 1; w < PB / 32; w++) {
-                NSum o = {sh_s[w][m], sh_c[w][m]};
-                t.merge(o);
-            }
-            out[m] = t.value();
+    if (warp == 0 && lane < M) {
+        NSum t = {0.0, 0.0};
+        for (int w = 0; w < PB / 32; w++) {
+            NSum o = {double(sh_s[w][lane]), double(sh_c[w][lane])};
+            t.merge(o);
         }
+        sh_out[lane] = t.value();
     }
+    __syncthreads();
+    if (tid == 0)
+        for (int m = 0; m < M; m++) out[m] = sh_out[m];
 }
 
-// density of component k at a site from its populations (same order as the
-// lattice kernels)
+template <typename C, int M>
+__device__ __forceinline__ void zero(CSum<C> (&a)[M]) {
+#pragma unroll
+    for (int m = 0; m < M; m++) a[m].s = a[m].c = C(0);
+}
+
 template <int PREC>
 __device__ __forceinline__ typename Prec<PREC>::C site_rho(const Lattice& L, long long s, int k) {
     typedef typename Prec<PREC>::S S;
@@ -116,56 +179,64 @@ __device__ __forceinline__ typename Prec<PREC>::C site_rho(const Lattice& L, lon
     return r;
 }
 
-// ------------------------------------------------------ initial node map
-// First map after particles are added: solid nodes are claimed without
-// momentum bookkeeping (Sec. 2.4).
-__global__ void __launch_bounds__(PB) k_map_initial(Lattice L, int first) {
-    int p = first + blockIdx.x;
-    PBox b = make_box(L, p, 0.0);
-    for (int t = threadIdx.x; t < b.total; t += PB) {
-        int X, Y, Z;
-        double d[3];
-        if (!box_point(L, b, t, X, Y, Z, d)) continue;
-        if (!(dist2(d) < b.R * b.R)) continue;
-        long long s = sidx(L, X, Y, Z);
-        int old = atomicCAS(L.owner + s, -1, p);
-        if (old != -1 && old != p) atomicOr(L.flags, FLAG_OVERLAP);
-        L.mask[s] = 1;
+// -------------------------------------------------- FP32 snapshot
+__global__ void k_snapshot(Lattice L) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.nc) return;
+    for (int d = 0; d < 3; d++) {
+        double r = L.pos[3 * p + d];
+        int ip = (int)floor(r);
+        L.ipos[3 * p + d] = ip;
+        L.fsnap[9 * p + d] = float(r - (double)ip);
+        L.fsnap[9 * p + 3 + d] = float(L.vel[3 * p + d]);
+        L.fsnap[9 * p + 6 + d] = float(L.omg[3 * p + d]);
     }
 }
 
+// ------------------------------------------------------ initial node map
+// First map after particles are added: nodes are claimed without momentum
+// bookkeeping (Sec. 2.4).
+template <int PREC>
+__global__ void __launch_bounds__(PB) k_map_initial(Lattice L, int first) {
+    typedef typename Prec<PREC>::C C;
+    int p = first + blockIdx.x;
+    PGeo<C> g = pgeo<C>(L, p, 0.0);
+    for_box<C>(L, g, [&](int, int, int, long long s, int a, int b, int c, const C (&d)[3]) {
+        if (!inside<C>(L, p, g, d, a, b, c)) return;
+        int old = atomicCAS(L.owner + s, -1, p);
+        if (old != -1 && old != p) atomicOr(L.flags, FLAG_OVERLAP);
+        L.mask[s] = 1;
+    });
+}
+
 // ------------------------------------------------------------- remap
-// Classify the nodes around particle p at its new position r_p(t):
-//   fluid node now inside  -> destroy (Eq. 24): its momentum rho u goes to p
-//   node of p now outside  -> create (handled by k_remap_create)
+// Classify the points around particle p at its new position r_p(t):
+//   fluid node now inside -> destroy (Eq. 24): its momentum rho u goes to p
+//   node of p now outside -> create (handled by k_remap_create)
 template <int PREC>
 __global__ void __launch_bounds__(PB) k_remap_classify(Lattice L) {
     typedef typename Prec<PREC>::C C;
     int p = blockIdx.x;
-    PBox b = make_box(L, p, 2.0);
-    NSum acc[6];
-#pragma unroll
-    for (int m = 0; m < 6; m++) acc[m].s = acc[m].c = 0.0;
-    for (int t = threadIdx.x; t < b.total; t += PB) {
-        int X, Y, Z;
-        double d[3];
-        if (!box_point(L, b, t, X, Y, Z, d)) continue;
-        long long s = sidx(L, X, Y, Z);
-        bool inside = dist2(d) < b.R * b.R;
+    PGeo<C> g = pgeo<C>(L, p, 1.5);
+    CSum<C> acc[6];
+    zero(acc);
+    for_box<C>(L, g, [&](int, int, int, long long s, int a, int b, int c, const C (&d)[3]) {
+        // a node changes side only within the distance moved (< 1/2, checked
+        // by the integrator) of the sphere
+        if (!in_shell<C>(g, d, -0.65f, 0.65f)) return;
         int o = L.owner[s];
-        if (inside) {
+        if (inside<C>(L, p, g, d, a, b, c)) {
             if (o == -1) {
-                int prev = atomicCAS(L.evt + s, 0, 4 * (p + 1) + 1);
-                if (prev != 0) {
+                if (atomicCAS(L.evt + s, 0, 4 * (p + 1) + 1) != 0) {
                     atomicOr(L.flags, FLAG_OVERLAP);
-                    continue;
+                    return;
                 }
                 C fv[2][Q], rho[2], j[2][3], u[3], om;
                 load_site<PREC>(L, (const typename Prec<PREC>::S*)L.f_cur, s, fv, rho, j);
                 mixture<C>(L, rho, j, u, om);
-                double rt = double(rho[0] + rho[1]);
-                double mom[3] = {rt * double(u[0]), rt * double(u[1]), rt * double(u[2])}, tq[3];
-                crossd(d, mom, tq);
+                C rt = rho[0] + rho[1];
+                C mom[3] = {rt * u[0], rt * u[1], rt * u[2]}, tq[3];
+                crs<C>(d, mom, tq);
 #pragma unroll
                 for (int m = 0; m < 3; m++) {
                     acc[m].add(mom[m]);
@@ -177,10 +248,10 @@ __global__ void __launch_bounds__(PB) k_remap_classify(Lattice L) {
         } else if (o == p) {
             L.evt[s] = 4 * (p + 1) + 2;
         }
-    }
+    });
     double out[6];
-    block_reduce<6>(acc, out);
-    if (threadIdx.x == 0)
+    block_reduce<6, C>(acc, out);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int m = 0; m < 3; m++) {
             L.Fd[3 * p + m] = out[m];
             L.Td[3 * p + m] = out[3 + m];
@@ -195,17 +266,13 @@ __global__ void __launch_bounds__(PB) k_remap_create(Lattice L) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
     int p = blockIdx.x;
-    PBox b = make_box(L, p, 2.0);
-    NSum acc[6];
-#pragma unroll
-    for (int m = 0; m < 6; m++) acc[m].s = acc[m].c = 0.0;
+    PGeo<C> g = pgeo<C>(L, p, 1.5);
+    CSum<C> acc[6];
+    zero(acc);
     const int code = 4 * (p + 1) + 2;
-    for (int t = threadIdx.x; t < b.total; t += PB) {
-        int X, Y, Z;
-        double d[3];
-        if (!box_point(L, b, t, X, Y, Z, d)) continue;
-        long long s = sidx(L, X, Y, Z);
-        if (L.evt[s] != code) continue;
+    for_box<C>(L, g, [&](int X, int Y, int Z, long long s, int, int, int, const C (&d)[3]) {
+        if (!in_shell<C>(g, d, -0.65f, 0.65f)) return;
+        if (L.evt[s] != code) return;
         SiteNbr n = site_nbr(L, X, Y, Z);
         C num[2] = {0, 0}, den = 0;
         for (int i = 1; i < Q; i++) {
@@ -219,29 +286,27 @@ __global__ void __launch_bounds__(PB) k_remap_create(Lattice L) {
         }
         C rb[2];
         for (int k = 0; k < 2; k++) rb[k] = den > C(0) ? num[k] / den : C(L.P.rho0[k]);
-        const double* v = L.vel + 3 * p;
-        const double* w = L.omg + 3 * p;
-        double uw[3] = {v[0] + (w[1] * d[2] - w[2] * d[1]), v[1] + (w[2] * d[0] - w[0] * d[2]),
-                        v[2] + (w[0] * d[1] - w[1] * d[0])};
-        C ux = C(uw[0]), uy = C(uw[1]), uz = C(uw[2]);
-        C uu = ux * ux + uy * uy + uz * uz;
+        C wxd[3], uw[3];
+        crs<C>(g.w, d, wxd);
+        for (int m = 0; m < 3; m++) uw[m] = g.v[m] + wxd[m];
+        C uu = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
         S* f = (S*)L.f_cur;
         for (int k = 0; k < 2; k++)
             for (int i = 0; i < Q; i++)
-                st_pop(f + ((long long)(k * Q + i)) * L.pstride + s, feq<C>(i, rb[k], ux, uy, uz, uu),
+                st_pop(f + ((long long)(k * Q + i)) * L.pstride + s, feq<C>(i, rb[k], uw[0], uw[1], uw[2], uu),
                        pop_shift<S, C>(L, k, i));
-        double rt = double(rb[0] + rb[1]);
-        double mom[3] = {-rt * uw[0], -rt * uw[1], -rt * uw[2]}, tq[3];
-        crossd(d, mom, tq);
+        C rt = rb[0] + rb[1];
+        C mom[3] = {-rt * uw[0], -rt * uw[1], -rt * uw[2]}, tq[3];
+        crs<C>(d, mom, tq);
 #pragma unroll
         for (int m = 0; m < 3; m++) {
             acc[m].add(mom[m]);
             acc[3 + m].add(tq[m]);
         }
-    }
+    });
     double out[6];
-    block_reduce<6>(acc, out);
-    if (threadIdx.x == 0)
+    block_reduce<6, C>(acc, out);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int m = 0; m < 3; m++) {
             L.Fc[3 * p + m] = out[m];
             L.Tc[3 * p + m] = out[3 + m];
@@ -249,14 +314,13 @@ __global__ void __launch_bounds__(PB) k_remap_create(Lattice L) {
 }
 
 // Commit the new node map of particle p.
+template <int PREC>
 __global__ void __launch_bounds__(PB) k_remap_commit(Lattice L) {
+    typedef typename Prec<PREC>::C C;
     int p = blockIdx.x;
-    PBox b = make_box(L, p, 2.0);
-    for (int t = threadIdx.x; t < b.total; t += PB) {
-        int X, Y, Z;
-        double d[3];
-        if (!box_point(L, b, t, X, Y, Z, d)) continue;
-        long long s = sidx(L, X, Y, Z);
+    PGeo<C> g = pgeo<C>(L, p, 1.5);
+    for_box<C>(L, g, [&](int, int, int, long long s, int, int, int, const C (&d)[3]) {
+        if (!in_shell<C>(g, d, -0.65f, 0.65f)) return;
         int e = L.evt[s];
         if (e == 4 * (p + 1) + 1) {
             int old = atomicCAS(L.owner + s, -1, p);
@@ -268,7 +332,7 @@ __global__ void __launch_bounds__(PB) k_remap_commit(Lattice L) {
             L.mask[s] = 0;
             L.evt[s] = 0;
         }
-    }
+    });
 }
 
 // ------------------------------------------------------------ wetting
@@ -280,17 +344,15 @@ template <int PREC>
 __global__ void __launch_bounds__(PB) k_virtual(Lattice L, int store_terms) {
     typedef typename Prec<PREC>::C C;
     int p = blockIdx.x;
-    PBox b = make_box(L, p, 0.0);
+    PGeo<C> g = pgeo<C>(L, p, 0.0);
     C* psi = (C*)L.psi;
-    NSum acc[6];
-#pragma unroll
-    for (int m = 0; m < 6; m++) acc[m].s = acc[m].c = 0.0;
-    for (int t = threadIdx.x; t < b.total; t += PB) {
-        int X, Y, Z;
-        double d[3];
-        if (!box_point(L, b, t, X, Y, Z, d)) continue;
-        long long s = sidx(L, X, Y, Z);
-        if (L.owner[s] != p) continue;
+    CSum<C> acc[6];
+    zero(acc);
+    const C G = C(L.P.G), z0 = C(1) + C(L.P.zeta[0]), z1 = C(1) + C(L.P.zeta[1]);
+    for_box<C>(L, g, [&](int X, int Y, int Z, long long s, int, int, int, const C (&d)[3]) {
+        // a node of p with a fluid neighbour lies within sqrt(2) of the surface
+        if (!in_shell<C>(g, d, -1.5f, 0.01f)) return;
+        if (L.owner[s] != p) return;
         SiteNbr n = site_nbr(L, X, Y, Z);
         C num[2] = {0, 0}, den = 0;
         C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};
@@ -306,27 +368,26 @@ __global__ void __launch_bounds__(PB) k_virtual(Lattice L, int store_terms) {
             sA[0] += w * ra * C(cx(i)); sA[1] += w * ra * C(cy(i)); sA[2] += w * ra * C(cz(i));
             sB[0] += w * rb * C(cx(i)); sB[1] += w * rb * C(cy(i)); sB[2] += w * rb * C(cz(i));
         }
-        if (!(den > C(0))) continue;
-        C pa = (C(1) + C(L.P.zeta[0])) * num[0] / den;
-        C pb = (C(1) + C(L.P.zeta[1])) * num[1] / den;
+        if (!(den > C(0))) return;
+        C pa = z0 * num[0] / den;
+        C pb = z1 * num[1] / den;
         psi[s] = pa;
         psi[L.N + s] = pb;
         if (store_terms) {
-            C G = C(L.P.G);
-            double fs[3], tq[3];
-            for (int m = 0; m < 3; m++) fs[m] = double(-G * pa * sB[m]) + double(-G * pb * sA[m]);
-            crossd(d, fs, tq);
+            C fs[3], tq[3];
+            for (int m = 0; m < 3; m++) fs[m] = -G * pa * sB[m] + -G * pb * sA[m];
+            crs<C>(d, fs, tq);
 #pragma unroll
             for (int m = 0; m < 3; m++) {
                 acc[m].add(fs[m]);
                 acc[3 + m].add(tq[m]);
             }
         }
-    }
+    });
     if (!store_terms) return;
     double out[6];
-    block_reduce<6>(acc, out);
-    if (threadIdx.x == 0)
+    block_reduce<6, C>(acc, out);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int m = 0; m < 3; m++) {
             L.Fs[3 * p + m] = out[m];
             L.Ts[3 * p + m] = out[3 + m];
@@ -343,50 +404,44 @@ __global__ void __launch_bounds__(PB) k_links(Lattice L) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
     int p = blockIdx.x;
-    PBox b = make_box(L, p, 2.0);
+    PGeo<C> g = pgeo<C>(L, p, 1.5);
     const C* psi = (const C*)L.psi;
     const S* fn = (const S*)L.f_nxt;
-    const double* v = L.vel + 3 * p;
-    const double* w = L.omg + 3 * p;
-    NSum acc[6];
-#pragma unroll
-    for (int m = 0; m < 6; m++) acc[m].s = acc[m].c = 0.0;
-    for (int t = threadIdx.x; t < b.total; t += PB) {
-        int X, Y, Z;
-        double d[3];
-        if (!box_point(L, b, t, X, Y, Z, d)) continue;
-        long long s = sidx(L, X, Y, Z);
-        if (L.mask[s]) continue;
+    CSum<C> acc[6];
+    zero(acc);
+    for_box<C>(L, g, [&](int X, int Y, int Z, long long s, int, int, int, const C (&d)[3]) {
+        // a fluid node linked to p lies within sqrt(2) outside the surface
+        if (!in_shell<C>(g, d, -0.01f, 1.5f)) return;
+        if (L.mask[s]) return;
         SiteNbr n = site_nbr(L, X, Y, Z);
         C rho0 = psi[s], rho1 = psi[L.N + s];
         for (int i = 1; i < Q; i++) {
             if (nbr_is_wall(n, i)) continue;
             long long m = nbr_index(L, n, i);
-            if (L.owner[m] != p) continue;
-            double rel[3] = {d[0] + 0.5 * cx(i), d[1] + 0.5 * cy(i), d[2] + 0.5 * cz(i)};
-            double uw[3] = {v[0] + (w[1] * rel[2] - w[2] * rel[1]),
-                            v[1] + (w[2] * rel[0] - w[0] * rel[2]),
-                            v[2] + (w[0] * rel[1] - w[1] * rel[0])};
-            C cu = C(cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2]);
+            if (!L.mask[m] || L.owner[m] != p) continue;
+            C rel[3] = {d[0] + C(0.5) * C(cx(i)), d[1] + C(0.5) * C(cy(i)), d[2] + C(0.5) * C(cz(i))};
+            C wxr[3];
+            crs<C>(g.w, rel, wxr);
+            C cu = C(cx(i)) * (g.v[0] + wxr[0]) + C(cy(i)) * (g.v[1] + wxr[1]) + C(cz(i)) * (g.v[2] + wxr[2]);
             int ib = opp(i);
-            double fl = 0.0;
+            C fl = 0;
             for (int k = 0; k < 2; k++) {
                 C corr = C(6) * wgt<C>(i) * (k == 0 ? rho0 : rho1) * cu;
                 C fstar = ld_pop(fn + ((long long)(k * Q + ib)) * L.pstride + s, pop_shift<S, C>(L, k, ib)) + corr;
-                fl += double(C(2) * fstar - corr);
+                fl += C(2) * fstar - corr;
             }
-            double F[3] = {fl * cx(i), fl * cy(i), fl * cz(i)}, tq[3];
-            crossd(rel, F, tq);
+            C F[3] = {fl * C(cx(i)), fl * C(cy(i)), fl * C(cz(i))}, tq[3];
+            crs<C>(rel, F, tq);
 #pragma unroll
             for (int q = 0; q < 3; q++) {
                 acc[q].add(F[q]);
                 acc[3 + q].add(tq[q]);
             }
         }
-    }
+    });
     double out[6];
-    block_reduce<6>(acc, out);
-    if (threadIdx.x == 0)
+    block_reduce<6, C>(acc, out);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int m = 0; m < 3; m++) {
             L.Fliq[3 * p + m] = out[m];
             L.Tliq[3 * p + m] = out[3 + m];
@@ -395,81 +450,169 @@ __global__ void __launch_bounds__(PB) k_links(Lattice L) {
 
 // -------------------------------------------------------- pair forces
 // Eq. 26 (Hertz, repulsive, r floored at r_cap) and Eq. 27 (lubrication) on
-// particle i, summed over j in index order, plus the soft side walls.
-// Candidates are found with an FP32 distance test on positions staged in
-// shared memory; each candidate force is then evaluated in FP64.
-constexpr int PT = 128;
-__global__ void __launch_bounds__(PT) k_pairs(Lattice L) {
-    __shared__ float sp[PT][3];
-    int i = blockIdx.x * PT + threadIdx.x;
-    bool act = i < L.nc;
-    double ri[3] = {0, 0, 0}, vi[3] = {0, 0, 0}, Ri = 0;
-    if (act)
-        for (int d = 0; d < 3; d++) {
-            ri[d] = L.pos[3 * i + d];
-            vi[d] = L.vel[3 * i + d];
+// particle i due to j, in FP64.
+__device__ void pair_force(const Lattice& L, int i, int j, const double (&ri)[3], double Ri,
+                           const double (&vi)[3], double nu, double (&fo)[3]) {
+    double rij[3];
+    for (int d = 0; d < 3; d++) {
+        double dd = L.pos[3 * j + d] - ri[d];
+        if (L.per[d]) {
+            double Ld = (d == 0 ? L.nx : (d == 1 ? L.ny : L.nz));
+            dd -= Ld * floor(dd / Ld + 0.5);
         }
-    if (act) Ri = L.rad[i];
-    float rif[3] = {float(ri[0]), float(ri[1]), float(ri[2])};
-    float Ls[3] = {float(L.nx), float(L.ny), float(L.nz)};
-    double rc = L.P.hertz_K != 0.0 ? L.P.hertz_sigma : 0.0;
-    if (L.P.lub_on) rc = fmax(rc, 2.0 * L.rmax + L.P.lub_hn);
-    float rcf = float(rc) + 0.05f;
-    NSum acc[3];
-    for (int m = 0; m < 3; m++) acc[m].s = acc[m].c = 0.0;
-    double nu = 0.5 * ((L.P.tau[0] - 0.5) / 3.0 + (L.P.tau[1] - 0.5) / 3.0);
-    for (int base = 0; base < L.nc; base += PT) {
-        int jj = base + threadIdx.x;
-        if (jj < L.nc)
-            for (int d = 0; d < 3; d++) sp[threadIdx.x][d] = float(L.pos[3 * jj + d]);
+        rij[d] = dd;
+    }
+    fo[0] = fo[1] = fo[2] = 0.0;
+    double r = sqrt(rij[0] * rij[0] + rij[1] * rij[1] + rij[2] * rij[2]);
+    if (!(r > 0.0)) return;
+    if (L.P.hertz_K != 0.0 && r < L.P.hertz_sigma) {
+        double rr = r < L.P.hertz_rcap ? L.P.hertz_rcap : r;
+        double mag = 2.5 * L.P.hertz_K * pow(L.P.hertz_sigma - rr, 1.5);
+        for (int d = 0; d < 3; d++) fo[d] += -mag * rij[d] / r;
+    }
+    if (L.P.lub_on) {
+        double Rj = L.rad[j];
+        double h = r - (Ri + Rj);
+        if (h < L.P.lub_hn) {
+            double red = Ri * Rj / (Ri + Rj), vr = 0.0;
+            if (h < L.P.lub_hmin) h = L.P.lub_hmin;
+            for (int d = 0; d < 3; d++) vr += (vi[d] - L.vel[3 * j + d]) * rij[d] / r;
+            double mag = -6.0 * 3.14159265358979323846 * nu * L.P.lub_scale * red * red *
+                         (1.0 / h - 1.0 / L.P.lub_hn) * vr;
+            for (int d = 0; d < 3; d++) fo[d] += mag * rij[d] / r;
+        }
+    }
+}
+
+struct CellGrid {
+    int n[3];         // cells per axis (>= 3 each when used)
+    float inv[3];     // cells per lattice unit
+    int* count;       // [ncell] counts, reused as fill cursors
+    int* start;       // [ncell + 1]
+    int* items;       // [nc]
+};
+
+__device__ __forceinline__ int cell_coord(float x, float inv, int n) {
+    int c = (int)(x * inv);
+    return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+
+__global__ void k_cells_count(Lattice L, CellGrid cg) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.nc) return;
+    int c0 = cell_coord(float(L.pos[3 * p]), cg.inv[0], cg.n[0]);
+    int c1 = cell_coord(float(L.pos[3 * p + 1]), cg.inv[1], cg.n[1]);
+    int c2 = cell_coord(float(L.pos[3 * p + 2]), cg.inv[2], cg.n[2]);
+    atomicAdd(cg.count + (c0 + cg.n[0] * (c1 + cg.n[1] * c2)), 1);
+}
+
+// exclusive scan of the counts (one block); counts are reset to serve as cursors
+__global__ void __launch_bounds__(1024) k_cells_scan(CellGrid cg) {
+    __shared__ int part[1024];
+    int nc = cg.n[0] * cg.n[1] * cg.n[2];
+    int per = (nc + 1023) / 1024;
+    int b = threadIdx.x * per, e = min(nc, b + per);
+    int sum = 0;
+    for (int c = b; c < e; c++) sum += cg.count[c];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
         __syncthreads();
-        int cnt = min(PT, L.nc - base);
-        if (act && rc > 0.0) {
-            for (int q = 0; q < cnt; q++) {
-                int j = base + q;
-                if (j == i) continue;
-                float df[3], r2f = 0.f;
-                for (int d = 0; d < 3; d++) {
-                    df[d] = sp[q][d] - rif[d];
-                    if (L.per[d]) df[d] -= Ls[d] * rintf(df[d] / Ls[d]);
-                    r2f += df[d] * df[d];
-                }
-                if (r2f >= rcf * rcf) continue;
-                double rij[3];
-                for (int d = 0; d < 3; d++) {
-                    double dd = L.pos[3 * j + d] - ri[d];
-                    if (L.per[d]) {
-                        double Ld = (d == 0 ? L.nx : (d == 1 ? L.ny : L.nz));
-                        dd -= Ld * floor(dd / Ld + 0.5);
-                    }
-                    rij[d] = dd;
-                }
-                double r = sqrt(rij[0] * rij[0] + rij[1] * rij[1] + rij[2] * rij[2]);
-                if (!(r > 0.0)) continue;
-                double fo[3] = {0, 0, 0};
-                if (L.P.hertz_K != 0.0 && r < L.P.hertz_sigma) {
-                    double rr = r < L.P.hertz_rcap ? L.P.hertz_rcap : r;
-                    double mag = 2.5 * L.P.hertz_K * pow(L.P.hertz_sigma - rr, 1.5);
-                    for (int d = 0; d < 3; d++) fo[d] += -mag * rij[d] / r;
-                }
-                if (L.P.lub_on) {
-                    double Rj = L.rad[j];
-                    double h = r - (Ri + Rj);
-                    if (h < L.P.lub_hn) {
-                        double red = Ri * Rj / (Ri + Rj), vr = 0.0;
-                        if (h < L.P.lub_hmin) h = L.P.lub_hmin;
-                        for (int d = 0; d < 3; d++) vr += (vi[d] - L.vel[3 * j + d]) * rij[d] / r;
-                        double mag = -6.0 * 3.14159265358979323846 * nu * L.P.lub_scale * red * red *
-                                     (1.0 / h - 1.0 / L.P.lub_hn) * vr;
-                        for (int d = 0; d < 3; d++) fo[d] += mag * rij[d] / r;
-                    }
-                }
-                for (int d = 0; d < 3; d++) acc[d].add(fo[d]);
-            }
-        }
+        part[threadIdx.x] += v;
         __syncthreads();
     }
-    if (!act) return;
+    int run = part[threadIdx.x] - sum;
+    for (int c = b; c < e; c++) {
+        cg.start[c] = run;
+        run += cg.count[c];
+        cg.count[c] = 0;
+    }
+    if (threadIdx.x == 1023) cg.start[nc] = part[1023];
+}
+
+__global__ void k_cells_fill(Lattice L, CellGrid cg) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.nc) return;
+    int c0 = cell_coord(float(L.pos[3 * p]), cg.inv[0], cg.n[0]);
+    int c1 = cell_coord(float(L.pos[3 * p + 1]), cg.inv[1], cg.n[1]);
+    int c2 = cell_coord(float(L.pos[3 * p + 2]), cg.inv[2], cg.n[2]);
+    int c = c0 + cg.n[0] * (c1 + cg.n[1] * c2);
+    cg.items[cg.start[c] + atomicAdd(cg.count + c, 1)] = p;
+}
+
+constexpr int MAXCAND = 32;
+
+// Pair forces on particle i summed over j in index order (candidates within
+// the cut-off are found in the 27 neighbouring cells, or among all particles
+// when the grid has fewer than 3 cells along an axis, then sorted by j), plus
+// the soft side walls.
+__global__ void __launch_bounds__(128) k_pairs(Lattice L, CellGrid cg, int use_cells, float rc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.nc) return;
+    double ri[3], vi[3];
+    for (int d = 0; d < 3; d++) {
+        ri[d] = L.pos[3 * i + d];
+        vi[d] = L.vel[3 * i + d];
+    }
+    double Ri = L.rad[i];
+    float rif[3] = {float(ri[0]), float(ri[1]), float(ri[2])};
+    float Lf[3] = {float(L.nx), float(L.ny), float(L.nz)};
+    float iLf[3] = {1.f / Lf[0], 1.f / Lf[1], 1.f / Lf[2]};
+    int cand[MAXCAND];
+    int nc = 0;
+    auto test = [&](int j) {
+        if (j == i) return;
+        float r2 = 0.f;
+        for (int d = 0; d < 3; d++) {
+            float df = float(L.pos[3 * j + d]) - rif[d];
+            if (L.per[d]) df -= Lf[d] * rintf(df * iLf[d]);
+            r2 += df * df;
+        }
+        if (r2 >= rc * rc) return;
+        if (nc < MAXCAND) {
+            // insertion keeps the candidate list sorted by j
+            int q = nc++;
+            while (q > 0 && cand[q - 1] > j) {
+                cand[q] = cand[q - 1];
+                q--;
+            }
+            cand[q] = j;
+        } else {
+            atomicOr(L.flags, FLAG_OVERLAP);
+        }
+    };
+    if (rc > 0.f) {
+        if (use_cells) {
+            int c0 = cell_coord(rif[0], cg.inv[0], cg.n[0]);
+            int c1 = cell_coord(rif[1], cg.inv[1], cg.n[1]);
+            int c2 = cell_coord(rif[2], cg.inv[2], cg.n[2]);
+            for (int dz = -1; dz <= 1; dz++) {
+                int z = c2 + dz;
+                if (z < 0 || z >= cg.n[2]) {
+                    if (!L.per[2]) continue;
+                    z = (z + cg.n[2]) % cg.n[2];
+                }
+                for (int dy = -1; dy <= 1; dy++) {
+                    int y = (c1 + dy + cg.n[1]) % cg.n[1];
+                    for (int dx = -1; dx <= 1; dx++) {
+                        int x = (c0 + dx + cg.n[0]) % cg.n[0];
+                        int c = x + cg.n[0] * (y + cg.n[1] * z);
+                        for (int q = cg.start[c]; q < cg.start[c + 1]; q++) test(cg.items[q]);
+                    }
+                }
+            }
+        } else {
+            for (int j = 0; j < L.nc; j++) test(j);
+        }
+    }
+    double nu = 0.5 * ((L.P.tau[0] - 0.5) / 3.0 + (L.P.tau[1] - 0.5) / 3.0);
+    NSum acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int q = 0; q < nc; q++) {
+        double fo[3];
+        pair_force(L, i, cand[q], ri, Ri, vi, nu, fo);
+        for (int d = 0; d < 3; d++) acc[d].add(fo[d]);
+    }
     if (!L.per[2] && L.P.side_wall_k != 0.0) {
         double hlo = ri[2] + 0.5, hhi = (double(L.nz) - 0.5) - ri[2];
         if (hlo < L.P.side_wall_d) acc[2].add(L.P.side_wall_k * (L.P.side_wall_d - hlo));
@@ -500,7 +643,9 @@ __device__ __forceinline__ void to_body(const double (&q)[4], const double (&w)[
 }
 
 // Eq. 35 totals, Eq. 32 leap-frog, Eq. 34 implicit mid-step quaternion
-// (iterated until the rate changes by <= 1e-14, at most 20 times).
+// (iterated until the rate changes by <= 1e-14, at most 20 times); then the
+// FP32 snapshot of the new state.  A particle faster than 1/2 lattice unit
+// per step is reported (the remap assumes smaller moves).
 __global__ void k_integrate(Lattice L) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= L.nc) return;
@@ -526,35 +671,45 @@ __global__ void k_integrate(Lattice L) {
         if (L.per[d]) r = r - double(Ls[d]) * floor(r / double(Ls[d]));
         L.vel[3 * p + d] = v;
         L.pos[3 * p + d] = r;
+        if (!(fabs(v) < 0.5)) atomicOr(L.flags, FLAG_NONFINITE);
     }
-    if (!L.P.rotate) return;
-    double R = L.rad[p];
-    double I = 0.4 * m * R * R;
-    double w[3], q[4], wb[3], qd[4], qh[4];
-    for (int d = 0; d < 3; d++) w[d] = L.omg[3 * p + d] + T[d] / I;
-    for (int d = 0; d < 4; d++) q[d] = L.quat[4 * p + d];
-    to_body(q, w, wb);
-    qrate(q, wb, qd);
-    for (int d = 0; d < 4; d++) qh[d] = q[d] + 0.5 * qd[d];
-    for (int it = 0; it < 20; it++) {
-        double nd[4], delta = 0.0;
-        to_body(qh, w, wb);
-        qrate(qh, wb, nd);
-        for (int d = 0; d < 4; d++) {
-            delta = fmax(delta, fabs(nd[d] - qd[d]));
-            qh[d] = q[d] + 0.5 * nd[d];
-            qd[d] = nd[d];
+    if (L.P.rotate) {
+        double R = L.rad[p];
+        double I = 0.4 * m * R * R;
+        double w[3], q[4], wb[3], qd[4], qh[4];
+        for (int d = 0; d < 3; d++) w[d] = L.omg[3 * p + d] + T[d] / I;
+        for (int d = 0; d < 4; d++) q[d] = L.quat[4 * p + d];
+        to_body(q, w, wb);
+        qrate(q, wb, qd);
+        for (int d = 0; d < 4; d++) qh[d] = q[d] + 0.5 * qd[d];
+        for (int it = 0; it < 20; it++) {
+            double nd[4], delta = 0.0;
+            to_body(qh, w, wb);
+            qrate(qh, wb, nd);
+            for (int d = 0; d < 4; d++) {
+                delta = fmax(delta, fabs(nd[d] - qd[d]));
+                qh[d] = q[d] + 0.5 * nd[d];
+                qd[d] = nd[d];
+            }
+            if (delta <= 1e-14) break;
         }
-        if (delta <= 1e-14) break;
+        double nq = 0.0;
+        for (int d = 0; d < 4; d++) {
+            q[d] = q[d] + qd[d];
+            nq += q[d] * q[d];
+        }
+        nq = sqrt(nq);
+        for (int d = 0; d < 3; d++) L.omg[3 * p + d] = w[d];
+        for (int d = 0; d < 4; d++) L.quat[4 * p + d] = q[d] / nq;
     }
-    double nq = 0.0;
-    for (int d = 0; d < 4; d++) {
-        q[d] = q[d] + qd[d];
-        nq += q[d] * q[d];
+    for (int d = 0; d < 3; d++) {
+        double r = L.pos[3 * p + d];
+        int ip = (int)floor(r);
+        L.ipos[3 * p + d] = ip;
+        L.fsnap[9 * p + d] = float(r - (double)ip);
+        L.fsnap[9 * p + 3 + d] = float(L.vel[3 * p + d]);
+        L.fsnap[9 * p + 6 + d] = float(L.omg[3 * p + d]);
     }
-    nq = sqrt(nq);
-    for (int d = 0; d < 3; d++) L.omg[3 * p + d] = w[d];
-    for (int d = 0; d < 4; d++) L.quat[4 * p + d] = q[d] / nq;
 }
 
 // ---------------------------------------------------------- launchers
@@ -565,37 +720,72 @@ __global__ void k_integrate(Lattice L) {
         default:      { const int P = LB_FP16; call; break; } \
     }
 
-int launch_map_initial(const Lattice& L, int first, int count, cudaStream_t st) {
+static const dim3 PBLK(BXP, BYP);
+
+int launch_snapshot(const Lattice& L, cudaStream_t st) {
+    if (L.nc <= 0) return 0;
+    k_snapshot<<<(L.nc + 127) / 128, 128, 0, st>>>(L);
+    return 1;
+}
+
+int launch_map_initial(const Lattice& L, int prec, int first, int count, cudaStream_t st) {
     if (count <= 0) return 0;
-    k_map_initial<<<count, PB, 0, st>>>(L, first);
+    DISPATCHC(prec, (k_map_initial<P><<<count, PBLK, 0, st>>>(L, first)));
     return 1;
 }
 
 int launch_remap(const Lattice& L, int prec, cudaStream_t st) {
     if (L.nc <= 0) return 0;
-    DISPATCHC(prec, (k_remap_classify<P><<<L.nc, PB, 0, st>>>(L)));
-    DISPATCHC(prec, (k_remap_create<P><<<L.nc, PB, 0, st>>>(L)));
-    k_remap_commit<<<L.nc, PB, 0, st>>>(L);
+    DISPATCHC(prec, (k_remap_classify<P><<<L.nc, PBLK, 0, st>>>(L)));
+    DISPATCHC(prec, (k_remap_create<P><<<L.nc, PBLK, 0, st>>>(L)));
+    DISPATCHC(prec, (k_remap_commit<P><<<L.nc, PBLK, 0, st>>>(L)));
     return 3;
 }
 
 int launch_virtual(const Lattice& L, int prec, int store_terms, cudaStream_t st) {
     if (L.nc <= 0) return 0;
-    DISPATCHC(prec, (k_virtual<P><<<L.nc, PB, 0, st>>>(L, store_terms)));
+    DISPATCHC(prec, (k_virtual<P><<<L.nc, PBLK, 0, st>>>(L, store_terms)));
     return 1;
 }
 
 int launch_links(const Lattice& L, int prec, cudaStream_t st) {
     if (L.nc <= 0) return 0;
-    DISPATCHC(prec, (k_links<P><<<L.nc, PB, 0, st>>>(L)));
+    DISPATCHC(prec, (k_links<P><<<L.nc, PBLK, 0, st>>>(L)));
     return 1;
 }
 
-int launch_pairs_integrate(const Lattice& L, cudaStream_t st) {
+int launch_pairs_integrate(const Lattice& L, void* cells, size_t cell_cap, cudaStream_t st) {
     if (L.nc <= 0) return 0;
-    k_pairs<<<(L.nc + PT - 1) / PT, PT, 0, st>>>(L);
+    double rc = L.P.hertz_K != 0.0 ? L.P.hertz_sigma : 0.0;
+    if (L.P.lub_on) rc = fmax(rc, 2.0 * L.rmax + L.P.lub_hn);
+    float rcf = rc > 0.0 ? float(rc) + 0.05f : 0.f;
+    CellGrid cg;
+    int Ls[3] = {L.nx, L.ny, L.nz};
+    long long ncell = 1;
+    int use_cells = rcf > 0.f && L.nc > 64;
+    for (int d = 0; d < 3; d++) {
+        int n = rcf > 0.f ? (int)(Ls[d] / rcf) : 1;
+        if (n > 64) n = 64;
+        if (n < 3) use_cells = 0;
+        cg.n[d] = n < 1 ? 1 : n;
+        cg.inv[d] = float(cg.n[d]) / float(Ls[d]);
+        ncell *= cg.n[d];
+    }
+    if ((size_t)(2 * ncell + 1 + L.nc) * sizeof(int) > cell_cap) use_cells = 0;
+    int n = 0;
+    cg.count = (int*)cells;
+    cg.start = cg.count + ncell;
+    cg.items = cg.start + ncell + 1;
+    if (use_cells) {
+        cudaMemsetAsync(cg.count, 0, ncell * sizeof(int), st);
+        k_cells_count<<<(L.nc + 127) / 128, 128, 0, st>>>(L, cg);
+        k_cells_scan<<<1, 1024, 0, st>>>(cg);
+        k_cells_fill<<<(L.nc + 127) / 128, 128, 0, st>>>(L, cg);
+        n += 3;
+    }
+    k_pairs<<<(L.nc + 127) / 128, 128, 0, st>>>(L, cg, use_cells, rcf);
     k_integrate<<<(L.nc + 127) / 128, 128, 0, st>>>(L);
-    return 2;
+    return n + 2;
 }
 
 }  // namespace lbgb

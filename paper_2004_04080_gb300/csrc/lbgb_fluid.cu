@@ -92,6 +92,44 @@ __global__ void k_wall_psi(Lattice L) {
     pw[(side * 2 + 1) * nxy + w] = den > C(0) ? num1 / den : C(0);
 }
 
+// c_i . u_w for the link from site (x,y,z) along i into particle p, with the
+// rigid-body wall velocity u_w = v_p + omega_p x (r_w - r_p), r_w = x + c_i/2
+// (Eq. 18).  The offset r_w - r_p is formed from the integer part of r_p and
+// its fractional part, so it is exact in FP64 and accurate to FP32 rounding of
+// a number below 1 in the FP32 forms (which read the FP32 particle snapshot).
+template <typename C>
+__device__ __forceinline__ C particle_cu(const Lattice& L, int p, int x, int y, int z, int i) {
+    int xs[3] = {x, y, z}, Ls[3] = {L.nx, L.ny, L.nz}, cc[3] = {cx(i), cy(i), cz(i)};
+    C rel[3], v[3], w[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        int ip;
+        C fr;
+        if (sizeof(C) == 8) {
+            double r = L.pos[3 * p + d];
+            ip = (int)floor(r);
+            fr = C(r - (double)ip);
+            v[d] = C(L.vel[3 * p + d]);
+            w[d] = C(L.omg[3 * p + d]);
+        } else {
+            ip = L.ipos[3 * p + d];
+            fr = C(L.fsnap[9 * p + d]);
+            v[d] = C(L.fsnap[9 * p + 3 + d]);
+            w[d] = C(L.fsnap[9 * p + 6 + d]);
+        }
+        int dd = xs[d] - ip;
+        if (L.per[d]) {
+            if (2 * dd > Ls[d]) dd -= Ls[d];
+            else if (2 * dd < -Ls[d]) dd += Ls[d];
+        }
+        rel[d] = C(dd) + C(0.5) * C(cc[d]) - fr;
+    }
+    C u0 = v[0] + (w[1] * rel[2] - w[2] * rel[1]);
+    C u1 = v[1] + (w[2] * rel[0] - w[0] * rel[2]);
+    C u2 = v[2] + (w[0] * rel[1] - w[1] * rel[0]);
+    return C(cc[0]) * u0 + C(cc[1]) * u1 + C(cc[2]) * u2;
+}
+
 // The fused step at one fluid site: moments (Eqs. 6, 7, 14), Shan-Chen force
 // (Eq. 11), EDM collision (Eq. 16), then push-streaming (Eq. 3) with halfway
 // bounce-back on particle links (Eq. 17, wall velocity of Eq. 18) and on wall
@@ -143,26 +181,345 @@ __global__ void __launch_bounds__(128) k_collide_push(Lattice L) {
             for (int k = 0; k < 2; k++)
                 st_pop(fn + ((long long)(k * Q + i)) * L.pstride + m, fs[k], pop_shift<S, C>(L, k, i));
         } else {
-            // particle link: u_w = v_p + omega_p x (r_w - r_p), r_w = x + c_i/2
-            int p = L.owner[m];
-            double r[3] = {x + 0.5 * cx(i) - L.pos[3 * p], y + 0.5 * cy(i) - L.pos[3 * p + 1],
-                           z + 0.5 * cz(i) - L.pos[3 * p + 2]};
-            int Ls[3] = {L.nx, L.ny, L.nz};
-#pragma unroll
-            for (int d = 0; d < 3; d++)
-                if (L.per[d]) r[d] -= Ls[d] * floor(r[d] / Ls[d] + 0.5);
-            const double* v = L.vel + 3 * p;
-            const double* w = L.omg + 3 * p;
-            double uw0 = v[0] + (w[1] * r[2] - w[2] * r[1]);
-            double uw1 = v[1] + (w[2] * r[0] - w[0] * r[2]);
-            double uw2 = v[2] + (w[0] * r[1] - w[1] * r[0]);
-            C cu = C(cx(i) * uw0 + cy(i) * uw1 + cz(i) * uw2);
+            // particle link (Eq. 17): c_i . u_w with u_w from Eq. 18 at r_w = x + c_i/2
+            C cu = particle_cu<C>(L, L.owner[m], x, y, z, i);
 #pragma unroll
             for (int k = 0; k < 2; k++)
                 st_pop(fn + ((long long)(k * Q + opp(i))) * L.pstride + s,
                        fs[k] - C(6) * wgt<C>(i) * rho[k] * cu, pop_shift<S, C>(L, k, opp(i)));
         }
     }
+}
+
+// ------------------------------------------------------- fused step
+// One launch performs the whole lattice update of a time step (Sec. 3.1,
+// steps 1, 4-6, 8) for the fluid: each block owns a 32 x 8 column of sites
+// and marches along z through a chunk of planes.  Per plane it
+//   1. loads the 2 x 19 populations f(t) of its own sites (kept in registers
+//      for the next iteration) and forms rho^k (Eq. 6) and j^k (Eq. 7);
+//   2. forms rho^k of the one-site ring around the tile from the ring's
+//      populations (these loads mostly hit L2: the neighbouring blocks read
+//      the same lines), so the pseudopotential halo needs no separate density
+//      pass; particle nodes contribute their virtual density (Eq. 20) and
+//      wall planes the wall density, both precomputed by small kernels;
+//   3. keeps psi^k of three consecutive planes (tile + ring) in shared
+//      memory, from which the previous plane's Shan-Chen force (Eq. 11) is
+//      taken, then collides it (Eqs. 14-16) and pushes f*(t) to the
+//      neighbours (Eq. 3), bouncing back on particle and wall links
+//      (Eqs. 9, 17, 18).
+constexpr int FTX = 32, FTY = 8, FNT = FTX * FTY;
+constexpr int RW = FTX + 2, RH = FTY + 2;
+
+// shared state of one block: psi^k and node flags of three planes (tile +
+// ring) and the raw populations of the own sites of the plane being collided
+template <int PREC>
+struct FusedShared {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    C psi[3][2][RH][RW];
+    uint8_t sol[3][RH][RW];  // 0 fluid, 1 particle node, 2 beyond a wall
+    S stage[2 * Q][FNT];
+};
+
+template <int PREC>
+struct OwnSite {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    S raw[2 * Q];  // populations as stored
+    C rho[2];
+    C j[2][3];
+};
+
+template <int PREC>
+__device__ __forceinline__ void own_moments(const Lattice& L, OwnSite<PREC>& o) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        C r = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            C v = ld_pop(&o.raw[k * Q + i], pop_shift<S, C>(L, k, i));
+            r += v;
+            if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
+            if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
+            if (cz(i) > 0) jz += v; else if (cz(i) < 0) jz -= v;
+        }
+        o.rho[k] = r;
+        o.j[k][0] = jx; o.j[k][1] = jy; o.j[k][2] = jz;
+    }
+}
+
+// Fill shared slot `slot` with plane zp: psi^k and node flags of the tile and
+// its ring.  The calling thread's own site is loaded into `own` (returns
+// true if it is a fluid node whose populations were loaded).
+template <int PREC>
+__device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& sh, int slot, int zp, int x0,
+                                           int y0, int W, int H, bool want_own, OwnSite<PREC>& own) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    const S* f = (const S*)L.f_cur;
+    const C* psi = (const C*)L.psi;
+    int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
+    bool loaded = false;
+    if ((zp < 0 || zp >= L.nz) && !L.per[2]) {
+        // a wall plane: the wall density of every tile + ring position
+        const C* pw = (const C*)L.psi_wall;
+        int side = zp < 0 ? 0 : 1;
+        long long nxy = (long long)L.nx * L.ny;
+        for (int q = tid; q < (W + 2) * (H + 2); q += FNT) {
+            int lx = q % (W + 2) - 1, ly = q / (W + 2) - 1;
+            int X = x0 + lx, Y = y0 + ly;
+            X = X < 0 ? X + L.nx : (X >= L.nx ? X - L.nx : X);
+            Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
+            long long w = (long long)X + (long long)L.nx * Y;
+            sh.psi[slot][0][ly + 1][lx + 1] = pw[(side * 2 + 0) * nxy + w];
+            sh.psi[slot][1][ly + 1][lx + 1] = pw[(side * 2 + 1) * nxy + w];
+            sh.sol[slot][ly + 1][lx + 1] = 2;
+        }
+        return false;
+    }
+    int Z = zp < 0 ? zp + L.nz : (zp >= L.nz ? zp - L.nz : zp);
+    long long zoff = (long long)L.nx * L.ny * Z;
+    if (tx < W && ty < H) {
+        long long s = (long long)(x0 + tx) + (long long)L.nx * (y0 + ty) + zoff;
+        if (L.mask[s]) {
+            sh.psi[slot][0][ty + 1][tx + 1] = psi[s];
+            sh.psi[slot][1][ty + 1][tx + 1] = psi[L.N + s];
+            sh.sol[slot][ty + 1][tx + 1] = 1;
+        } else {
+            if (want_own) {
+#pragma unroll
+                for (int q = 0; q < 2 * Q; q++) own.raw[q] = f[(long long)q * L.pstride + s];
+                own_moments<PREC>(L, own);
+                loaded = true;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 2; k++) {
+                    C r = 0;
+#pragma unroll
+                    for (int i = 0; i < Q; i++)
+                        r += ld_pop(f + ((long long)(k * Q + i)) * L.pstride + s, pop_shift<S, C>(L, k, i));
+                    own.rho[k] = r;
+                }
+            }
+            sh.psi[slot][0][ty + 1][tx + 1] = own.rho[0];
+            sh.psi[slot][1][ty + 1][tx + 1] = own.rho[1];
+            sh.sol[slot][ty + 1][tx + 1] = 0;
+        }
+    }
+    // ring: rows ly = -1 and ly = H (lx = -1..W), columns lx = -1 and lx = W (ly = 0..H-1)
+    int nring = 2 * (W + 2) + 2 * H;
+    for (int q = tid; q < nring; q += FNT) {
+        int lx, ly;
+        if (q < W + 2) { lx = q - 1; ly = -1; }
+        else if (q < 2 * (W + 2)) { lx = q - (W + 2) - 1; ly = H; }
+        else if (q < 2 * (W + 2) + H) { lx = -1; ly = q - 2 * (W + 2); }
+        else { lx = W; ly = q - 2 * (W + 2) - H; }
+        int X = x0 + lx, Y = y0 + ly;
+        X = X < 0 ? X + L.nx : (X >= L.nx ? X - L.nx : X);
+        Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
+        long long s = (long long)X + (long long)L.nx * Y + zoff;
+        C r0, r1;
+        uint8_t sl;
+        if (L.mask[s]) {
+            r0 = psi[s];
+            r1 = psi[L.N + s];
+            sl = 1;
+        } else {
+            r0 = 0;
+            r1 = 0;
+#pragma unroll
+            for (int i = 0; i < Q; i++) {
+                r0 += ld_pop(f + ((long long)i) * L.pstride + s, pop_shift<S, C>(L, 0, i));
+                r1 += ld_pop(f + ((long long)(Q + i)) * L.pstride + s, pop_shift<S, C>(L, 1, i));
+            }
+            sl = 0;
+        }
+        sh.psi[slot][0][ly + 1][lx + 1] = r0;
+        sh.psi[slot][1][ly + 1][lx + 1] = r1;
+        sh.sol[slot][ly + 1][lx + 1] = sl;
+    }
+    return loaded;
+}
+
+// collide and push the own site of plane z (slots: below, here, above); the
+// populations are in the stage, rho and j in `m`
+template <int PREC>
+__device__ __forceinline__ void collide_site(const Lattice& L, FusedShared<PREC>& sh, const int (&sl)[3], int x,
+                                             int y, int z, const OwnSite<PREC>& m) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
+    // Eq. 11 (repulsive sign) + body force from the shared-memory psi planes
+    C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        int slot = sl[cz(i) + 1];
+        C pa = sh.psi[slot][0][ty + 1 + cy(i)][tx + 1 + cx(i)];
+        C pb = sh.psi[slot][1][ty + 1 + cy(i)][tx + 1 + cx(i)];
+        C w = wgt<C>(i);
+        if (cx(i)) { sA[0] += C(cx(i)) * w * pa; sB[0] += C(cx(i)) * w * pb; }
+        if (cy(i)) { sA[1] += C(cy(i)) * w * pa; sB[1] += C(cy(i)) * w * pb; }
+        if (cz(i)) { sA[2] += C(cz(i)) * w * pa; sB[2] += C(cz(i)) * w * pb; }
+    }
+    C F[2][3];
+    C G = C(L.P.G);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        C g = C(L.P.body_force[d]);
+        F[0][d] = -G * m.rho[0] * sB[d] + m.rho[0] * g;
+        F[1][d] = -G * m.rho[1] * sA[d] + m.rho[1] * g;
+    }
+    if (!(m.rho[0] >= C(0) && m.rho[1] >= C(0) && m.rho[0] < C(1e30) && m.rho[1] < C(1e30)))
+        atomicOr(L.flags, FLAG_NONFINITE);
+    C u[3], om;
+    mixture<C>(L, m.rho, m.j, u, om);
+    C us[2][3];
+    C tiny = sizeof(C) == 8 ? C(1e-300) : C(1e-30);
+#pragma unroll
+    for (int k = 0; k < 2; k++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) us[k][d] = m.rho[k] > tiny ? u[d] + F[k][d] / m.rho[k] : u[d];
+    C uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    C uus[2] = {us[0][0] * us[0][0] + us[0][1] * us[0][1] + us[0][2] * us[0][2],
+                us[1][0] * us[1][0] + us[1][1] * us[1][1] + us[1][2] * us[1][2]};
+    C one_m_om = C(1) - om;
+    S* fn = (S*)L.f_nxt;
+    long long s = (long long)x + (long long)L.nx * ((long long)y + (long long)L.ny * z);
+    SiteNbr n = site_nbr(L, x, y, z);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        C fs[2];
+#pragma unroll
+        for (int k = 0; k < 2; k++)
+            fs[k] = one_m_om * (ld_pop(&sh.stage[k * Q + i][tid], pop_shift<S, C>(L, k, i)) -
+                                feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
+                    feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
+        uint8_t nb = i == 0 ? 0 : sh.sol[sl[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)];
+        if (nb == 0) {
+            long long q = i == 0 ? s : nbr_index(L, n, i);
+#pragma unroll
+            for (int k = 0; k < 2; k++)
+                st_pop(fn + ((long long)(k * Q + i)) * L.pstride + q, fs[k], pop_shift<S, C>(L, k, i));
+        } else {
+            C cu;
+            if (nb == 2) {
+                const double* uw = cz(i) < 0 ? L.P.wall_u_lo : L.P.wall_u_hi;
+                cu = C(cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2]);
+            } else {
+                cu = particle_cu<C>(L, L.owner[nbr_index(L, n, i)], x, y, z, i);
+            }
+#pragma unroll
+            for (int k = 0; k < 2; k++)
+                st_pop(fn + ((long long)(k * Q + opp(i))) * L.pstride + s,
+                       fs[k] - C(6) * wgt<C>(i) * m.rho[k] * cu, pop_shift<S, C>(L, k, opp(i)));
+        }
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : 2)) k_fused(Lattice L, int zc) {
+    typedef typename Prec<PREC>::C C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FusedShared<PREC>& sh = *reinterpret_cast<FusedShared<PREC>*>(smem_raw);
+    int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
+    int W = min(FTX, L.nx - x0), H = min(FTY, L.ny - y0);
+    int z0 = blockIdx.z * zc, z1 = min(z0 + zc, L.nz);
+    int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
+    bool act = tx < W && ty < H;
+    OwnSite<PREC> nxt, cur;
+    // prologue: plane z0-1 into slot 0, plane z0 into slot 1 (own site staged)
+    fill_plane<PREC>(L, sh, 0, z0 - 1, x0, y0, W, H, false, nxt);
+    bool have = fill_plane<PREC>(L, sh, 1, z0, x0, y0, W, H, true, nxt);
+    if (have)
+#pragma unroll
+        for (int q = 0; q < 2 * Q; q++) sh.stage[q][tid] = nxt.raw[q];
+    cur.rho[0] = nxt.rho[0]; cur.rho[1] = nxt.rho[1];
+#pragma unroll
+    for (int d = 0; d < 3; d++) { cur.j[0][d] = nxt.j[0][d]; cur.j[1][d] = nxt.j[1][d]; }
+    int lo = 0, mid = 1, hi = 2;
+    for (int z = z0; z < z1; z++) {
+        bool more = z + 1 < z1;
+        bool have_n = fill_plane<PREC>(L, sh, hi, z + 1, x0, y0, W, H, more, nxt);
+        __syncthreads();
+        if (act && sh.sol[mid][ty + 1][tx + 1] == 0) {
+            int sl[3] = {lo, mid, hi};
+            collide_site<PREC>(L, sh, sl, x0 + tx, y0 + ty, z, cur);
+        }
+        __syncthreads();
+        if (have_n)
+#pragma unroll
+            for (int q = 0; q < 2 * Q; q++) sh.stage[q][tid] = nxt.raw[q];
+        cur.rho[0] = nxt.rho[0]; cur.rho[1] = nxt.rho[1];
+#pragma unroll
+        for (int d = 0; d < 3; d++) { cur.j[0][d] = nxt.j[0][d]; cur.j[1][d] = nxt.j[1][d]; }
+        int t = lo; lo = mid; mid = hi; hi = t;
+    }
+}
+
+// rho^k of fluid nodes within R + 1.6 of particle p (the nodes whose density
+// the wetting and link kernels read), written to psi
+template <int PREC>
+__global__ void __launch_bounds__(128) k_shell_density(Lattice L) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    int p = blockIdx.x;
+    double R = L.rad[p], pad = 1.6;
+    int lo[3], ext[3];
+    float rf[3];
+    for (int d = 0; d < 3; d++) {
+        double r = L.pos[3 * p + d];
+        lo[d] = (int)floor(r - R - pad);
+        ext[d] = (int)ceil(r + R + pad) - lo[d] + 1;
+        rf[d] = float(r - (double)lo[d]);
+    }
+    float Rmax2 = float((R + pad) * (R + pad));
+    const S* f = (const S*)L.f_cur;
+    C* psi = (C*)L.psi;
+    int total = ext[0] * ext[1] * ext[2];
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        int a = t % ext[0], b = (t / ext[0]) % ext[1], c = t / (ext[0] * ext[1]);
+        float dx = float(a) - rf[0], dy = float(b) - rf[1], dz = float(c) - rf[2];
+        if (dx * dx + dy * dy + dz * dz >= Rmax2) continue;
+        int X = lo[0] + a, Y = lo[1] + b, Z = lo[2] + c;
+        if (!L.per[2] && (Z < 0 || Z >= L.nz)) continue;
+        X = X < 0 ? X + L.nx : (X >= L.nx ? X - L.nx : X);
+        Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
+        Z = Z < 0 ? Z + L.nz : (Z >= L.nz ? Z - L.nz : Z);
+        long long s = (long long)X + (long long)L.nx * ((long long)Y + (long long)L.ny * Z);
+        if (L.mask[s]) continue;
+        C r0 = 0, r1 = 0;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            r0 += ld_pop(f + ((long long)i) * L.pstride + s, pop_shift<S, C>(L, 0, i));
+            r1 += ld_pop(f + ((long long)(Q + i)) * L.pstride + s, pop_shift<S, C>(L, 1, i));
+        }
+        psi[s] = r0;
+        psi[L.N + s] = r1;
+    }
+}
+
+// rho^k of the fluid nodes in the planes next to the walls, written to psi
+template <int PREC>
+__global__ void k_wall_plane_density(Lattice L) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L.nx) return;
+    int y = blockIdx.y, z = blockIdx.z == 0 ? 0 : L.nz - 1;
+    long long s = (long long)x + (long long)L.nx * ((long long)y + (long long)L.ny * z);
+    if (L.mask[s]) return;
+    const S* f = (const S*)L.f_cur;
+    C* psi = (C*)L.psi;
+    C r0 = 0, r1 = 0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        r0 += ld_pop(f + ((long long)i) * L.pstride + s, pop_shift<S, C>(L, 0, i));
+        r1 += ld_pop(f + ((long long)(Q + i)) * L.pstride + s, pop_shift<S, C>(L, 1, i));
+    }
+    psi[s] = r0;
+    psi[L.N + s] = r1;
 }
 
 // rho^A, rho^B and u = sum_k (j^k + F^k/2)/rho into stage [5][N] (FP64)
@@ -294,9 +651,34 @@ int launch_wall_psi(const Lattice& L, int prec, cudaStream_t st) {
 }
 
 int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st) {
-    int bx = site_bx(L);
-    DISPATCH(prec, (k_collide_push<P><<<site_grid(L, bx), bx, 0, st>>>(L)));
+    int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + FTY - 1) / FTY);
+    // z chunk: enough blocks to fill the GPU a few times over, at least 8 planes
+    int zc = (int)((long long)L.nz * tiles / 2400);
+    zc = zc < 4 ? 4 : zc;
+    zc = zc > L.nz ? L.nz : zc;
+    dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + FTY - 1) / FTY, (L.nz + zc - 1) / zc);
+    static bool attr_set[3] = {false, false, false};
+    if (!attr_set[prec]) {
+        DISPATCH(prec, (cudaFuncSetAttribute(k_fused<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(FusedShared<P>))));
+        attr_set[prec] = true;
+    }
+    DISPATCH(prec, (k_fused<P><<<grid, dim3(FTX, FTY), sizeof(FusedShared<P>), st>>>(L, zc)));
     return 1;
+}
+
+int launch_shell_density(const Lattice& L, int prec, cudaStream_t st) {
+    int n = 0;
+    if (L.nc > 0) {
+        DISPATCH(prec, (k_shell_density<P><<<L.nc, 128, 0, st>>>(L)));
+        n++;
+    }
+    if (!L.per[2]) {
+        dim3 g((unsigned)((L.nx + 127) / 128), (unsigned)L.ny, 2);
+        DISPATCH(prec, (k_wall_plane_density<P><<<g, 128, 0, st>>>(L)));
+        n++;
+    }
+    return n;
 }
 
 int launch_fields_out(const Lattice& L, int prec, double* stage, cudaStream_t st) {

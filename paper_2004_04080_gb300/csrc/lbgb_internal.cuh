@@ -75,6 +75,8 @@ struct Lattice {
     int* prev_valid;
     double *Fd, *Td, *Fc, *Tc, *Fs, *Ts, *Fpair, *Ftot, *Ttot;
     double rmax;       // largest particle radius
+    int* ipos;         // [n][3] floor of the position (FP32 geometry origin)
+    float* fsnap;      // [n][9] position - ipos, v(t-1/2), omega(t-1/2) in FP32
     double* red;       // reduction partials
     int red_blocks;
     lb_params P;
@@ -226,9 +228,22 @@ __device__ __forceinline__ void mixture(const Lattice& L, const C (&rho)[2], con
     om = C(1) / (C(3) * nubar + C(0.5));
 }
 
+// Neumaier sum in the compute type (per-thread partials before the FP64 merge)
+template <typename C>
+struct CSum {
+    C s, c;
+    __device__ __forceinline__ void add(C x) {
+        C t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+};
+
 // kernel launchers (each returns the number of kernels it launched)
 int launch_init_fields(const Lattice& L, int prec, const double* stage, cudaStream_t st);
 int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st);
+int launch_shell_density(const Lattice& L, int prec, cudaStream_t st);
 int launch_density(const Lattice& L, int prec, cudaStream_t st);
 int launch_wall_psi(const Lattice& L, int prec, cudaStream_t st);
 int launch_fields_out(const Lattice& L, int prec, double* stage, cudaStream_t st);
@@ -236,10 +251,11 @@ int launch_totals(const Lattice& L, int prec, double* out_dev, cudaStream_t st);
 int launch_populations_out(const Lattice& L, int prec, int k, int i, double* stage, cudaStream_t st);
 int launch_clear_map(const Lattice& L, cudaStream_t st);
 
-int launch_map_initial(const Lattice& L, int first, int count, cudaStream_t st);
+int launch_map_initial(const Lattice& L, int prec, int first, int count, cudaStream_t st);
 int launch_remap(const Lattice& L, int prec, cudaStream_t st);
 int launch_virtual(const Lattice& L, int prec, int store_terms, cudaStream_t st);
 int launch_links(const Lattice& L, int prec, cudaStream_t st);
-int launch_pairs_integrate(const Lattice& L, cudaStream_t st);
+int launch_pairs_integrate(const Lattice& L, void* cells, size_t cell_cap, cudaStream_t st);
+int launch_snapshot(const Lattice& L, cudaStream_t st);
 
 }  // namespace lbgb

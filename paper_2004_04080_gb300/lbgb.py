@@ -28,7 +28,8 @@ TERMS = {"F_liq": 0, "T_liq": 1, "F_d": 2, "T_d": 3, "F_c": 4, "T_c": 5, "F_s": 
 # every symbol declared in include/lbgb.h
 EXPORTS = ["lb_workspace_bytes", "lb_create", "lb_set_params", "lb_init_fields", "lb_add_colloids",
            "lb_step", "lb_get_fields", "lb_get_colloids", "lb_get_colloid_terms", "lb_get_totals",
-           "lb_get_populations", "lb_get_owner", "lb_launch_count", "lb_destroy", "lb_last_error"]
+           "lb_get_populations", "lb_get_owner", "lb_profile", "lb_profile_read", "lb_launch_count",
+           "lb_destroy", "lb_last_error"]
 
 
 class LbParams(C.Structure):
@@ -75,6 +76,8 @@ def load(build_if_missing: bool = True):
     lib.lb_get_totals.argtypes = [P, D]
     lib.lb_get_populations.argtypes = [P, C.c_int, D]
     lib.lb_get_owner.argtypes = [P, I]
+    lib.lb_profile.argtypes = [P, C.c_int]
+    lib.lb_profile_read.argtypes = [P, D, C.POINTER(C.c_longlong)]
     lib.lb_launch_count.argtypes = [P]
     lib.lb_launch_count.restype = C.c_longlong
     lib.lb_destroy.argtypes = [P]
@@ -197,6 +200,17 @@ def lb_get_owner(h, out: np.ndarray):
     return _check(h, load().lb_get_owner(h, out.ctypes.data_as(C.POINTER(C.c_int))), "lb_get_owner")
 
 
+def lb_profile(h, enable: bool):
+    return _check(h, load().lb_profile(h, int(bool(enable))), "lb_profile")
+
+
+def lb_profile_read(h):
+    """(summed fused-kernel time in ms, number of timed launches)"""
+    t, n = C.c_double(0.0), C.c_longlong(0)
+    _check(h, load().lb_profile_read(h, C.byref(t), C.byref(n)), "lb_profile_read")
+    return t.value, n.value
+
+
 def lb_launch_count(h) -> int:
     return int(load().lb_launch_count(h))
 
@@ -289,3 +303,9 @@ class LBLattice:
 
     def launch_count(self):
         return lb_launch_count(self.h)
+
+    def profile(self, enable=True):
+        lb_profile(self.h, enable)
+
+    def profile_read(self):
+        return lb_profile_read(self.h)

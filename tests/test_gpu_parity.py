@@ -1,8 +1,19 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances: FP64 storage 1e-12 relative (max-norm over the field, the state
-after 100 steps); FP32 1e-5; FP16 deviation storage 1e-3.  Boxes are chosen to
-span several thread blocks and ragged tails (nx a multiple of 4, odd ny, nz).
+Every quantity is compared on its natural lattice scale, at the bound that
+the storage form states: 1e-12 for FP64, 1e-5 for FP32, 1e-3 for FP16
+deviation storage.
+  * densities: relative to max |rho| (rho is O(1));
+  * fluid velocity: relative to max(|u|_max, c = 1 lattice speed); in the
+    bijel workloads the mixture relaxes to |u| ~ 1e-8, where a comparison
+    relative to |u| itself only measures rounding of j = sum_i f_i c_i
+    (sum_i |f_i| / |j| ~ 1e7), so the lattice speed is the scale there; the
+    sheared-wall cases (|u| ~ 0.05) test the velocity relative to itself;
+  * particle position (lattice spacing), velocity and angular velocity
+    (lattice speed), orientation (unit quaternion) and force / torque terms
+    (lattice momentum per step): absolute in those units.
+Boxes span several thread blocks with ragged tails (nx a multiple of 4, odd
+ny and nz).
 """
 import math
 
@@ -38,31 +49,29 @@ def run_both(shape, params, steps, prec="fp64", colloids=None, dens=None, u=None
     return g, o
 
 
-def rel(x, y):
-    den = max(np.abs(y).max(), 1e-300)
+def rel(x, y, floor=0.0):
+    den = max(np.abs(y).max(), floor, 1e-300)
     return np.abs(x - y).max() / den
 
 
-def compare_fields(g, o, tol, tol_u=None):
+def compare_fields(g, o, tol, u_scale=1.0):
     ga, gb, gu = g.get_fields()
     ra, rb, ru = o.get_fields()
     assert np.array_equal(g.owner(), o.owner())
-    ea, eb, eu = rel(ga, ra), rel(gb, rb), rel(gu, ru)
+    ea, eb, eu = rel(ga, ra), rel(gb, rb), rel(gu, ru, floor=u_scale)
     assert ea < tol and eb < tol, (ea, eb)
-    assert eu < (tol_u or tol), eu
+    assert eu < tol, eu
     return ea, eb, eu
 
 
 def compare_colloids(g, o, tol):
     gc, rc = g.get_colloids(), o.get_colloids()
     for key in ("pos", "vel", "omega", "quat"):
-        scale = {"pos": 1.0}.get(key, max(np.abs(rc[key]).max(), 1e-300))
-        err = np.abs(gc[key] - rc[key]).max() / scale
+        err = np.abs(gc[key] - rc[key]).max()
         assert err < tol, (key, err)
-    for term in ("F_liq", "T_liq", "F_s", "F_d", "F_c", "F_pair", "F_total"):
-        gt, rt = g.term(term), o.term(term)
-        scale = max(np.abs(rt).max(), 1e-12)
-        assert np.abs(gt - rt).max() / scale < max(tol, 1e-10), term
+    for term in ("F_liq", "T_liq", "F_s", "T_s", "F_d", "F_c", "F_pair", "F_total", "T_total"):
+        err = np.abs(g.term(term) - o.term(term)).max()
+        assert err < tol, (term, err)
 
 
 def test_fp64_small_workload_100_steps():
@@ -105,28 +114,31 @@ def test_fp64_fluid_only_populations_exact():
         assert rel(g.populations(k), o.populations(k)) < 1e-13
 
 
-def test_fp32_small_workload():
-    """FP32 storage and arithmetic vs the FP64 oracle: 1e-5 on rho and u
-    after 100 steps."""
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 1e-3)])
+def test_reduced_precision_small_workload(prec, tol):
+    """FP32 storage, and FP16 deviation storage with FP32 arithmetic, vs the
+    FP64 oracle on the 32^3 bijel workload after 100 steps."""
     w = workload("small_fp64")
-    g, o = run_both(w.shape, w.params, w.steps, "fp32", w.colloids(), w.densities())
-    ga, gb, gu = g.get_fields()
-    ra, rb, ru = o.get_fields()
-    assert rel(ga, ra) < 1e-5 and rel(gb, rb) < 1e-5
-    # velocities are ~1e-4 of the density scale: compare on the density scale
-    assert np.abs(gu - ru).max() < 1e-5 * np.abs(ra).max()
-    assert np.abs(g.get_colloids()["pos"] - o.get_colloids()["pos"]).max() < 1e-5
+    g, o = run_both(w.shape, w.params, w.steps, prec, w.colloids(), w.densities())
+    compare_fields(g, o, tol)
+    compare_colloids(g, o, tol)
 
 
-def test_fp16_storage_small_workload():
-    """FP16 deviation storage (FP32 arithmetic) vs the FP64 oracle: 1e-3 on
-    the fields after 100 steps."""
-    w = workload("small_fp64")
-    g, o = run_both(w.shape, w.params, w.steps, "fp16", w.colloids(), w.densities())
-    ga, gb, gu = g.get_fields()
-    ra, rb, ru = o.get_fields()
-    assert rel(ga, ra) < 1e-3 and rel(gb, rb) < 1e-3
-    assert np.abs(gu - ru).max() < 1e-3 * np.abs(ra).max()
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("fp16", 1e-3)])
+def test_sheared_walls_with_particles(prec, tol):
+    """Walls at z = -1/2, nz - 1/2 moving at -/+0.05 (the confined shear
+    workload's boundary), four particles, 100 steps: velocities are O(0.05)
+    here and are compared relative to themselves."""
+    shape = (32, 21, 23)
+    w = workload("shear512")
+    params = dict(w.params, side_wall_d=6.5)
+    col = dict(pos=[[8.2, 5.3, 7.7], [22.6, 14.1, 11.4], [9.9, 16.2, 15.8], [25.1, 4.4, 16.0]],
+               radius=5.5, mass=700.0)
+    g, o = run_both(shape, params, 100, prec, col)
+    ru = o.get_fields()[2]
+    assert np.abs(ru).max() > 0.02
+    compare_fields(g, o, tol, u_scale=0.0)
+    compare_colloids(g, o, tol)
 
 
 def test_mass_conservation_gpu_fp64():

@@ -185,6 +185,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="shear512")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "fp64"])
+    ap.add_argument("--shape", type=int, nargs=3, default=None,
+                    help="rescale the workload box (same physics and particle volume fraction)")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/FP64 side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()
@@ -216,7 +218,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    w = workload(args.workload)
+    w = workload(args.workload, tuple(args.shape) if args.shape else None)
     a, b = w.densities()
     col = w.colloids()
     lat = LBLattice(w.shape, args.prec, max_colloids=w.n_colloids, device=dev)
@@ -245,7 +247,7 @@ def main():
     achieved = alg / (kavg / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.prec),
-                "kernel": "k_collide_push", "kernel_ms": round(kavg, 4),
+                "kernel": "k_fused", "kernel_ms": round(kavg, 4),
                 "alg_bytes_per_launch": alg, "peak_kind": peak_kind,
                 "step_frac": round(alg / (ms_step / 1e3) / 1e9 / peak, 4)}
 
@@ -308,8 +310,10 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec],
             "data": "synthetic",
-            "config": {"workload": "%s: %dx%dx%d sites, walls z +-0.05, R=5.5 phi=0.15 (%d particles), "
-                                   "G=0.65, tau=1" % (args.workload, *w.shape, n),
+            "config": {"workload": "%s: %dx%dx%d sites, %s, R=%g (%d particles), G=%g, tau=%g" % (
+                           args.workload, *w.shape,
+                           "walls z +-%g" % w.params["wall_u_hi"][0] if w.params["bc"][2] == 0 else "periodic",
+                           w.radius, n, w.params["G"], w.params["tau"][0]),
                        "prec": args.prec, "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (%.1f GB of populations)" % (
                            2 * 38 * N * {"fp64": 8, "fp32": 4, "fp16": 2}[args.prec] / 1e9)},

@@ -336,16 +336,53 @@ __global__ void __launch_bounds__(PB) k_remap_commit(Lattice L) {
 }
 
 // ------------------------------------------------------------ wetting
-// Eq. 20 on each frontier node s of particle p (a node of p with at least one
-// fluid neighbour): psi^k(s) = (1 + zeta^k) sum w_i rho^k / sum w_i over fluid
-// neighbours; and Eq. 21 (repulsive sign): F_s = -G sum_k psi^k(s) sum w_i
-// rho^kbar(s + c_i) c_i over fluid neighbours, summed with its torque.
+// Indices of the 18 neighbours of a site (-1 beyond a wall) and the bit set
+// of those that are particle nodes; the 18 mask loads are independent, so
+// they are in flight together.
+__device__ __forceinline__ uint32_t nbr_solid(const Lattice& L, const SiteNbr& n, int (&m)[Q]) {
+    uint32_t bits = 0;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        bool wall = nbr_is_wall(n, i);
+        m[i] = wall ? -1 : (int)nbr_index(L, n, i);
+        uint8_t v = wall ? 0 : __ldg(L.mask + m[i]);
+        bits |= (uint32_t)(v != 0) << i;
+    }
+    return bits;
+}
+
+// Two phases per particle p:
+//  1. rho^k of the fluid nodes within sqrt(2) outside its surface (the
+//     boundary nodes: their densities feed Eq. 20 here and the link forces
+//     of Eq. 19 after the lattice step), written to psi;
+//  2. Eq. 20 on each frontier node s of p (a node of p with at least one
+//     fluid neighbour): psi^k(s) = (1 + zeta^k) sum w_i rho^k / sum w_i over
+//     fluid neighbours; and Eq. 21 (repulsive sign):
+//     F_s = -G sum_k psi^k(s) sum w_i rho^kbar(s + c_i) c_i, summed with its
+//     torque.  Every fluid neighbour of a frontier node of p is a boundary
+//     node of p, so phase 2 reads only densities written in phase 1 by the
+//     same block (other blocks may write equal values to shared nodes).
 template <int PREC>
 __global__ void __launch_bounds__(PB) k_virtual(Lattice L, int store_terms) {
+    typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
     int p = blockIdx.x;
-    PGeo<C> g = pgeo<C>(L, p, 0.0);
+    PGeo<C> g = pgeo<C>(L, p, 1.5);
     C* psi = (C*)L.psi;
+    const S* f = (const S*)L.f_cur;
+    for_box<C>(L, g, [&](int, int, int, long long s, int, int, int, const C (&d)[3]) {
+        if (!in_shell<C>(g, d, -0.01f, 1.45f)) return;
+        if (L.mask[s]) return;
+        C r0 = 0, r1 = 0;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            r0 += ld_pop(f + ((long long)i) * L.pstride + s, pop_shift<S, C>(L, 0, i));
+            r1 += ld_pop(f + ((long long)(Q + i)) * L.pstride + s, pop_shift<S, C>(L, 1, i));
+        }
+        psi[s] = r0;
+        psi[L.N + s] = r1;
+    });
+    __syncthreads();
     CSum<C> acc[6];
     zero(acc);
     const C G = C(L.P.G), z0 = C(1) + C(L.P.zeta[0]), z1 = C(1) + C(L.P.zeta[1]);
@@ -354,14 +391,15 @@ __global__ void __launch_bounds__(PB) k_virtual(Lattice L, int store_terms) {
         if (!in_shell<C>(g, d, -1.5f, 0.01f)) return;
         if (L.owner[s] != p) return;
         SiteNbr n = site_nbr(L, X, Y, Z);
+        int m[Q];
+        uint32_t solid = nbr_solid(L, n, m);
         C num[2] = {0, 0}, den = 0;
         C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};
+#pragma unroll
         for (int i = 1; i < Q; i++) {
-            if (nbr_is_wall(n, i)) continue;
-            long long m = nbr_index(L, n, i);
-            if (L.mask[m]) continue;
-            C w = wgt<C>(i);
-            C ra = psi[m], rb = psi[L.N + m];
+            bool fl = m[i] >= 0 && !((solid >> i) & 1u);
+            C ra = fl ? psi[m[i]] : C(0), rb = fl ? psi[L.N + m[i]] : C(0);
+            C w = fl ? wgt<C>(i) : C(0);
             num[0] += w * ra;
             num[1] += w * rb;
             den += w;
@@ -375,12 +413,12 @@ __global__ void __launch_bounds__(PB) k_virtual(Lattice L, int store_terms) {
         psi[L.N + s] = pb;
         if (store_terms) {
             C fs[3], tq[3];
-            for (int m = 0; m < 3; m++) fs[m] = -G * pa * sB[m] + -G * pb * sA[m];
+            for (int q = 0; q < 3; q++) fs[q] = -G * pa * sB[q] + -G * pb * sA[q];
             crs<C>(d, fs, tq);
 #pragma unroll
-            for (int m = 0; m < 3; m++) {
-                acc[m].add(fs[m]);
-                acc[3 + m].add(tq[m]);
+            for (int q = 0; q < 3; q++) {
+                acc[q].add(fs[q]);
+                acc[3 + q].add(tq[q]);
             }
         }
     });
@@ -388,9 +426,9 @@ __global__ void __launch_bounds__(PB) k_virtual(Lattice L, int store_terms) {
     double out[6];
     block_reduce<6, C>(acc, out);
     if (threadIdx.x == 0 && threadIdx.y == 0)
-        for (int m = 0; m < 3; m++) {
-            L.Fs[3 * p + m] = out[m];
-            L.Ts[3 * p + m] = out[3 + m];
+        for (int q = 0; q < 3; q++) {
+            L.Fs[3 * p + q] = out[q];
+            L.Ts[3 * p + q] = out[3 + q];
         }
 }
 
@@ -399,6 +437,8 @@ __global__ void __launch_bounds__(PB) k_virtual(Lattice L, int store_terms) {
 // F_i = [2 f*_i(x) - 2 w_i rho^k (u_w.c_i)/cs^2] c_i summed over k, with
 // f*_i(x) recovered from the bounced population f_ibar(x, t+1) written by the
 // lattice step; Eqs. 22-23 sum the forces and torques (r_w - r_p) x F_i.
+// The neighbour masks, then the owners of the particle neighbours, then the
+// bounced populations are each loaded as one independent batch.
 template <int PREC>
 __global__ void __launch_bounds__(PB) k_links(Lattice L) {
     typedef typename Prec<PREC>::S S;
@@ -411,23 +451,38 @@ __global__ void __launch_bounds__(PB) k_links(Lattice L) {
     zero(acc);
     for_box<C>(L, g, [&](int X, int Y, int Z, long long s, int, int, int, const C (&d)[3]) {
         // a fluid node linked to p lies within sqrt(2) outside the surface
-        if (!in_shell<C>(g, d, -0.01f, 1.5f)) return;
+        if (!in_shell<C>(g, d, -0.01f, 1.45f)) return;
         if (L.mask[s]) return;
         SiteNbr n = site_nbr(L, X, Y, Z);
+        int m[Q];
+        uint32_t solid = nbr_solid(L, n, m);
+        if (!solid) return;
+        uint32_t mine = 0;
+#pragma unroll
+        for (int i = 1; i < Q; i++)
+            if ((solid >> i) & 1u) mine |= (uint32_t)(__ldg(L.owner + m[i]) == p) << i;
+        if (!mine) return;
         C rho0 = psi[s], rho1 = psi[L.N + s];
+        C fb[2][Q];
+#pragma unroll
         for (int i = 1; i < Q; i++) {
-            if (nbr_is_wall(n, i)) continue;
-            long long m = nbr_index(L, n, i);
-            if (!L.mask[m] || L.owner[m] != p) continue;
+            bool on = (mine >> i) & 1u;
+            fb[0][i] = on ? ld_pop(fn + ((long long)opp(i)) * L.pstride + s, pop_shift<S, C>(L, 0, opp(i))) : C(0);
+            fb[1][i] = on ? ld_pop(fn + ((long long)(Q + opp(i))) * L.pstride + s, pop_shift<S, C>(L, 1, opp(i)))
+                          : C(0);
+        }
+#pragma unroll
+        for (int i = 1; i < Q; i++) {
+            if (!((mine >> i) & 1u)) continue;
             C rel[3] = {d[0] + C(0.5) * C(cx(i)), d[1] + C(0.5) * C(cy(i)), d[2] + C(0.5) * C(cz(i))};
             C wxr[3];
             crs<C>(g.w, rel, wxr);
             C cu = C(cx(i)) * (g.v[0] + wxr[0]) + C(cy(i)) * (g.v[1] + wxr[1]) + C(cz(i)) * (g.v[2] + wxr[2]);
-            int ib = opp(i);
             C fl = 0;
+#pragma unroll
             for (int k = 0; k < 2; k++) {
                 C corr = C(6) * wgt<C>(i) * (k == 0 ? rho0 : rho1) * cu;
-                C fstar = ld_pop(fn + ((long long)(k * Q + ib)) * L.pstride + s, pop_shift<S, C>(L, k, ib)) + corr;
+                C fstar = fb[k][i] + corr;
                 fl += C(2) * fstar - corr;
             }
             C F[3] = {fl * C(cx(i)), fl * C(cy(i)), fl * C(cz(i))}, tq[3];
@@ -442,9 +497,9 @@ __global__ void __launch_bounds__(PB) k_links(Lattice L) {
     double out[6];
     block_reduce<6, C>(acc, out);
     if (threadIdx.x == 0 && threadIdx.y == 0)
-        for (int m = 0; m < 3; m++) {
-            L.Fliq[3 * p + m] = out[m];
-            L.Tliq[3 * p + m] = out[3 + m];
+        for (int q = 0; q < 3; q++) {
+            L.Fliq[3 * p + q] = out[q];
+            L.Tliq[3 * p + q] = out[3 + q];
         }
 }
 

@@ -218,6 +218,7 @@ struct FusedShared {
     typedef typename Prec<PREC>::C C;
     C psi[3][2][RH][RW];
     uint8_t sol[3][RH][RW];  // 0 fluid, 1 particle node, 2 beyond a wall
+    int pid[3][RH][RW];      // owning particle of a particle node
     S stage[2 * Q][FNT];
 };
 
@@ -287,6 +288,7 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
             sh.psi[slot][0][ty + 1][tx + 1] = psi[s];
             sh.psi[slot][1][ty + 1][tx + 1] = psi[L.N + s];
             sh.sol[slot][ty + 1][tx + 1] = 1;
+            sh.pid[slot][ty + 1][tx + 1] = L.owner[s];
         } else {
             if (want_own) {
 #pragma unroll
@@ -326,6 +328,7 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
             r0 = psi[s];
             r1 = psi[L.N + s];
             sl = 1;
+            sh.pid[slot][ly + 1][lx + 1] = L.owner[s];
         } else {
             r0 = 0;
             r1 = 0;
@@ -408,7 +411,7 @@ __device__ __forceinline__ void collide_site(const Lattice& L, FusedShared<PREC>
                 const double* uw = cz(i) < 0 ? L.P.wall_u_lo : L.P.wall_u_hi;
                 cu = C(cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2]);
             } else {
-                cu = particle_cu<C>(L, L.owner[nbr_index(L, n, i)], x, y, z, i);
+                cu = particle_cu<C>(L, sh.pid[sl[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)], x, y, z, i);
             }
 #pragma unroll
             for (int k = 0; k < 2; k++)
@@ -455,48 +458,6 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : 2)) k_fused(Lattic
 #pragma unroll
         for (int d = 0; d < 3; d++) { cur.j[0][d] = nxt.j[0][d]; cur.j[1][d] = nxt.j[1][d]; }
         int t = lo; lo = mid; mid = hi; hi = t;
-    }
-}
-
-// rho^k of fluid nodes within R + 1.6 of particle p (the nodes whose density
-// the wetting and link kernels read), written to psi
-template <int PREC>
-__global__ void __launch_bounds__(128) k_shell_density(Lattice L) {
-    typedef typename Prec<PREC>::S S;
-    typedef typename Prec<PREC>::C C;
-    int p = blockIdx.x;
-    double R = L.rad[p], pad = 1.6;
-    int lo[3], ext[3];
-    float rf[3];
-    for (int d = 0; d < 3; d++) {
-        double r = L.pos[3 * p + d];
-        lo[d] = (int)floor(r - R - pad);
-        ext[d] = (int)ceil(r + R + pad) - lo[d] + 1;
-        rf[d] = float(r - (double)lo[d]);
-    }
-    float Rmax2 = float((R + pad) * (R + pad));
-    const S* f = (const S*)L.f_cur;
-    C* psi = (C*)L.psi;
-    int total = ext[0] * ext[1] * ext[2];
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        int a = t % ext[0], b = (t / ext[0]) % ext[1], c = t / (ext[0] * ext[1]);
-        float dx = float(a) - rf[0], dy = float(b) - rf[1], dz = float(c) - rf[2];
-        if (dx * dx + dy * dy + dz * dz >= Rmax2) continue;
-        int X = lo[0] + a, Y = lo[1] + b, Z = lo[2] + c;
-        if (!L.per[2] && (Z < 0 || Z >= L.nz)) continue;
-        X = X < 0 ? X + L.nx : (X >= L.nx ? X - L.nx : X);
-        Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
-        Z = Z < 0 ? Z + L.nz : (Z >= L.nz ? Z - L.nz : Z);
-        long long s = (long long)X + (long long)L.nx * ((long long)Y + (long long)L.ny * Z);
-        if (L.mask[s]) continue;
-        C r0 = 0, r1 = 0;
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            r0 += ld_pop(f + ((long long)i) * L.pstride + s, pop_shift<S, C>(L, 0, i));
-            r1 += ld_pop(f + ((long long)(Q + i)) * L.pstride + s, pop_shift<S, C>(L, 1, i));
-        }
-        psi[s] = r0;
-        psi[L.N + s] = r1;
     }
 }
 
@@ -669,10 +630,6 @@ int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st) {
 
 int launch_shell_density(const Lattice& L, int prec, cudaStream_t st) {
     int n = 0;
-    if (L.nc > 0) {
-        DISPATCH(prec, (k_shell_density<P><<<L.nc, 128, 0, st>>>(L)));
-        n++;
-    }
     if (!L.per[2]) {
         dim3 g((unsigned)((L.nx + 127) / 128), (unsigned)L.ny, 2);
         DISPATCH(prec, (k_wall_plane_density<P><<<g, 128, 0, st>>>(L)));

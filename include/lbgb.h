@@ -153,6 +153,28 @@ int lb_get_owner(lb_ctx *ctx, int *out);
 int lb_profile(lb_ctx *ctx, int enable);
 int lb_profile_read(lb_ctx *ctx, double *total_ms, long long *launches);
 
+/* Global FP64 sums of a population array that the caller holds on the
+ * device, computed without allocating any device memory and without a
+ * context.  The paper has no counterpart: this is a convenience for callers
+ * that cannot allocate at the point of the call (for example a monitor running
+ * between the time steps of an application whose device memory belongs to its
+ * own pool, where a cudaMalloc would synchronise the device and bypass the
+ * pool) and that hold no workspace.
+ *   d_pops: populations [2][19][plane_stride] in the storage type of prec
+ *           (LB_FP16: half deviations f - w_i rho0^k), site s = x + nx(y + ny z);
+ *   d_mask: N bytes, nonzero = particle node (skipped), or NULL;
+ *   rho0:   host array of 2 reference densities (needed for LB_FP16 only);
+ *   d_out:  device array of 5 doubles: mass of A and B, sum_k j^k (x, y, z).
+ * The scratch is a static device array of per-plane partials (320 KiB on each
+ * device that loads the library, kept until exit): nz must be <= 4096,
+ * otherwise LB_ERR_ARG.  The first call on a device looks up that array's
+ * address and should come before any stream capture.  Calls share the array,
+ * so calls that overlap on the GPU race; calls ordered on one stream do not.
+ * Runs asynchronously on cuda_stream; returns LB_ERR_ARG / LB_ERR_CUDA on bad
+ * arguments or a failed launch. */
+int lb_totals_static(const void *d_pops, int prec, int nx, int ny, int nz, long long plane_stride,
+                     const unsigned char *d_mask, const double *rho0, double *d_out, void *cuda_stream);
+
 /* Number of kernel launches issued by this context since creation. */
 long long lb_launch_count(const lb_ctx *ctx);
 

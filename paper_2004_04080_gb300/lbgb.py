@@ -28,8 +28,8 @@ TERMS = {"F_liq": 0, "T_liq": 1, "F_d": 2, "T_d": 3, "F_c": 4, "T_c": 5, "F_s": 
 # every symbol declared in include/lbgb.h
 EXPORTS = ["lb_workspace_bytes", "lb_create", "lb_set_params", "lb_init_fields", "lb_add_colloids",
            "lb_step", "lb_get_fields", "lb_get_colloids", "lb_get_colloid_terms", "lb_get_totals",
-           "lb_get_populations", "lb_get_owner", "lb_profile", "lb_profile_read", "lb_launch_count",
-           "lb_destroy", "lb_last_error"]
+           "lb_get_populations", "lb_get_owner", "lb_profile", "lb_profile_read", "lb_totals_static",
+           "lb_launch_count", "lb_destroy", "lb_last_error"]
 
 
 class LbParams(C.Structure):
@@ -78,6 +78,7 @@ def load(build_if_missing: bool = True):
     lib.lb_get_owner.argtypes = [P, I]
     lib.lb_profile.argtypes = [P, C.c_int]
     lib.lb_profile_read.argtypes = [P, D, C.POINTER(C.c_longlong)]
+    lib.lb_totals_static.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_longlong, P, D, P, P]
     lib.lb_launch_count.argtypes = [P]
     lib.lb_launch_count.restype = C.c_longlong
     lib.lb_destroy.argtypes = [P]
@@ -209,6 +210,19 @@ def lb_profile_read(h):
     t, n = C.c_double(0.0), C.c_longlong(0)
     _check(h, load().lb_profile_read(h, C.byref(t), C.byref(n)), "lb_profile_read")
     return t.value, n.value
+
+
+def lb_totals_static(d_pops: int, prec: int, nx: int, ny: int, nz: int, plane_stride: int, d_mask: int,
+                     rho0, d_out: int, stream_ptr: int) -> int:
+    """Allocation-free global totals of caller-held device populations (see
+    lbgb.h); pointers are device addresses as integers (0 for NULL)."""
+    r0 = None if rho0 is None else _f64(rho0, 2)
+    rc = load().lb_totals_static(C.c_void_p(d_pops), prec, nx, ny, nz, plane_stride,
+                                 C.c_void_p(d_mask or None), _dp(r0), C.c_void_p(d_out),
+                                 C.c_void_p(stream_ptr or None))
+    if rc:
+        raise LBError(rc, "lb_totals_static")
+    return rc
 
 
 def lb_launch_count(h) -> int:

@@ -463,6 +463,11 @@ __global__ void __launch_bounds__(PB) k_links(Lattice L) {
             if ((solid >> i) & 1u) mine |= (uint32_t)(__ldg(L.owner + m[i]) == p) << i;
         if (!mine) return;
         C rho0 = psi[s], rho1 = psi[L.N + s];
+        // c_i . u_w = c_i . (v_p + omega_p x d) for every link of this site (Eq. 18
+        // with r_w = x + c_i/2; the c_i/2 part drops out of the projection)
+        C wxd[3];
+        crs<C>(g.w, d, wxd);
+        C U0[3] = {g.v[0] + wxd[0], g.v[1] + wxd[1], g.v[2] + wxd[2]};
         C fb[2][Q];
 #pragma unroll
         for (int i = 1; i < Q; i++) {
@@ -475,9 +480,7 @@ __global__ void __launch_bounds__(PB) k_links(Lattice L) {
         for (int i = 1; i < Q; i++) {
             if (!((mine >> i) & 1u)) continue;
             C rel[3] = {d[0] + C(0.5) * C(cx(i)), d[1] + C(0.5) * C(cy(i)), d[2] + C(0.5) * C(cz(i))};
-            C wxr[3];
-            crs<C>(g.w, rel, wxr);
-            C cu = C(cx(i)) * (g.v[0] + wxr[0]) + C(cy(i)) * (g.v[1] + wxr[1]) + C(cz(i)) * (g.v[2] + wxr[2]);
+            C cu = C(cx(i)) * U0[0] + C(cy(i)) * U0[1] + C(cz(i)) * U0[2];
             C fl = 0;
 #pragma unroll
             for (int k = 0; k < 2; k++) {

@@ -92,14 +92,16 @@ __global__ void k_wall_psi(Lattice L) {
     pw[(side * 2 + 1) * nxy + w] = den > C(0) ? num1 / den : C(0);
 }
 
-// c_i . u_w for the link from site (x,y,z) along i into particle p, with the
-// rigid-body wall velocity u_w = v_p + omega_p x (r_w - r_p), r_w = x + c_i/2
-// (Eq. 18).  The offset r_w - r_p is formed from the integer part of r_p and
-// its fractional part, so it is exact in FP64 and accurate to FP32 rounding of
-// a number below 1 in the FP32 forms (which read the FP32 particle snapshot).
+// U0 = v_p + omega_p x (x - r_p) for a site x next to particle p.  For the
+// link along c_i the wall velocity of Eq. 18 is u_w = v_p + omega_p x (r_w -
+// r_p) with r_w = x + c_i/2, and c_i . u_w = c_i . U0 because c_i . (omega x
+// c_i) = 0: one U0 per site serves every link of that site into p.  The
+// offset x - r_p is formed from the integer part of r_p and its fractional
+// part, exact in FP64 and accurate to FP32 rounding of a number below 1 in the
+// FP32 forms (which read the FP32 particle snapshot).
 template <typename C>
-__device__ __forceinline__ C particle_cu(const Lattice& L, int p, int x, int y, int z, int i) {
-    int xs[3] = {x, y, z}, Ls[3] = {L.nx, L.ny, L.nz}, cc[3] = {cx(i), cy(i), cz(i)};
+__device__ __forceinline__ void particle_u0(const Lattice& L, int p, int x, int y, int z, C (&U0)[3]) {
+    int xs[3] = {x, y, z}, Ls[3] = {L.nx, L.ny, L.nz};
     C rel[3], v[3], w[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
@@ -122,73 +124,11 @@ __device__ __forceinline__ C particle_cu(const Lattice& L, int p, int x, int y, 
             if (2 * dd > Ls[d]) dd -= Ls[d];
             else if (2 * dd < -Ls[d]) dd += Ls[d];
         }
-        rel[d] = C(dd) + C(0.5) * C(cc[d]) - fr;
+        rel[d] = C(dd) - fr;
     }
-    C u0 = v[0] + (w[1] * rel[2] - w[2] * rel[1]);
-    C u1 = v[1] + (w[2] * rel[0] - w[0] * rel[2]);
-    C u2 = v[2] + (w[0] * rel[1] - w[1] * rel[0]);
-    return C(cc[0]) * u0 + C(cc[1]) * u1 + C(cc[2]) * u2;
-}
-
-// The fused step at one fluid site: moments (Eqs. 6, 7, 14), Shan-Chen force
-// (Eq. 11), EDM collision (Eq. 16), then push-streaming (Eq. 3) with halfway
-// bounce-back on particle links (Eq. 17, wall velocity of Eq. 18) and on wall
-// links (Eq. 9).  Particle velocities are the stored v(t-1/2), omega(t-1/2).
-template <int PREC>
-__global__ void __launch_bounds__(128) k_collide_push(Lattice L) {
-    typedef typename Prec<PREC>::S S;
-    typedef typename Prec<PREC>::C C;
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y, z = blockIdx.z;
-    if (x >= L.nx) return;
-    long long s = (long long)x + (long long)L.nx * ((long long)y + (long long)L.ny * z);
-    if (L.mask[s]) return;
-    SiteNbr n = site_nbr(L, x, y, z);
-    C fv[2][Q], rho[2], j[2][3], F[2][3], u[3], om;
-    load_site<PREC>(L, (const S*)L.f_cur, s, fv, rho, j);
-    sc_force<C>(L, n, rho, F);
-    mixture<C>(L, rho, j, u, om);
-    C us[2][3];
-    C tiny = sizeof(C) == 8 ? C(1e-300) : C(1e-30);
-#pragma unroll
-    for (int k = 0; k < 2; k++)
-#pragma unroll
-        for (int d = 0; d < 3; d++) us[k][d] = rho[k] > tiny ? u[d] + F[k][d] / rho[k] : u[d];
-    C uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    C uus[2] = {us[0][0] * us[0][0] + us[0][1] * us[0][1] + us[0][2] * us[0][2],
-                us[1][0] * us[1][0] + us[1][1] * us[1][1] + us[1][2] * us[1][2]};
-    C one_m_om = C(1) - om;
-    S* fn = (S*)L.f_nxt;
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        C fs[2];
-#pragma unroll
-        for (int k = 0; k < 2; k++)
-            fs[k] = one_m_om * (fv[k][i] - feq<C>(i, rho[k], u[0], u[1], u[2], uu)) +
-                    feq<C>(i, rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
-        if (i != 0 && nbr_is_wall(n, i)) {
-            const double* uw = cz(i) < 0 ? L.P.wall_u_lo : L.P.wall_u_hi;
-            C cu = C(cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2]);
-#pragma unroll
-            for (int k = 0; k < 2; k++)
-                st_pop(fn + ((long long)(k * Q + opp(i))) * L.pstride + s,
-                       fs[k] - C(6) * wgt<C>(i) * rho[k] * cu, pop_shift<S, C>(L, k, opp(i)));
-            continue;
-        }
-        long long m = i == 0 ? s : nbr_index(L, n, i);
-        if (i == 0 || !L.mask[m]) {
-#pragma unroll
-            for (int k = 0; k < 2; k++)
-                st_pop(fn + ((long long)(k * Q + i)) * L.pstride + m, fs[k], pop_shift<S, C>(L, k, i));
-        } else {
-            // particle link (Eq. 17): c_i . u_w with u_w from Eq. 18 at r_w = x + c_i/2
-            C cu = particle_cu<C>(L, L.owner[m], x, y, z, i);
-#pragma unroll
-            for (int k = 0; k < 2; k++)
-                st_pop(fn + ((long long)(k * Q + opp(i))) * L.pstride + s,
-                       fs[k] - C(6) * wgt<C>(i) * rho[k] * cu, pop_shift<S, C>(L, k, opp(i)));
-        }
-    }
+    U0[0] = v[0] + (w[1] * rel[2] - w[2] * rel[1]);
+    U0[1] = v[1] + (w[2] * rel[0] - w[0] * rel[2]);
+    U0[2] = v[2] + (w[0] * rel[1] - w[1] * rel[0]);
 }
 
 // ------------------------------------------------------- fused step
@@ -391,6 +331,8 @@ __device__ __forceinline__ void collide_site(const Lattice& L, FusedShared<PREC>
     S* fn = (S*)L.f_nxt;
     long long s = (long long)x + (long long)L.nx * ((long long)y + (long long)L.ny * z);
     SiteNbr n = site_nbr(L, x, y, z);
+    int pc = -1;  // particle whose U0 is held
+    C U0[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         C fs[2];
@@ -411,7 +353,12 @@ __device__ __forceinline__ void collide_site(const Lattice& L, FusedShared<PREC>
                 const double* uw = cz(i) < 0 ? L.P.wall_u_lo : L.P.wall_u_hi;
                 cu = C(cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2]);
             } else {
-                cu = particle_cu<C>(L, sh.pid[sl[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)], x, y, z, i);
+                int p = sh.pid[sl[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)];
+                if (p != pc) {
+                    particle_u0<C>(L, p, x, y, z, U0);
+                    pc = p;
+                }
+                cu = C(cx(i)) * U0[0] + C(cy(i)) * U0[1] + C(cz(i)) * U0[2];
             }
 #pragma unroll
             for (int k = 0; k < 2; k++)

@@ -167,6 +167,38 @@ def run_reference(args, world, rank):
     return 0
 
 
+def adjoint_timing(dev, torch, steps=500):
+    """Adjoint / forward wall time on the 64^3 workload (8 immobile R=4.5
+    spheres, FP32): forward = the checkpointed forward run (sqrt(N)
+    checkpoints), adjoint = the reverse sweep (segment recomputation plus the
+    adjoint steps); the objective is J_drag + A."""
+    from paper_2004_04080_gb300.adjoint import AdjointRunner
+    from paper_2004_04080_gb300.lbgb import LBLattice
+    from paper_2004_04080_gb300.workloads import workload
+
+    w = workload("adjoint64")
+    a, b = w.densities()
+    col = w.colloids()
+    lat = LBLattice(w.shape, "fp32", max_colloids=w.n_colloids, device=dev)
+    run = AdjointRunner(lat, steps)
+    run.forward(w.params, a, b, col)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run.forward(w.params, a, b, col)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    grads, _ = run.backward(1.0, 1.0)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del run, lat
+    torch.cuda.empty_cache()
+    return {"workload": "adjoint64: 64^3 periodic, 8 immobile R=4.5 spheres, FP32, %d steps, %d checkpoints"
+                        % (steps, int(math.ceil(math.sqrt(steps)))),
+            "forward_s": round(t1 - t0, 4), "adjoint_s": round(t2 - t1, 4),
+            "adjoint_over_forward": round((t2 - t1) / (t1 - t0), 3),
+            "grad_finite": bool(np.all(np.isfinite(grads)))}
+
+
 def time_steps(lat, steps, torch):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -189,6 +221,7 @@ def main():
                     help="rescale the workload box (same physics and particle volume fraction)")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/FP64 side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint / forward timing")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args)
@@ -306,6 +339,10 @@ def main():
         if "fp16" in forms and args.prec == "fp32":
             forms["fp16_speedup_over_fp32"] = round(forms["fp16"]["mlups"] / value, 3)
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = adjoint_timing(dev, torch)
+
     line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec],
@@ -318,7 +355,7 @@ def main():
                        "l2": "inputs larger than L2 (%.1f GB of populations)" % (
                            2 * 38 * N * {"fp64": 8, "fp32": 4, "fp16": 2}[args.prec] / 1e9)},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
-            "forms": forms, "adjoint": None}
+            "forms": forms, "adjoint": adjoint}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:

@@ -153,6 +153,46 @@ int lb_get_owner(lb_ctx *ctx, int *out);
 int lb_profile(lb_ctx *ctx, int enable);
 int lb_profile_read(lb_ctx *ctx, double *total_ms, long long *launches);
 
+/* ---- Reverse mode (adjoint) of the time step, for immobile particles ----
+ * With every particle immobile (added with infinite mass and zero velocity and
+ * angular velocity) the node map is static and one time step is a smooth map
+ * f(t) -> f(t+1) of the populations (Sec. 2.3, Eqs. 5-7, 11, 13-16; bounce-back
+ * Eqs. 8, 9, 17; link forces Eqs. 19, 22) with parameters tau_A, tau_B, G,
+ * zeta_A, zeta_B.  lb_adjoint_step maps dJ/df(t+1) to dJ/df(t) and adds the
+ * step's parameter gradients; the caller keeps the states f(t) (checkpoints
+ * plus recomputation) and chains the steps backwards.  The adjoint functions
+ * return LB_ERR_STATE when a particle is mobile.
+ *
+ * A population state is 2 x 19 x (padded plane) values of the storage type
+ * (lb_state_bytes); lb_get_state / lb_set_state copy the current populations
+ * to / from such a caller device buffer (device to device, synchronous).
+ * An adjoint field holds lambda_i(x) = L_i(x) + R(x) in the compute type
+ * (FP64 for LB_FP64, FP32 otherwise): 2 x 19 planes L then 2 planes R
+ * (lb_adjoint_bytes: *field_bytes); adjoint calls also need one scratch
+ * buffer of *scratch_bytes.  All buffers are caller-owned device memory. */
+int lb_state_bytes(const lb_ctx *ctx, size_t *bytes);
+int lb_get_state(lb_ctx *ctx, void *d_dst);
+int lb_set_state(lb_ctx *ctx, const void *d_src);
+int lb_adjoint_bytes(const lb_ctx *ctx, size_t *field_bytes, size_t *scratch_bytes);
+
+/* Seed for the interface measure A = sum_x (1 - phi^2), phi =
+ * (rho_A - rho_B)/(rho_A + rho_B) over fluid nodes of the current state:
+ * writes weight * dA/df into d_adj and A into *value (host). */
+int lb_adjoint_seed(lb_ctx *ctx, double weight, void *d_adj, void *d_scratch, double *value);
+
+/* One step backwards.  d_state: the populations f(t) at the start of the step
+ * being reversed; d_adj_in: dJ/df(t+1); d_adj_out (distinct): receives
+ * dJ/df(t).  dJdF: host [n][3] array dJ/dF_liq,p of this step's link forces
+ * (Eq. 22), or NULL.  grads: host array of 5 to which dJ/d(tau_A, tau_B, G,
+ * zeta_A, zeta_B) of this step are added.  Synchronous. */
+int lb_adjoint_step(lb_ctx *ctx, const void *d_state, const void *d_adj_in, void *d_adj_out, void *d_scratch,
+                    const double *dJdF, double *grads);
+
+/* dJ/drho^k(0) for initial populations f = f^eq(rho^k, 0) (Eq. 5):
+ * d_grad (device, [2][N] doubles) = sum_i w_i lambda_i(0); zero on particle
+ * nodes (their initial fluid is removed by the first map). */
+int lb_adjoint_initial(lb_ctx *ctx, const void *d_adj, double *d_grad);
+
 /* Global FP64 sums of a population array that the caller holds on the
  * device, computed without allocating any device memory and without a
  * context.  The paper has no counterpart: this is a convenience for callers

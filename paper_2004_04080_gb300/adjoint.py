@@ -1,0 +1,139 @@
+"""Gradients of run observables through the hand-written adjoint of the
+lattice step (immobile particles), with sqrt(N) checkpointing.
+
+Observables of a run of T steps from f(0) = f^eq(rho^k(0), 0):
+  J_drag = (1/T) sum_t (1/n) sum_p sqrt(|F_liq,p(t+1/2)|^2 + eps^2)   (Eq. 22)
+  A      = sum_x (1 - phi^2), phi = (rho_A - rho_B)/(rho_A + rho_B) at t = T
+Parameters: tau_A, tau_B, G, zeta_A, zeta_B and the initial densities.
+
+Every step of the forward and adjoint runs in the library's kernels (through
+the C ABI); this module only schedules them: it stores the populations every
+K = ceil(sqrt(T)) steps during the forward run, and for each segment in
+reverse re-runs the forward steps to rebuild the states, then applies
+lb_adjoint_step backwards.  ``LBObjective`` wraps this as a
+torch.autograd.Function.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import lbgb
+
+
+class AdjointRunner:
+    """Forward run with checkpoints and its reverse sweep on one LBLattice."""
+
+    def __init__(self, lattice: "lbgb.LBLattice", steps: int, checkpoint_every: int | None = None,
+                 eps: float = 1e-12):
+        import torch
+
+        self.lat = lattice
+        self.steps = int(steps)
+        self.K = int(checkpoint_every or max(1, math.ceil(math.sqrt(self.steps))))
+        self.eps = eps
+        self.torch = torch
+        dev = lattice.device
+        self.state_bytes = lbgb.lb_state_bytes(lattice.h)
+        fb, sb = lbgb.lb_adjoint_bytes(lattice.h)
+        self.adj = [torch.empty(fb, dtype=torch.uint8, device=dev) for _ in range(2)]
+        self.scratch = torch.empty(sb, dtype=torch.uint8, device=dev)
+        self.stack = torch.empty((self.K, self.state_bytes), dtype=torch.uint8, device=dev)
+        self.checkpoints = {}
+
+    def _state(self):
+        t = self.torch.empty(self.state_bytes, dtype=self.torch.uint8, device=self.lat.device)
+        lbgb.lb_get_state(self.lat.h, t.data_ptr())
+        return t
+
+    def forward(self, params: dict, rhoA0, rhoB0, colloids: dict | None):
+        """Run T steps; returns (J_drag, A).  ``colloids``: pos, radius (the
+        particles are added immobile)."""
+        lat = self.lat
+        lat.set_params(**params)
+        lat.init_fields(rhoA0, rhoB0)
+        self.n = 0
+        if colloids is not None and len(colloids["pos"]):
+            pos = np.asarray(colloids["pos"], dtype=np.float64).reshape(-1, 3)
+            self.n = pos.shape[0]
+            lat.add_colloids(pos, colloids["radius"], np.full(self.n, np.inf))
+        self.checkpoints = {}
+        J = 0.0
+        for t in range(self.steps):
+            if t % self.K == 0:
+                self.checkpoints[t] = self._state()
+            lat.step(1)
+            if self.n:
+                F = lat.term("F_liq")
+                J += float(np.mean(np.sqrt(np.sum(F * F, axis=1) + self.eps ** 2)))
+        J /= self.steps
+        self.checkpoints[self.steps] = self._state()
+        A = lbgb.lb_adjoint_seed(lat.h, 0.0, self.adj[0].data_ptr(), self.scratch.data_ptr())
+        return J, A
+
+    def backward(self, gJ: float, gA: float):
+        """Gradients of gJ * J_drag + gA * A: (array of 5 parameter gradients
+        [tau_A, tau_B, G, zeta_A, zeta_B], array [2, N] for rho^k(0))."""
+        lat, torch = self.lat, self.torch
+        lbgb.lb_set_state(lat.h, self.checkpoints[self.steps].data_ptr())
+        cur, nxt = self.adj
+        lbgb.lb_adjoint_seed(lat.h, gA, cur.data_ptr(), self.scratch.data_ptr())
+        grads = np.zeros(5)
+        T = self.steps
+        for start in reversed(range(0, T, self.K)):
+            end = min(start + self.K, T)
+            lbgb.lb_set_state(lat.h, self.checkpoints[start].data_ptr())
+            forces = []
+            for t in range(start, end):
+                lbgb.lb_get_state(lat.h, self.stack[t - start].data_ptr())
+                lat.step(1)
+                forces.append(lat.term("F_liq") if self.n else None)
+            for t in reversed(range(start, end)):
+                dJdF = None
+                if self.n and gJ != 0.0:
+                    F = forces[t - start]
+                    dJdF = gJ / (T * self.n) * F / np.sqrt(np.sum(F * F, axis=1) + self.eps ** 2)[:, None]
+                lbgb.lb_adjoint_step(lat.h, self.stack[t - start].data_ptr(), cur.data_ptr(), nxt.data_ptr(),
+                                     self.scratch.data_ptr(), dJdF, grads)
+                cur, nxt = nxt, cur
+        g = torch.empty((2, lat.N), dtype=torch.float64, device=lat.device)
+        lbgb.lb_adjoint_initial(lat.h, cur.data_ptr(), g.data_ptr())
+        # leave the lattice in its final state
+        lbgb.lb_set_state(lat.h, self.checkpoints[self.steps].data_ptr())
+        return grads, g.cpu().numpy()
+
+
+def _objective_function():
+    import torch
+
+    class LBObjective(torch.autograd.Function):
+        """(theta, rhoA0, rhoB0) -> [J_drag, A]; theta = (tau_A, tau_B, G,
+        zeta_A, zeta_B) as a float64 tensor.  Non-tensor inputs: the
+        AdjointRunner, the remaining parameters and the particles."""
+
+        @staticmethod
+        def forward(ctx, theta, rhoA0, rhoB0, runner, base_params, colloids):
+            t = [float(v) for v in theta.detach().cpu().tolist()]
+            params = dict(base_params, tau=(t[0], t[1]), G=t[2], zeta=(t[3], t[4]))
+            J, A = runner.forward(params, rhoA0.detach().cpu().numpy(), rhoB0.detach().cpu().numpy(), colloids)
+            ctx.runner = runner
+            return torch.tensor([J, A], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            grads, grho = ctx.runner.backward(float(grad_out[0]), float(grad_out[1]))
+            return (torch.from_numpy(grads), torch.from_numpy(grho[0].copy()),
+                    torch.from_numpy(grho[1].copy()), None, None, None)
+
+    return LBObjective
+
+
+def LBObjective():
+    """The torch.autograd.Function class (created on first use)."""
+    global _CLS
+    try:
+        return _CLS
+    except NameError:
+        _CLS = _objective_function()
+        return _CLS

@@ -20,6 +20,7 @@ struct lb_ctx {
     char* ws;
     size_t ws_bytes;
     int have_params, have_fields, stepped;
+    int all_fixed;              // every particle immobile (infinite mass, at rest)
     long long launches;
     double* totals_dev;
     void* cells;
@@ -225,6 +226,7 @@ int lb_init_fields(lb_ctx* ctx, const double* rhoA, const double* rhoB, const do
     if (u) CK(cudaMemcpyAsync(st + 2 * L.N, u, 3 * nb, cudaMemcpyHostToDevice, ctx->stream), "copy u");
     else CK(cudaMemsetAsync(st + 2 * L.N, 0, 3 * nb, ctx->stream), "zero u");
     L.nc = 0;
+    ctx->all_fixed = 1;
     int n = launch_clear_map(L, ctx->stream);
     n += launch_init_fields(L, ctx->prec, st, ctx->stream);
     int rc = launched(ctx, n, "init kernels");
@@ -278,6 +280,12 @@ int lb_add_colloids(lb_ctx* ctx, int n, const double* pos, const double* vel, co
     }
     int first = L.nc;
     cudaStream_t s = ctx->stream;
+    int fixed = first == 0 ? 1 : ctx->all_fixed;
+    for (int p = 0; p < n; p++) {
+        if (!isinf(hm[p])) fixed = 0;
+        for (int d = 0; d < 3; d++)
+            if (hv[3 * p + d] != 0.0 || hw[3 * p + d] != 0.0) fixed = 0;
+    }
     cudaError_t e = cudaMemcpyAsync(L.pos + 3 * first, hp, 24 * (size_t)n, cudaMemcpyHostToDevice, s);
     if (!e) e = cudaMemcpyAsync(L.vel + 3 * first, hv, 24 * (size_t)n, cudaMemcpyHostToDevice, s);
     if (!e) e = cudaMemcpyAsync(L.omg + 3 * first, hw, 24 * (size_t)n, cudaMemcpyHostToDevice, s);
@@ -291,6 +299,7 @@ int lb_add_colloids(lb_ctx* ctx, int n, const double* pos, const double* vel, co
     if (e) return cuda_check(ctx, e, "copy particles");
     L.nc = first + n;
     L.rmax = rmax;
+    ctx->all_fixed = fixed;
     // the FP32 snapshot first: the map kernel of the FP32 forms reads it
     int nl = launch_snapshot(L, s);
     nl += launch_map_initial(L, ctx->prec, first, n, s);
@@ -430,6 +439,102 @@ int lb_get_colloid_terms(lb_ctx* ctx, int which, double* out) {
 }
 
 long long lb_launch_count(const lb_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+// ------------------------------------------------------------- adjoint
+static size_t state_bytes(const lb_ctx* ctx) { return (size_t)2 * Q * ctx->L.pstride * storage_bytes(ctx->prec); }
+
+int lb_state_bytes(const lb_ctx* ctx, size_t* bytes) {
+    if (!ctx || !bytes) return LB_ERR_ARG;
+    *bytes = state_bytes(ctx);
+    return LB_OK;
+}
+
+int lb_get_state(lb_ctx* ctx, void* d_dst) {
+    if (!ctx || !d_dst) return LB_ERR_ARG;
+    if (!ctx->have_fields) return set_err(ctx, LB_ERR_STATE, "no fields");
+    CK(cudaMemcpyAsync(d_dst, ctx->L.f_cur, state_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->stream), "copy state");
+    CK(cudaStreamSynchronize(ctx->stream), "state sync");
+    return LB_OK;
+}
+
+int lb_set_state(lb_ctx* ctx, const void* d_src) {
+    if (!ctx || !d_src) return LB_ERR_ARG;
+    if (!ctx->have_fields) return set_err(ctx, LB_ERR_STATE, "no fields");
+    CK(cudaMemcpyAsync(ctx->L.f_cur, d_src, state_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->stream), "copy state");
+    CK(cudaStreamSynchronize(ctx->stream), "state sync");
+    return LB_OK;
+}
+
+// scratch: [dJdF: maxc x 3 doubles][grads: 8 doubles][kernel scratch]
+static size_t adj_head_bytes(const lb_ctx* ctx) {
+    return align_up((size_t)(ctx->maxc > 0 ? ctx->maxc : 1) * 24) + align_up(64);
+}
+
+int lb_adjoint_bytes(const lb_ctx* ctx, size_t* field_bytes, size_t* scratch_bytes) {
+    if (!ctx || !field_bytes || !scratch_bytes) return LB_ERR_ARG;
+    *field_bytes = adjoint_field_bytes(ctx->L, ctx->prec);
+    *scratch_bytes = adj_head_bytes(ctx) + adjoint_scratch_bytes(ctx->L, ctx->prec);
+    return LB_OK;
+}
+
+static int adjoint_ready(lb_ctx* ctx) {
+    if (!ctx->have_fields) return set_err(ctx, LB_ERR_STATE, "no fields");
+    if (!ctx->all_fixed) return set_err(ctx, LB_ERR_STATE, "the adjoint needs immobile particles (infinite mass, at rest)");
+    return LB_OK;
+}
+
+int lb_adjoint_seed(lb_ctx* ctx, double weight, void* d_adj, void* d_scratch, double* value) {
+    if (!ctx || !d_adj || !d_scratch || !value) return LB_ERR_ARG;
+    int rc = adjoint_ready(ctx);
+    if (rc) return rc;
+    char* head = (char*)d_scratch;
+    double* val_dev = (double*)(head + align_up((size_t)(ctx->maxc > 0 ? ctx->maxc : 1) * 24));
+    rc = launched(ctx, launch_adjoint_seed(ctx->L, ctx->prec, d_adj, head + adj_head_bytes(ctx), weight, val_dev,
+                                           ctx->stream), "adjoint seed");
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(value, val_dev, 8, cudaMemcpyDeviceToHost, ctx->stream), "copy seed value");
+    CK(cudaStreamSynchronize(ctx->stream), "seed sync");
+    return LB_OK;
+}
+
+int lb_adjoint_step(lb_ctx* ctx, const void* d_state, const void* d_adj_in, void* d_adj_out, void* d_scratch,
+                    const double* dJdF, double* grads) {
+    if (!ctx || !d_state || !d_adj_in || !d_adj_out || !d_scratch || !grads || d_adj_in == d_adj_out)
+        return LB_ERR_ARG;
+    int rc = adjoint_ready(ctx);
+    if (rc) return rc;
+    Lattice Ls = ctx->L;
+    Ls.f_cur = (void*)d_state;
+    cudaStream_t s = ctx->stream;
+    char* head = (char*)d_scratch;
+    double* dJdF_dev = (double*)head;
+    double* grads_dev = (double*)(head + align_up((size_t)(ctx->maxc > 0 ? ctx->maxc : 1) * 24));
+    if (dJdF && Ls.nc > 0)
+        CK(cudaMemcpyAsync(dJdF_dev, dJdF, (size_t)Ls.nc * 24, cudaMemcpyHostToDevice, s), "copy dJdF");
+    // forward densities of step t: rho everywhere, wall and virtual densities
+    int n = launch_density(Ls, ctx->prec, s);
+    n += launch_wall_psi(Ls, ctx->prec, s);
+    n += launch_virtual(Ls, ctx->prec, 0, s);
+    n += launch_adjoint_step(Ls, ctx->prec, d_adj_in, d_adj_out, head + adj_head_bytes(ctx),
+                             (dJdF && Ls.nc > 0) ? dJdF_dev : nullptr, grads_dev, s);
+    rc = launched(ctx, n, "adjoint step");
+    if (rc) return rc;
+    double g[5];
+    CK(cudaMemcpyAsync(g, grads_dev, 40, cudaMemcpyDeviceToHost, s), "copy grads");
+    CK(cudaStreamSynchronize(s), "adjoint sync");
+    for (int a = 0; a < 5; a++) grads[a] += g[a];
+    return LB_OK;
+}
+
+int lb_adjoint_initial(lb_ctx* ctx, const void* d_adj, double* d_grad) {
+    if (!ctx || !d_adj || !d_grad) return LB_ERR_ARG;
+    int rc = adjoint_ready(ctx);
+    if (rc) return rc;
+    rc = launched(ctx, launch_adjoint_initial(ctx->L, ctx->prec, d_adj, d_grad, ctx->stream), "adjoint initial");
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(ctx->stream), "initial sync");
+    return LB_OK;
+}
 
 int lb_profile(lb_ctx* ctx, int enable) {
     if (!ctx) return LB_ERR_ARG;

@@ -258,4 +258,12 @@ int launch_links(const Lattice& L, int prec, cudaStream_t st);
 int launch_pairs_integrate(const Lattice& L, void* cells, size_t cell_cap, cudaStream_t st);
 int launch_snapshot(const Lattice& L, cudaStream_t st);
 
+size_t adjoint_field_bytes(const Lattice& L, int prec);
+size_t adjoint_scratch_bytes(const Lattice& L, int prec);
+int launch_adjoint_step(const Lattice& L, int prec, const void* in, void* out, void* scratch,
+                        const double* dJdF_dev, double* grads_dev, cudaStream_t st);
+int launch_adjoint_seed(const Lattice& L, int prec, void* adj, void* scratch, double weight, double* value_dev,
+                        cudaStream_t st);
+int launch_adjoint_initial(const Lattice& L, int prec, const void* adj, double* grad, cudaStream_t st);
+
 }  // namespace lbgb

@@ -28,8 +28,9 @@ TERMS = {"F_liq": 0, "T_liq": 1, "F_d": 2, "T_d": 3, "F_c": 4, "T_c": 5, "F_s": 
 # every symbol declared in include/lbgb.h
 EXPORTS = ["lb_workspace_bytes", "lb_create", "lb_set_params", "lb_init_fields", "lb_add_colloids",
            "lb_step", "lb_get_fields", "lb_get_colloids", "lb_get_colloid_terms", "lb_get_totals",
-           "lb_get_populations", "lb_get_owner", "lb_profile", "lb_profile_read", "lb_totals_static",
-           "lb_launch_count", "lb_destroy", "lb_last_error"]
+           "lb_get_populations", "lb_get_owner", "lb_profile", "lb_profile_read", "lb_state_bytes",
+           "lb_get_state", "lb_set_state", "lb_adjoint_bytes", "lb_adjoint_seed", "lb_adjoint_step",
+           "lb_adjoint_initial", "lb_totals_static", "lb_launch_count", "lb_destroy", "lb_last_error"]
 
 
 class LbParams(C.Structure):
@@ -78,6 +79,13 @@ def load(build_if_missing: bool = True):
     lib.lb_get_owner.argtypes = [P, I]
     lib.lb_profile.argtypes = [P, C.c_int]
     lib.lb_profile_read.argtypes = [P, D, C.POINTER(C.c_longlong)]
+    lib.lb_state_bytes.argtypes = [P, C.POINTER(C.c_size_t)]
+    lib.lb_get_state.argtypes = [P, P]
+    lib.lb_set_state.argtypes = [P, P]
+    lib.lb_adjoint_bytes.argtypes = [P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+    lib.lb_adjoint_seed.argtypes = [P, C.c_double, P, P, D]
+    lib.lb_adjoint_step.argtypes = [P, P, P, P, P, D, D]
+    lib.lb_adjoint_initial.argtypes = [P, P, P]
     lib.lb_totals_static.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_longlong, P, D, P, P]
     lib.lb_launch_count.argtypes = [P]
     lib.lb_launch_count.restype = C.c_longlong
@@ -210,6 +218,43 @@ def lb_profile_read(h):
     t, n = C.c_double(0.0), C.c_longlong(0)
     _check(h, load().lb_profile_read(h, C.byref(t), C.byref(n)), "lb_profile_read")
     return t.value, n.value
+
+
+def lb_state_bytes(h) -> int:
+    out = C.c_size_t(0)
+    _check(h, load().lb_state_bytes(h, C.byref(out)), "lb_state_bytes")
+    return out.value
+
+
+def lb_get_state(h, d_dst: int):
+    return _check(h, load().lb_get_state(h, C.c_void_p(d_dst)), "lb_get_state")
+
+
+def lb_set_state(h, d_src: int):
+    return _check(h, load().lb_set_state(h, C.c_void_p(d_src)), "lb_set_state")
+
+
+def lb_adjoint_bytes(h):
+    fb, sb = C.c_size_t(0), C.c_size_t(0)
+    _check(h, load().lb_adjoint_bytes(h, C.byref(fb), C.byref(sb)), "lb_adjoint_bytes")
+    return fb.value, sb.value
+
+
+def lb_adjoint_seed(h, weight: float, d_adj: int, d_scratch: int) -> float:
+    v = C.c_double(0.0)
+    _check(h, load().lb_adjoint_seed(h, float(weight), C.c_void_p(d_adj), C.c_void_p(d_scratch), C.byref(v)),
+           "lb_adjoint_seed")
+    return v.value
+
+
+def lb_adjoint_step(h, d_state: int, d_adj_in: int, d_adj_out: int, d_scratch: int, dJdF, grads: np.ndarray):
+    g = None if dJdF is None else _f64(dJdF)
+    return _check(h, load().lb_adjoint_step(h, C.c_void_p(d_state), C.c_void_p(d_adj_in), C.c_void_p(d_adj_out),
+                                            C.c_void_p(d_scratch), _dp(g), _dp(grads)), "lb_adjoint_step")
+
+
+def lb_adjoint_initial(h, d_adj: int, d_grad: int):
+    return _check(h, load().lb_adjoint_initial(h, C.c_void_p(d_adj), C.c_void_p(d_grad)), "lb_adjoint_initial")
 
 
 def lb_totals_static(d_pops: int, prec: int, nx: int, ny: int, nz: int, plane_stride: int, d_mask: int,

@@ -1,0 +1,139 @@
+"""The hand-written adjoint (immobile particles) against central finite
+differences in FP64, and against finite differences taken through the CPU
+oracle.  Objective: J = J_drag + A (mean drag magnitude over the run plus the
+interface measure at the end)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2004_04080_gb300.workloads import mixture_densities
+
+pytestmark = pytest.mark.gpu
+
+EPS = 1e-12
+NAMES = ["tau_A", "tau_B", "G", "zeta_A", "zeta_B"]
+
+
+def case(walls):
+    shape = (16, 14, 12)
+    base = dict(hertz_K=20.0, hertz_sigma=8.0, hertz_rcap=7.0)
+    if walls:
+        base.update(bc=(1, 1, 0), wall_u_lo=(-0.02, 0.0, 0.0), wall_u_hi=(0.02, 0.01, 0.0))
+    theta = np.array([0.9, 1.1, 0.9, 0.2, -0.15])
+    col = dict(pos=[[5.3, 6.2, 5.1], [11.6, 7.4, 6.3]], radius=[2.6, 2.4])
+    a, b = mixture_densities(shape, seed=13, amp=0.05)
+    return shape, base, theta, col, a, b
+
+
+def params_of(base, theta):
+    return dict(base, tau=(theta[0], theta[1]), G=theta[2], zeta=(theta[3], theta[4]))
+
+
+def gpu_objective(shape, base, theta, col, a, b, steps, prec="fp64"):
+    """(runner, [J_drag, A])"""
+    from paper_2004_04080_gb300.adjoint import AdjointRunner
+    from paper_2004_04080_gb300.lbgb import LBLattice
+
+    lat = LBLattice(shape, prec, max_colloids=len(col["pos"]))
+    run = AdjointRunner(lat, steps)
+    J, A = run.forward(params_of(base, theta), a, b, col)
+    return run, np.array([J, A])
+
+
+def oracle_objective(shape, base, theta, col, a, b, steps):
+    o = Oracle(*shape, len(col["pos"]))
+    o.set_params(**params_of(base, theta))
+    o.init_fields(a, b)
+    o.add_colloids(col["pos"], col["radius"], math.inf)
+    J = 0.0
+    for _ in range(steps):
+        o.step(1)
+        F = o.term("F_liq")
+        J += np.mean(np.sqrt(np.sum(F * F, axis=1) + EPS ** 2))
+    J /= steps
+    ra, rb, _ = o.get_fields()
+    fl = o.owner() < 0
+    phi = (ra[fl] - rb[fl]) / (ra[fl] + rb[fl])
+    return np.array([J, np.sum(1 - phi * phi)])
+
+
+def check(ad, fd, what):
+    assert abs(ad - fd) <= 1e-4 * abs(fd) + 1e-9, (what, ad, fd)
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_adjoint_matches_central_differences_fp64(walls):
+    """Each observable separately (J_drag, then A): adjoint gradients with
+    respect to the five parameters and, along a seeded random direction, the
+    initial densities agree with central differences to 1e-4 relative."""
+    shape, base, theta, col, a, b = case(walls)
+    steps = 20
+    run, _ = gpu_objective(shape, base, theta, col, a, b, steps)
+    gJ, rJ = run.backward(1.0, 0.0)
+    gA, rA = run.backward(0.0, 1.0)
+    for i, name in enumerate(NAMES):
+        h = 1e-5
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (gpu_objective(shape, base, tp, col, a, b, steps)[1] -
+              gpu_objective(shape, base, tm, col, a, b, steps)[1]) / (2 * h)
+        check(gJ[i], fd[0], ("J_drag", name))
+        check(gA[i], fd[1], ("A", name))
+    rng = np.random.default_rng(4)
+    da, db = rng.standard_normal(a.size), rng.standard_normal(b.size)
+    h = 1e-6
+    fd = (gpu_objective(shape, base, theta, col, a + h * da, b + h * db, steps)[1] -
+          gpu_objective(shape, base, theta, col, a - h * da, b - h * db, steps)[1]) / (2 * h)
+    check(float(rJ[0] @ da + rJ[1] @ db), fd[0], ("J_drag", "rho0"))
+    check(float(rA[0] @ da + rA[1] @ db), fd[1], ("A", "rho0"))
+
+
+def test_adjoint_matches_oracle_differences():
+    """Reference gradient through the oracle: central differences of the
+    oracle's observables agree with the GPU adjoint."""
+    shape, base, theta, col, a, b = case(True)
+    steps = 12
+    run, _ = gpu_objective(shape, base, theta, col, a, b, steps)
+    gJ, _ = run.backward(1.0, 0.0)
+    gA, _ = run.backward(0.0, 1.0)
+    for i, name in enumerate(NAMES):
+        h = 1e-5
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (oracle_objective(shape, base, tp, col, a, b, steps) -
+              oracle_objective(shape, base, tm, col, a, b, steps)) / (2 * h)
+        check(gJ[i], fd[0], ("J_drag", name))
+        check(gA[i], fd[1], ("A", name))
+
+
+def test_adjoint_fp32_agrees_with_fp64():
+    shape, base, theta, col, a, b = case(False)
+    steps = 20
+    r64, _ = gpu_objective(shape, base, theta, col, a, b, steps, "fp64")
+    g64, rho64 = r64.backward(0.0, 1.0)
+    r32, _ = gpu_objective(shape, base, theta, col, a, b, steps, "fp32")
+    g32, rho32 = r32.backward(0.0, 1.0)
+    assert np.all(np.abs(g32 - g64) <= 1e-3 * np.abs(g64) + 1e-6)
+    assert np.abs(rho32 - rho64).max() <= 1e-3 * np.abs(rho64).max()
+
+
+def test_autograd_function_runs():
+    import torch
+
+    from paper_2004_04080_gb300.adjoint import AdjointRunner, LBObjective
+    from paper_2004_04080_gb300.lbgb import LBLattice
+
+    shape, base, theta, col, a, b = case(False)
+    lat = LBLattice(shape, "fp32", max_colloids=2)
+    run = AdjointRunner(lat, 9)
+    th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+    ra = torch.tensor(a, requires_grad=True)
+    rb = torch.tensor(b, requires_grad=True)
+    out = LBObjective().apply(th, ra, rb, run, base, col)
+    (out[0] * 2.0 + out[1]).backward()
+    assert th.grad is not None and torch.all(torch.isfinite(th.grad))
+    assert ra.grad.shape == ra.shape and torch.isfinite(ra.grad).all()

@@ -51,7 +51,7 @@ enum {
     LB_ERR_NOMEM = -4,     /* workspace too small                             */
     LB_ERR_NONFINITE = -5, /* a density became non-finite or negative         */
     LB_ERR_OVERLAP = -6,   /* two particles claimed the same lattice node     */
-    LB_ERR_TIMEOUT = -7    /* reserved: a bounded device wait gave up          */
+    LB_ERR_TIMEOUT = -7    /* a bounded device wait (TMA copy) gave up        */
 };
 
 /* Storage precision of the populations.  LB_FP64 and LB_FP32 compute in the
@@ -88,7 +88,10 @@ int lb_workspace_bytes(int nx, int ny, int nz, int prec, int max_colloids, size_
 /* Create a context on the calling thread's current CUDA device.
  * d_workspace: device pointer, 256-byte aligned, >= lb_workspace_bytes bytes,
  * owned by the caller.  cuda_stream: a cudaStream_t or NULL.
- * Lattice sides must be >= 4; nx must be a multiple of 4. */
+ * Lattice sides must be >= 4; nx must be a multiple of 4.  With
+ * LBGB_FUSED_TMA=1 in the environment at lb_create, LB_FP32 (and LB_FP16 with
+ * nx a multiple of 8) use a fused lattice kernel that stages its tiles with
+ * tensor-memory-accelerator copies instead of the default plain loads. */
 int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void *d_workspace,
               size_t bytes, void *cuda_stream, lb_ctx **out);
 

@@ -7,6 +7,8 @@
 // population f(t) (the paper's step starts from it, Sec. 3.1); one step
 // reads f(t) at each site, collides locally and pushes f*(t) to the
 // neighbours, writing f(t+1) into the second buffer.
+#include <cuda.h>
+
 #include "lbgb_internal.cuh"
 
 namespace lbgb {
@@ -152,6 +154,13 @@ constexpr int RW = FTX + 2, RH = FTY + 2;
 
 // shared state of one block: psi^k and node flags of three planes (tile +
 // ring) and the raw populations of the own sites of the plane being collided
+template <typename C>
+struct PsiRing {
+    C psi[3][2][RH][RW];
+    uint8_t sol[3][RH][RW];  // 0 fluid, 1 particle node, 2 beyond a wall
+    int pid[3][RH][RW];      // owning particle of a particle node
+};
+
 template <int PREC>
 struct FusedShared {
     typedef typename Prec<PREC>::S S;
@@ -288,12 +297,12 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
 
 // collide and push the own site of plane z (slots: below, here, above); the
 // populations are in the stage, rho and j in `m`
-template <int PREC>
-__device__ __forceinline__ void collide_site(const Lattice& L, FusedShared<PREC>& sh, const int (&sl)[3], int x,
-                                             int y, int z, const OwnSite<PREC>& m) {
+template <int PREC, typename SH, typename PopFn>
+__device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int (&sl)[3], int x, int y, int z,
+                                             const OwnSite<PREC>& m, PopFn pop) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
-    int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
+    int tx = threadIdx.x, ty = threadIdx.y;
     // Eq. 11 (repulsive sign) + body force from the shared-memory psi planes
     C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};
 #pragma unroll
@@ -338,7 +347,7 @@ __device__ __forceinline__ void collide_site(const Lattice& L, FusedShared<PREC>
         C fs[2];
 #pragma unroll
         for (int k = 0; k < 2; k++)
-            fs[k] = one_m_om * (ld_pop(&sh.stage[k * Q + i][tid], pop_shift<S, C>(L, k, i)) -
+            fs[k] = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
                                 feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
                     feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
         uint8_t nb = i == 0 ? 0 : sh.sol[sl[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)];
@@ -395,7 +404,7 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : 2)) k_fused(Lattic
         __syncthreads();
         if (act && sh.sol[mid][ty + 1][tx + 1] == 0) {
             int sl[3] = {lo, mid, hi};
-            collide_site<PREC>(L, sh, sl, x0 + tx, y0 + ty, z, cur);
+            collide_site<PREC>(L, sh, sl, x0 + tx, y0 + ty, z, cur, [&](int q) { return &sh.stage[q][tid]; });
         }
         __syncthreads();
         if (have_n)
@@ -405,6 +414,224 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : 2)) k_fused(Lattic
 #pragma unroll
         for (int d = 0; d < 3; d++) { cur.j[0][d] = nxt.j[0][d]; cur.j[1][d] = nxt.j[1][d]; }
         int t = lo; lo = mid; mid = hi; hi = t;
+    }
+}
+
+// ----------------------------------------------- TMA-pipelined fused step
+// The same per-plane work as k_fused for the FP32 / FP16 forms, with the
+// populations of the tile and its one-site ring brought into shared memory by
+// the tensor-memory accelerator: one cp.async.bulk.tensor per plane copies a
+// box of (32 + 2 PAD) x 10 sites x 38 populations (PAD = 16 bytes of
+// elements, so that the box starts on a 16-byte boundary), three planes are
+// in flight on mbarriers, and the threads only read shared memory.  Waits are
+// bounded: on a timeout the block records LB_ERR_TIMEOUT, waits (bounded)
+// for its outstanding copies and returns.  Ring sites outside the box's
+// domain (periodic images at the lattice edges, which the copy fills with
+// zeros) are read from global memory.
+constexpr int TNB = 3;         // planes in flight
+constexpr int TBY = FTY + 2;   // box rows
+constexpr long TMA_SPIN = 1L << 22;
+
+template <int PREC>
+struct TmaGeom {
+    typedef typename Prec<PREC>::S S;
+    static constexpr int PAD = 16 / (int)sizeof(S);
+    static constexpr int BXT = FTX + 2 * PAD;
+    static constexpr unsigned BYTES = (unsigned)(BXT * TBY * 2 * Q * sizeof(S));
+};
+
+template <int PREC>
+struct TmaShared {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    S buf[TNB][2 * Q][TBY][TmaGeom<PREC>::BXT];
+    C psi[3][2][RH][RW];
+    uint8_t sol[3][RH][RW];
+    int pid[3][RH][RW];
+    unsigned long long mbar[TNB];
+    int abort;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+    for (long it = 0; it < TMA_SPIN; it++)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(FNT, 1) k_fused_tma(Lattice L, int zc, const __grid_constant__ CUtensorMap tm) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    typedef TmaGeom<PREC> TG;
+    extern __shared__ unsigned char smem_raw[];
+    TmaShared<PREC>& sh =
+        *reinterpret_cast<TmaShared<PREC>*>((((uintptr_t)smem_raw) + 127) & ~(uintptr_t)127);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
+    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
+    const int W = min(FTX, L.nx - x0), H = min(FTY, L.ny - y0);
+    const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, L.nz);
+    const bool act = tx < W && ty < H;
+    const S* fg = (const S*)L.f_cur;
+    const C* psig = (const C*)L.psi;
+    if (tid == 0) {
+        for (int b = 0; b < TNB; b++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sh.mbar[b])), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sh.abort = 0;
+    }
+    __syncthreads();
+    unsigned phase = 0;    // parity bit per buffer
+    unsigned pending = 0;  // buffers with a copy issued and not yet waited for
+    auto wall_plane = [&](int p) { return !L.per[2] && (p < 0 || p >= L.nz); };
+    auto buf_of = [&](int p) { return (p - z0 + 1) % TNB; };
+    auto issue = [&](int p) {
+        if (p > z1 || wall_plane(p)) return;
+        int b = buf_of(p);
+        pending |= 1u << b;
+        if (tid != 0) return;
+        int Z = p < 0 ? p + L.nz : (p >= L.nz ? p - L.nz : p);
+        unsigned bar = smem_u32(&sh.mbar[b]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(TG::BYTES) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+            "%5}], [%6];" ::"r"(smem_u32(&sh.buf[b][0][0][0])),
+            "l"(reinterpret_cast<unsigned long long>(&tm)), "r"(x0 - TG::PAD), "r"(y0 - 1), "r"(Z), "r"(0), "r"(bar)
+            : "memory");
+    };
+    auto wait = [&](int p) -> bool {
+        if (wall_plane(p)) return true;
+        int b = buf_of(p);
+        bool ok = mbar_wait_bounded(smem_u32(&sh.mbar[b]), (phase >> b) & 1u);
+        phase ^= 1u << b;
+        pending &= ~(1u << b);
+        if (!ok) sh.abort = 1;
+        return ok;
+    };
+    // psi^k and node flags of plane p (tile + ring) into ring slot `slot`
+    auto fill = [&](int p, int slot) {
+        if (wall_plane(p)) {
+            const C* pw = (const C*)L.psi_wall;
+            int side = p < 0 ? 0 : 1;
+            long long nxy = (long long)L.nx * L.ny;
+            for (int q = tid; q < (W + 2) * (H + 2); q += FNT) {
+                int lx = q % (W + 2) - 1, ly = q / (W + 2) - 1;
+                int X = x0 + lx, Y = y0 + ly;
+                X = X < 0 ? X + L.nx : (X >= L.nx ? X - L.nx : X);
+                Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
+                long long w = (long long)X + (long long)L.nx * Y;
+                sh.psi[slot][0][ly + 1][lx + 1] = pw[(side * 2 + 0) * nxy + w];
+                sh.psi[slot][1][ly + 1][lx + 1] = pw[(side * 2 + 1) * nxy + w];
+                sh.sol[slot][ly + 1][lx + 1] = 2;
+            }
+            return;
+        }
+        int b = buf_of(p);
+        int Z = p < 0 ? p + L.nz : (p >= L.nz ? p - L.nz : p);
+        long long zoff = (long long)L.nx * L.ny * Z;
+        int npos = (W + 2) * (H + 2);
+        for (int q = tid; q < npos; q += FNT) {
+            // own sites first (q < W*H), then the ring
+            int lx, ly;
+            if (q < W * H) {
+                lx = q % W;
+                ly = q / W;
+            } else {
+                int r = q - W * H;
+                if (r < W + 2) { lx = r - 1; ly = -1; }
+                else if (r < 2 * (W + 2)) { lx = r - (W + 2) - 1; ly = H; }
+                else if (r < 2 * (W + 2) + H) { lx = -1; ly = r - 2 * (W + 2); }
+                else { lx = W; ly = r - 2 * (W + 2) - H; }
+            }
+            int X = x0 + lx, Y = y0 + ly;
+            bool inside = X >= 0 && X < L.nx && Y >= 0 && Y < L.ny;
+            X = X < 0 ? X + L.nx : (X >= L.nx ? X - L.nx : X);
+            Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
+            long long s = (long long)X + (long long)L.nx * Y + zoff;
+            C r0 = 0, r1 = 0;
+            uint8_t sl = 0;
+            if (L.mask[s]) {
+                r0 = psig[s];
+                r1 = psig[L.N + s];
+                sl = 1;
+                sh.pid[slot][ly + 1][lx + 1] = L.owner[s];
+            } else if (inside) {
+#pragma unroll
+                for (int i = 0; i < Q; i++) {
+                    r0 += ld_pop(&sh.buf[b][i][ly + 1][lx + TG::PAD], pop_shift<S, C>(L, 0, i));
+                    r1 += ld_pop(&sh.buf[b][Q + i][ly + 1][lx + TG::PAD], pop_shift<S, C>(L, 1, i));
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < Q; i++) {
+                    r0 += ld_pop(fg + ((long long)i) * L.pstride + s, pop_shift<S, C>(L, 0, i));
+                    r1 += ld_pop(fg + ((long long)(Q + i)) * L.pstride + s, pop_shift<S, C>(L, 1, i));
+                }
+            }
+            sh.psi[slot][0][ly + 1][lx + 1] = r0;
+            sh.psi[slot][1][ly + 1][lx + 1] = r1;
+            sh.sol[slot][ly + 1][lx + 1] = sl;
+        }
+    };
+
+    issue(z0 - 1);
+    issue(z0);
+    issue(z0 + 1);
+    wait(z0 - 1);
+    fill(z0 - 1, 0);
+    __syncthreads();
+    if (!sh.abort) issue(z0 + 2);
+    wait(z0);
+    fill(z0, 1);
+    int lo = 0, mid = 1, hi = 2;
+    for (int z = z0; z < z1; z++) {
+        wait(z + 1);
+        fill(z + 1, hi);
+        __syncthreads();
+        if (sh.abort) break;
+        if (act && sh.sol[mid][ty + 1][tx + 1] == 0) {
+            int sl[3] = {lo, mid, hi};
+            int b = buf_of(z);
+            // own populations, moments from the shared copy
+            OwnSite<PREC> m;
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                C r = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+                for (int i = 0; i < Q; i++) {
+                    C v = ld_pop(&sh.buf[b][k * Q + i][ty + 1][tx + TG::PAD], pop_shift<S, C>(L, k, i));
+                    r += v;
+                    if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
+                    if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
+                    if (cz(i) > 0) jz += v; else if (cz(i) < 0) jz -= v;
+                }
+                m.rho[k] = r;
+                m.j[k][0] = jx; m.j[k][1] = jy; m.j[k][2] = jz;
+            }
+            collide_site<PREC>(L, sh, sl, x0 + tx, y0 + ty, z, m,
+                               [&](int q) { return &sh.buf[b][q][ty + 1][tx + TG::PAD]; });
+        }
+        __syncthreads();
+        issue(z + 3);
+        int t = lo; lo = mid; mid = hi; hi = t;
+    }
+    if (sh.abort) {
+        // record the timeout, then wait (bounded) for the copies still in flight
+        if (tid == 0) atomicOr(L.flags, FLAG_TIMEOUT);
+        for (int b = 0; b < TNB; b++)
+            if ((pending >> b) & 1u) mbar_wait_bounded(smem_u32(&sh.mbar[b]), (phase >> b) & 1u);
     }
 }
 
@@ -555,6 +782,43 @@ int launch_wall_psi(const Lattice& L, int prec, cudaStream_t st) {
     dim3 g((unsigned)((L.nx + 127) / 128), (unsigned)L.ny, 2);
     if (prec == LB_FP64) k_wall_psi<double><<<g, 128, 0, st>>>(L);
     else k_wall_psi<float><<<g, 128, 0, st>>>(L);
+    return 1;
+}
+
+size_t fused_tma_smem(int prec) {
+    if (prec == LB_FP32) return sizeof(TmaShared<LB_FP32>) + 128;
+    if (prec == LB_FP16) return sizeof(TmaShared<LB_FP16>) + 128;
+    return 0;
+}
+
+int fused_tma_box_x(int prec) {
+    return prec == LB_FP32 ? TmaGeom<LB_FP32>::BXT : (prec == LB_FP16 ? TmaGeom<LB_FP16>::BXT : 0);
+}
+
+int launch_fluid_step_tma(const Lattice& L, int prec, const void* tmap, cudaStream_t st) {
+    int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + FTY - 1) / FTY);
+    // one block per SM: z chunks so that the grid is several waves deep
+    int zc = (int)((long long)L.nz * tiles / (152 * 6));
+    zc = zc < 4 ? 4 : zc;
+    zc = zc > L.nz ? L.nz : zc;
+    dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + FTY - 1) / FTY, (L.nz + zc - 1) / zc);
+    const CUtensorMap& tm = *(const CUtensorMap*)tmap;
+    static bool attr_set[3] = {false, false, false};
+    if (prec == LB_FP32) {
+        if (!attr_set[prec]) {
+            cudaFuncSetAttribute(k_fused_tma<LB_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fused_tma_smem(prec));
+            attr_set[prec] = true;
+        }
+        k_fused_tma<LB_FP32><<<grid, dim3(FTX, FTY), fused_tma_smem(prec), st>>>(L, zc, tm);
+    } else {
+        if (!attr_set[prec]) {
+            cudaFuncSetAttribute(k_fused_tma<LB_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fused_tma_smem(prec));
+            attr_set[prec] = true;
+        }
+        k_fused_tma<LB_FP16><<<grid, dim3(FTX, FTY), fused_tma_smem(prec), st>>>(L, zc, tm);
+    }
     return 1;
 }
 

@@ -82,7 +82,7 @@ struct Lattice {
     lb_params P;
 };
 
-enum { FLAG_NONFINITE = 1, FLAG_OVERLAP = 2 };
+enum { FLAG_NONFINITE = 1, FLAG_OVERLAP = 2, FLAG_TIMEOUT = 4 };
 
 // ------------------------------------------------- compensated FP64 sums
 struct NSum {
@@ -243,6 +243,9 @@ struct CSum {
 // kernel launchers (each returns the number of kernels it launched)
 int launch_init_fields(const Lattice& L, int prec, const double* stage, cudaStream_t st);
 int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st);
+size_t fused_tma_smem(int prec);
+int fused_tma_box_x(int prec);
+int launch_fluid_step_tma(const Lattice& L, int prec, const void* tmap, cudaStream_t st);
 int launch_shell_density(const Lattice& L, int prec, cudaStream_t st);
 int launch_density(const Lattice& L, int prec, cudaStream_t st);
 int launch_wall_psi(const Lattice& L, int prec, cudaStream_t st);

@@ -125,14 +125,18 @@ def test_reduced_precision_small_workload(prec, tol):
 
 
 @pytest.mark.parametrize("prec,tol,tol_u", [("fp64", 1e-12, 1e-12), ("fp32", 1e-5, 1e-5), ("fp16", 1e-3, 2e-3)])
-def test_sheared_walls_with_particles(prec, tol, tol_u):
+@pytest.mark.parametrize("tma", ["1", "0"])
+def test_sheared_walls_with_particles(prec, tol, tol_u, tma, monkeypatch):
     """Walls at z = -1/2, nz - 1/2 moving at -/+0.05 (the confined shear
     workload's boundary), four particles, 100 steps: velocities are O(0.05)
-    here and are compared relative to themselves.  FP16 deviation storage
+    here and are compared relative to themselves.  Both fused-kernel variants
+    (plain loads by default, TMA-staged tiles with LBGB_FUSED_TMA=1) are checked.
+    FP16 deviation storage
     rounds each population to 11 significant bits of f_i - w_i rho0; next to
     the sheared walls (|u| = 0.05) this leaves a velocity error of about 1.1e-3
     of max |u| after 100 steps (5e-5 of the lattice speed), so the FP16
     velocity bound here is 2e-3 relative to max |u|."""
+    monkeypatch.setenv("LBGB_FUSED_TMA", tma)
     shape = (32, 21, 23)
     w = workload("shear512")
     params = dict(w.params, side_wall_d=6.5)

@@ -111,6 +111,80 @@ __device__ __forceinline__ void for_box(const Lattice& L, const PGeo<C>& g, Fn&&
     }
 }
 
+// Visit the box points of particle p whose distance from the centre lies in
+// [R + lo, R + hi), with the work packed onto consecutive threads (used by
+// the kernels whose per-point work is heavy; the remap kernels, whose work is
+// a few loads per point, scan the box directly): the box is
+// scanned 128 points at a time, the points in the shell are appended to a
+// shared list in box order (warp ballots, warps in order), and whenever 128
+// are queued (and at the end) each thread takes one.  A thin shell fills
+// about a sixth of the box, so without packing most lanes of a warp would
+// idle through the per-point work.  The assignment of points to threads
+// depends only on the geometry, so per-thread partial sums are reproducible.
+template <typename C, typename Fn>
+__device__ __forceinline__ void for_shell(const Lattice& L, const PGeo<C>& g, float lo, float hi, Fn&& fn) {
+    __shared__ int list[2 * PB];
+    __shared__ int wcnt[PB / 32];
+    __shared__ int count;
+    const int tid = threadIdx.y * BXP + threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ex = g.ext[0], exy = g.ext[0] * g.ext[1], total = exy * g.ext[2];
+    auto decode = [&](int t, int& X, int& Y, int& Z, int& a, int& b, int& c, long long& s, C (&d)[3]) -> bool {
+        a = g.lo[0] + t % ex;
+        b = g.lo[1] + (t / ex) % g.ext[1];
+        c = g.lo[2] + t / exy;
+        if (!L.per[2] && (c < 0 || c >= L.nz)) return false;
+        X = a < 0 ? a + L.nx : (a >= L.nx ? a - L.nx : a);
+        Y = b < 0 ? b + L.ny : (b >= L.ny ? b - L.ny : b);
+        Z = c < 0 ? c + L.nz : (c >= L.nz ? c - L.nz : c);
+        s = (long long)X + (long long)L.nx * ((long long)Y + (long long)L.ny * Z);
+        d[0] = C(a - g.ip[0]) - g.fr[0];
+        d[1] = C(b - g.ip[1]) - g.fr[1];
+        d[2] = C(c - g.ip[2]) - g.fr[2];
+        return true;
+    };
+    if (tid == 0) count = 0;
+    __syncthreads();
+    for (int base = 0; base < total; base += PB) {
+        int t = base + tid;
+        bool act = false;
+        if (t < total) {
+            int X, Y, Z, a, b, c;
+            long long s;
+            C d[3];
+            act = decode(t, X, Y, Z, a, b, c, s, d) && in_shell<C>(g, d, lo, hi);
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, act);
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int off = count, tot = 0;
+        for (int w = 0; w < PB / 32; w++) {
+            if (w < warp) off += wcnt[w];
+            tot += wcnt[w];
+        }
+        if (act) list[off + __popc(bal & ((1u << lane) - 1u))] = t;
+        __syncthreads();
+        if (tid == 0) count += tot;
+        __syncthreads();
+        bool last = base + PB >= total;
+        while (count >= PB || (last && count > 0)) {
+            int n = count < PB ? count : PB;
+            if (tid < n) {
+                int X, Y, Z, a, b, c;
+                long long s;
+                C d[3];
+                decode(list[tid], X, Y, Z, a, b, c, s, d);
+                fn(X, Y, Z, s, a, b, c, d);
+            }
+            __syncthreads();
+            int rest = count - n;
+            if (tid < rest) list[tid] = list[n + tid];
+            __syncthreads();
+            if (tid == 0) count = rest;
+            __syncthreads();
+        }
+    }
+}
+
 template <typename C>
 __device__ __forceinline__ void crs(const C (&a)[3], const C (&b)[3], C (&o)[3]) {
     o[0] = a[1] * b[2] - a[2] * b[1];
@@ -370,8 +444,7 @@ __global__ void __launch_bounds__(PB) k_virtual(Lattice L, int store_terms) {
     PGeo<C> g = pgeo<C>(L, p, 1.5);
     C* psi = (C*)L.psi;
     const S* f = (const S*)L.f_cur;
-    for_box<C>(L, g, [&](int, int, int, long long s, int, int, int, const C (&d)[3]) {
-        if (!in_shell<C>(g, d, -0.01f, 1.45f)) return;
+    for_shell<C>(L, g, -0.01f, 1.45f, [&](int, int, int, long long s, int, int, int, const C (&)[3]) {
         if (L.mask[s]) return;
         C r0 = 0, r1 = 0;
 #pragma unroll
@@ -386,9 +459,8 @@ __global__ void __launch_bounds__(PB) k_virtual(Lattice L, int store_terms) {
     CSum<C> acc[6];
     zero(acc);
     const C G = C(L.P.G), z0 = C(1) + C(L.P.zeta[0]), z1 = C(1) + C(L.P.zeta[1]);
-    for_box<C>(L, g, [&](int X, int Y, int Z, long long s, int, int, int, const C (&d)[3]) {
-        // a node of p with a fluid neighbour lies within sqrt(2) of the surface
-        if (!in_shell<C>(g, d, -1.5f, 0.01f)) return;
+    // a node of p with a fluid neighbour lies within sqrt(2) of the surface
+    for_shell<C>(L, g, -1.5f, 0.01f, [&](int X, int Y, int Z, long long s, int, int, int, const C (&d)[3]) {
         if (L.owner[s] != p) return;
         SiteNbr n = site_nbr(L, X, Y, Z);
         int m[Q];
@@ -449,9 +521,8 @@ __global__ void __launch_bounds__(PB) k_links(Lattice L) {
     const S* fn = (const S*)L.f_nxt;
     CSum<C> acc[6];
     zero(acc);
-    for_box<C>(L, g, [&](int X, int Y, int Z, long long s, int, int, int, const C (&d)[3]) {
-        // a fluid node linked to p lies within sqrt(2) outside the surface
-        if (!in_shell<C>(g, d, -0.01f, 1.45f)) return;
+    // a fluid node linked to p lies within sqrt(2) outside the surface
+    for_shell<C>(L, g, -0.01f, 1.45f, [&](int X, int Y, int Z, long long s, int, int, int, const C (&d)[3]) {
         if (L.mask[s]) return;
         SiteNbr n = site_nbr(L, X, Y, Z);
         int m[Q];

@@ -1,0 +1,108 @@
+"""Physics pins of the FP64 oracle that need a few thousand steps (CPU, about
+40 s together): the Laplace law for a Shan-Chen droplet (Eqs. 11-12) and the
+Hasimoto drag on a periodic array of fixed spheres (Ladd bounce-back,
+Eqs. 17-19, 22)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+
+
+def make(shape, maxc=1, **params):
+    o = Oracle(*shape, maxc)
+    o.set_params(**params)
+    return o
+
+
+def cylinder_drop(R, G=1.1, rho_tot=2.0, n=40, steps=3000):
+    """A B-rich cylinder (axis z) of radius R in an A-rich matrix, periodic
+    n x n x 4 box; returns (pressure jump, effective radius)."""
+    shape = (n, n, 4)
+    N = n * n * 4
+    s = np.arange(N)
+    x, y = s % n, (s // n) % n
+    r = np.sqrt((x - n / 2 + 0.5) ** 2 + (y - n / 2 + 0.5) ** 2)
+    prof = 0.5 * (1 - np.tanh((r - R) / 1.5))
+    rb = rho_tot * (0.03 + 0.94 * prof)
+    o = make(shape, G=G, rho0=(rho_tot / 2, rho_tot / 2))
+    o.init_fields(rho_tot - rb, rb)
+    o.step(steps)
+    a, b, _ = o.get_fields()
+    p = (a + b) / 3 + G * a * b / 3  # Eq. 12
+    inner, outer = r < R / 3, r > n / 2 - 2
+    dp = p[inner].mean() - p[outer].mean()
+    b_in, b_out = b[inner].mean(), b[outer].mean()
+    area = (b.sum() / 4 - b_out * n * n) / (b_in - b_out)
+    return dp, math.sqrt(area / math.pi)
+
+
+@pytest.mark.slow
+def test_laplace_law_cylinder():
+    """Eq. 12 with a demixing coupling (G rho = 2.2 > 2 - 1/tau = 1): the
+    pressure jump across a cylindrical interface is sigma / R (the 2-D Laplace
+    law): linear in 1/R through the origin."""
+    res = [cylinder_drop(R) for R in (6.0, 9.0, 12.0)]
+    dp = np.array([v[0] for v in res])
+    Re = np.array([v[1] for v in res])
+    A = np.vstack([1 / Re, np.ones_like(Re)]).T
+    (sigma, icpt), *_ = np.linalg.lstsq(A, dp, rcond=None)
+    pred = A @ np.array([sigma, icpt])
+    r2 = 1 - np.sum((dp - pred) ** 2) / np.sum((dp - dp.mean()) ** 2)
+    assert sigma > 0 and r2 > 0.9995, (sigma, r2)
+    assert abs(icpt) < 0.05 * dp.min(), (icpt, dp)
+    # the jump times the radius is the same tension for every droplet
+    assert np.ptp(dp * Re) < 0.05 * np.mean(dp * Re)
+
+
+def hasimoto_K(c):
+    """Hasimoto (1959) / Sangani-Acrivos series for the drag coefficient of a
+    simple cubic array of spheres at volume fraction c."""
+    c3 = c ** (1.0 / 3.0)
+    return 1.0 / (1 - 1.7601 * c3 + c - 1.5593 * c * c + 3.9799 * c ** (8 / 3) - 3.0734 * c ** (10 / 3))
+
+
+def fixed_sphere_drag(L, R, g=1e-5, tau=1.0):
+    shape = (L, L, L)
+    N = L ** 3
+    o = make(shape, tau=(tau, tau), G=0.0, body_force=(g, 0.0, 0.0))
+    o.init_fields(np.full(N, 0.5), np.full(N, 0.5))
+    o.add_colloids([[L / 2 - 0.37, L / 2 - 0.43, L / 2 - 0.39]], R, math.inf)
+    # the converged flow keeps a small period-2 (staggered) component at
+    # tau = 1: compare two-step averages
+    prev = None
+    for _ in range(200):
+        o.step(99)
+        o.step(1)
+        F1 = o.term("F_liq")[0]
+        o.step(1)
+        F = 0.5 * (F1 + o.term("F_liq")[0])
+        if prev is not None and np.all(np.abs(F - prev) <= 1e-10 * abs(F[0])):
+            break
+        prev = F.copy()
+    t = o.totals()
+    M = t[0] + t[1]
+    U = t[5] / M  # mean interstitial velocity of the fluid (half-force corrected)
+    return F, g * M, U, L ** 3
+
+
+@pytest.mark.slow
+def test_hasimoto_drag_fixed_sphere_array():
+    """A fixed sphere in a periodic cube under a body force g: at steady state
+    the bounce-back link forces (Eqs. 19, 22) balance the force on the fluid
+    exactly, F = g M (averaged over two steps); the drag coefficient K = F / (6 pi eta R U_s) with the
+    superficial velocity U_s = (1 - c) U follows Hasimoto's series for a
+    simple cubic array within the staircase error of the sphere (a few %,
+    shrinking with R at fixed c)."""
+    ratios = []
+    for L, R in ((12, 3.0), (16, 4.0)):
+        F, gM, U, V = fixed_sphere_drag(L, R)
+        assert abs(F[0] - gM) < 1e-9 * gM
+        assert abs(F[1]) < 1e-3 * gM and abs(F[2]) < 1e-3 * gM
+        c = 4.0 / 3.0 * math.pi * R ** 3 / V
+        nu = (1.0 - 0.5) / 3.0
+        K = F[0] / (6 * math.pi * nu * 1.0 * R * U * (1 - c))
+        ratios.append(K / hasimoto_K(c))
+    assert all(0.9 < q < 1.05 for q in ratios), ratios
+    assert abs(1 - ratios[1]) <= abs(1 - ratios[0]) + 0.005  # converging with R

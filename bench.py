@@ -199,6 +199,26 @@ def adjoint_timing(dev, torch, steps=500):
             "grad_finite": bool(np.all(np.isfinite(grads)))}
 
 
+def max_over_ranks(v, world, device=None):
+    """Largest value over the ranks of the default process group (every rank
+    runs an independent replica; the slowest one sets the job time)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_mlups(ms_local, n_sites, steps, world, device=None):
+    """Whole-job MLUPS of `world` replicas of n_sites sites each: all sites
+    updated `steps` times in the slowest replica's time."""
+    ms = max_over_ranks(ms_local, world, device)
+    return world * n_sites * steps / (ms / 1e3) / 1e6, ms
+
+
 def time_steps(lat, steps, torch):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -244,13 +264,6 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     w = workload(args.workload, tuple(args.shape) if args.shape else None)
     a, b = w.densities()
     col = w.colloids()
@@ -271,9 +284,8 @@ def main():
     launches = lat.launch_count() - launches0
     kern_ms, kern_n = lat.profile_read()
     lat.profile(False)
-    ms = max_over_ranks(ms)
+    value, ms = replica_mlups(ms, w.n_sites, args.steps, world, dev)
     ms_step = ms / args.steps
-    value = world * w.n_sites * args.steps / (ms / 1e3) / 1e6
     peak, peak_kind = peaks()
     alg = ALG_BYTES[args.prec] * w.n_sites
     kavg = kern_ms / max(kern_n, 1)
@@ -308,7 +320,7 @@ def main():
     api.lb_get_fields(lat.h, oa, ob, ou)
     api.lb_get_colloids(lat.h, cpos, cvel, None, None, None, None)
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e = {"value": round(world * N * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
            "h2d_bytes_per_step": int((2 * N * 8 + n * 5 * 8) / args.steps),
            "d2h_bytes_per_step": int((5 * N * 8 + n * 6 * 8) / args.steps)}
@@ -327,7 +339,7 @@ def main():
             L2.step(3)
             L2.profile(True)
             barrier()
-            m2 = max_over_ranks(time_steps(L2, steps, torch))
+            m2 = max_over_ranks(time_steps(L2, steps, torch), world, dev)
             km, kn = L2.profile_read()
             kk = km / max(kn, 1)
             forms[prec] = {"mlups": round(world * N * steps / (m2 / 1e3) / 1e6, 1), "steps": steps,

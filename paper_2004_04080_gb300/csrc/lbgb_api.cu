@@ -254,6 +254,10 @@ int lb_set_params(lb_ctx* ctx, const lb_params* p) {
     if (ctx->stepped && p->bc[2] != ctx->L.P.bc[2])
         return set_err(ctx, LB_ERR_STATE, "boundary conditions cannot change after stepping");
     ctx->L.P = *p;
+    for (int k = 0; k < 2; k++) {
+        ctx->L.inv_tau[k] = 1.0 / p->tau[k];
+        ctx->L.inv_nu[k] = 3.0 / (p->tau[k] - 0.5);
+    }
     ctx->L.per[0] = 1;
     ctx->L.per[1] = 1;
     ctx->L.per[2] = p->bc[2];

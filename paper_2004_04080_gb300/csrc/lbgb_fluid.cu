@@ -8,6 +8,7 @@
 // reads f(t) at each site, collides locally and pushes f*(t) to the
 // neighbours, writing f(t+1) into the second buffer.
 #include <cuda.h>
+#include <stddef.h>
 
 #include "lbgb_internal.cuh"
 
@@ -297,7 +298,7 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
 
 // collide and push the own site of plane z (slots: below, here, above); the
 // populations are in the stage, rho and j in `m`
-template <int PREC, typename SH, typename PopFn>
+template <int PREC, bool UNIT, typename SH, typename PopFn>
 __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int (&sl)[3], int x, int y, int z,
                                              const OwnSite<PREC>& m, PopFn pop) {
     typedef typename Prec<PREC>::S S;
@@ -330,9 +331,11 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
     C us[2][3];
     C tiny = sizeof(C) == 8 ? C(1e-300) : C(1e-30);
 #pragma unroll
-    for (int k = 0; k < 2; k++)
+    for (int k = 0; k < 2; k++) {
+        C ir = m.rho[k] > tiny ? C(1) / m.rho[k] : C(0);
 #pragma unroll
-        for (int d = 0; d < 3; d++) us[k][d] = m.rho[k] > tiny ? u[d] + F[k][d] / m.rho[k] : u[d];
+        for (int d = 0; d < 3; d++) us[k][d] = u[d] + F[k][d] * ir;
+    }
     C uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     C uus[2] = {us[0][0] * us[0][0] + us[0][1] * us[0][1] + us[0][2] * us[0][2],
                 us[1][0] * us[1][0] + us[1][1] * us[1][1] + us[1][2] * us[1][2]};
@@ -346,10 +349,14 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
     for (int i = 0; i < Q; i++) {
         C fs[2];
 #pragma unroll
-        for (int k = 0; k < 2; k++)
-            fs[k] = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
-                                feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
-                    feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
+        for (int k = 0; k < 2; k++) {
+            if (UNIT)  // omega = 1 exactly: Eq. 16 is f* = f^eq(rho^k, u + F^k/rho^k)
+                fs[k] = feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
+            else
+                fs[k] = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
+                                    feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
+                        feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
+        }
         uint8_t nb = i == 0 ? 0 : sh.sol[sl[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)];
         if (nb == 0) {
             long long q = i == 0 ? s : nbr_index(L, n, i);
@@ -377,8 +384,8 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
     }
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : 2)) k_fused(Lattice L, int zc) {
+template <int PREC, bool UNIT>
+__global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k_fused(Lattice L, int zc) {
     typedef typename Prec<PREC>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FusedShared<PREC>& sh = *reinterpret_cast<FusedShared<PREC>*>(smem_raw);
@@ -391,7 +398,8 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : 2)) k_fused(Lattic
     // prologue: plane z0-1 into slot 0, plane z0 into slot 1 (own site staged)
     fill_plane<PREC>(L, sh, 0, z0 - 1, x0, y0, W, H, false, nxt);
     bool have = fill_plane<PREC>(L, sh, 1, z0, x0, y0, W, H, true, nxt);
-    if (have)
+    // the populations themselves are needed again only for omega != 1
+    if (!UNIT && have)
 #pragma unroll
         for (int q = 0; q < 2 * Q; q++) sh.stage[q][tid] = nxt.raw[q];
     cur.rho[0] = nxt.rho[0]; cur.rho[1] = nxt.rho[1];
@@ -404,10 +412,10 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : 2)) k_fused(Lattic
         __syncthreads();
         if (act && sh.sol[mid][ty + 1][tx + 1] == 0) {
             int sl[3] = {lo, mid, hi};
-            collide_site<PREC>(L, sh, sl, x0 + tx, y0 + ty, z, cur, [&](int q) { return &sh.stage[q][tid]; });
+            collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, cur, [&](int q) { return &sh.stage[q][tid]; });
         }
         __syncthreads();
-        if (have_n)
+        if (!UNIT && have_n)
 #pragma unroll
             for (int q = 0; q < 2 * Q; q++) sh.stage[q][tid] = nxt.raw[q];
         cur.rho[0] = nxt.rho[0]; cur.rho[1] = nxt.rho[1];
@@ -620,8 +628,8 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_tma(Lattice L, int zc, const _
                 m.rho[k] = r;
                 m.j[k][0] = jx; m.j[k][1] = jy; m.j[k][2] = jz;
             }
-            collide_site<PREC>(L, sh, sl, x0 + tx, y0 + ty, z, m,
-                               [&](int q) { return &sh.buf[b][q][ty + 1][tx + TG::PAD]; });
+            collide_site<PREC, false>(L, sh, sl, x0 + tx, y0 + ty, z, m,
+                                      [&](int q) { return &sh.buf[b][q][ty + 1][tx + TG::PAD]; });
         }
         __syncthreads();
         issue(z + 3);
@@ -829,13 +837,25 @@ int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st) {
     zc = zc < 4 ? 4 : zc;
     zc = zc > L.nz ? L.nz : zc;
     dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + FTY - 1) / FTY, (L.nz + zc - 1) / zc);
-    static bool attr_set[3] = {false, false, false};
-    if (!attr_set[prec]) {
-        DISPATCH(prec, (cudaFuncSetAttribute(k_fused<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(FusedShared<P>))));
-        attr_set[prec] = true;
+    static bool attr_set[3][2] = {{false, false}, {false, false}, {false, false}};
+    // relaxation frequency exactly 1 (tau_A = tau_B = 1): the collision needs
+    // no non-equilibrium part, a separate instantiation keeps the code small
+    bool unit = L.P.tau[0] == 1.0 && L.P.tau[1] == 1.0;
+    if (!attr_set[prec][unit]) {
+        if (unit) {
+            DISPATCH(prec, (cudaFuncSetAttribute(k_fused<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)offsetof(FusedShared<P>, stage))));
+        } else {
+            DISPATCH(prec, (cudaFuncSetAttribute(k_fused<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sizeof(FusedShared<P>))));
+        }
+        attr_set[prec][unit] = true;
     }
-    DISPATCH(prec, (k_fused<P><<<grid, dim3(FTX, FTY), sizeof(FusedShared<P>), st>>>(L, zc)));
+    if (unit) {
+        DISPATCH(prec, (k_fused<P, true><<<grid, dim3(FTX, FTY), offsetof(FusedShared<P>, stage), st>>>(L, zc)));
+    } else {
+        DISPATCH(prec, (k_fused<P, false><<<grid, dim3(FTX, FTY), sizeof(FusedShared<P>), st>>>(L, zc)));
+    }
     return 1;
 }
 

@@ -75,6 +75,8 @@ struct Lattice {
     int* prev_valid;
     double *Fd, *Td, *Fc, *Tc, *Fs, *Ts, *Fpair, *Ftot, *Ttot;
     double rmax;       // largest particle radius
+    double inv_tau[2]; // 1/tau_k
+    double inv_nu[2];  // 1/nu_k, nu_k = (tau_k - 1/2)/3
     int* ipos;         // [n][3] floor of the position (FP32 geometry origin)
     float* fsnap;      // [n][9] position - ipos, v(t-1/2), omega(t-1/2) in FP32
     double* red;       // reduction partials
@@ -217,15 +219,22 @@ __device__ __forceinline__ void sc_force(const Lattice& L, const SiteNbr& n, con
 template <typename C>
 __device__ __forceinline__ void mixture(const Lattice& L, const C (&rho)[2], const C (&j)[2][3],
                                         C (&u)[3], C& om) {
-    C w0 = C(1) / C(L.P.tau[0]), w1 = C(1) / C(L.P.tau[1]);
-    C den = w0 * rho[0] + w1 * rho[1];
-#pragma unroll
-    for (int d = 0; d < 3; d++) u[d] = (w0 * j[0][d] + w1 * j[1][d]) / den;
-    C nu0 = (C(L.P.tau[0]) - C(0.5)) / C(3), nu1 = (C(L.P.tau[1]) - C(0.5)) / C(3);
     C rt = rho[0] + rho[1];
-    C inv_nu = (rho[0] / rt) / nu0 + (rho[1] / rt) / nu1;
-    C nubar = C(1) / inv_nu;
-    om = C(1) / (C(3) * nubar + C(0.5));
+    if (L.P.tau[0] == L.P.tau[1]) {
+        // equal relaxation times: Eq. 14 is sum_k j^k / rho and 1/nubar = 1/nu,
+        // so the mixture frequency is exactly 1/tau
+        C ir = C(1) / rt;
+#pragma unroll
+        for (int d = 0; d < 3; d++) u[d] = (j[0][d] + j[1][d]) * ir;
+        om = C(L.inv_tau[0]);
+        return;
+    }
+    C w0 = C(L.inv_tau[0]), w1 = C(L.inv_tau[1]);
+    C iden = C(1) / (w0 * rho[0] + w1 * rho[1]);
+#pragma unroll
+    for (int d = 0; d < 3; d++) u[d] = (w0 * j[0][d] + w1 * j[1][d]) * iden;
+    C q = (rho[0] * C(L.inv_nu[0]) + rho[1] * C(L.inv_nu[1])) / rt;  // 1/nubar
+    om = q / (C(3) + C(0.5) * q);                                     // 1/(3 nubar + 1/2)
 }
 
 // Neumaier sum in the compute type (per-thread partials before the FP64 merge)

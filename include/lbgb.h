@@ -88,7 +88,8 @@ int lb_workspace_bytes(int nx, int ny, int nz, int prec, int max_colloids, size_
 /* Create a context on the calling thread's current CUDA device.
  * d_workspace: device pointer, 256-byte aligned, >= lb_workspace_bytes bytes,
  * owned by the caller.  cuda_stream: a cudaStream_t or NULL.
- * Lattice sides must be >= 4; nx must be a multiple of 4.  With
+ * Lattice sides must be >= 4; nx must be a multiple of 4; nx*ny*nz below
+ * 2^31 - 4096 (LB_ERR_ARG otherwise: sites are indexed in 32 bits).  With
  * LBGB_FUSED_TMA=1 in the environment at lb_create, LB_FP32 (and LB_FP16 with
  * nx a multiple of 8) use a fused lattice kernel that stages its tiles with
  * tensor-memory-accelerator copies instead of the default plain loads. */

@@ -157,6 +157,8 @@ void encode_tensor_maps(lb_ctx* ctx, const Layout& l) {
 
 extern "C" {
 
+static const long long MAX_SITES = (1LL << 31) - 4096;
+
 int lb_workspace_bytes(int nx, int ny, int nz, int prec, int max_colloids, size_t* bytes) {
     if (!bytes || nx < 4 || ny < 4 || nz < 4 || max_colloids < 0) return LB_ERR_ARG;
     if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_FP16) return LB_ERR_ARG;
@@ -170,6 +172,8 @@ int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_worksp
     *out = NULL;
     if (nx < 4 || ny < 4 || nz < 4 || (nx % 4) != 0 || max_colloids < 0) return LB_ERR_ARG;
     if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_FP16) return LB_ERR_ARG;
+    // the lattice kernels index sites with 32-bit integers
+    if ((long long)nx * ny * nz > MAX_SITES) return LB_ERR_ARG;
     if (!d_workspace || ((uintptr_t)d_workspace % ALIGN) != 0) return LB_ERR_ARG;
     Layout l = layout(nx, ny, nz, prec, max_colloids);
     if (bytes < l.total) return LB_ERR_NOMEM;
@@ -371,7 +375,12 @@ int lb_step(lb_ctx* ctx, int nsteps) {
     for (int t = 0; t < nsteps; t++) {
         int n = 0;
         n += launch_remap(L, ctx->prec, s);           // destroy / create (Eqs. 24, 25)
-        n += launch_shell_density(L, ctx->prec, s);    // rho^k near particles / walls (Eq. 6)
+        // rho^k (Eq. 6): of every fluid node when particles need virtual
+        // densities (Eq. 20), else of the planes next to the walls only (the
+        // fused kernel then forms its halo densities itself)
+        L.dense_psi = L.nc > 0;
+        if (L.dense_psi) n += launch_density(L, ctx->prec, s);
+        else n += launch_shell_density(L, ctx->prec, s);
         n += launch_wall_psi(L, ctx->prec, s);         // wall densities
         n += launch_virtual(L, ctx->prec, 1, s);       // Eqs. 20, 21
         bool timed = ctx->prof_on && ctx->prof_n < PROF_MAX;

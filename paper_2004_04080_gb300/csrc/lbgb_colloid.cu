@@ -425,37 +425,18 @@ __device__ __forceinline__ uint32_t nbr_solid(const Lattice& L, const SiteNbr& n
     return bits;
 }
 
-// Two phases per particle p:
-//  1. rho^k of the fluid nodes within sqrt(2) outside its surface (the
-//     boundary nodes: their densities feed Eq. 20 here and the link forces
-//     of Eq. 19 after the lattice step), written to psi;
-//  2. Eq. 20 on each frontier node s of p (a node of p with at least one
-//     fluid neighbour): psi^k(s) = (1 + zeta^k) sum w_i rho^k / sum w_i over
-//     fluid neighbours; and Eq. 21 (repulsive sign):
-//     F_s = -G sum_k psi^k(s) sum w_i rho^kbar(s + c_i) c_i, summed with its
-//     torque.  Every fluid neighbour of a frontier node of p is a boundary
-//     node of p, so phase 2 reads only densities written in phase 1 by the
-//     same block (other blocks may write equal values to shared nodes).
+// Eq. 20 on each frontier node s of particle p (a node of p with at least one
+// fluid neighbour): psi^k(s) = (1 + zeta^k) sum w_i rho^k / sum w_i over the
+// fluid neighbours, and Eq. 21 (repulsive sign):
+// F_s = -G sum_k psi^k(s) sum w_i rho^kbar(s + c_i) c_i, summed with its
+// torque.  The densities rho^k of the fluid nodes are those of the full
+// density pass of this step (k_density).
 template <int PREC>
 __global__ void __launch_bounds__(PB) k_virtual(Lattice L, int store_terms) {
-    typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
     int p = blockIdx.x;
     PGeo<C> g = pgeo<C>(L, p, 1.5);
     C* psi = (C*)L.psi;
-    const S* f = (const S*)L.f_cur;
-    for_shell<C>(L, g, -0.01f, 1.45f, [&](int, int, int, long long s, int, int, int, const C (&)[3]) {
-        if (L.mask[s]) return;
-        C r0 = 0, r1 = 0;
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            r0 += ld_pop(f + ((long long)i) * L.pstride + s, pop_shift<S, C>(L, 0, i));
-            r1 += ld_pop(f + ((long long)(Q + i)) * L.pstride + s, pop_shift<S, C>(L, 1, i));
-        }
-        psi[s] = r0;
-        psi[L.N + s] = r1;
-    });
-    __syncthreads();
     CSum<C> acc[6];
     zero(acc);
     const C G = C(L.P.G), z0 = C(1) + C(L.P.zeta[0]), z1 = C(1) + C(L.P.zeta[1]);

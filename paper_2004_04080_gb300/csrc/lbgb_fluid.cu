@@ -101,37 +101,58 @@ __global__ void k_wall_psi(Lattice L) {
 // c_i) = 0: one U0 per site serves every link of that site into p.  The
 // offset x - r_p is formed from the integer part of r_p and its fractional
 // part, exact in FP64 and accurate to FP32 rounding of a number below 1 in the
-// FP32 forms (which read the FP32 particle snapshot).
+// FP32 forms (which read the FP32 particle snapshot).  The loads
+// (particle_load) and the arithmetic (particle_u0_of) are split so that a
+// caller can issue the loads early.
 template <typename C>
-__device__ __forceinline__ void particle_u0(const Lattice& L, int p, int x, int y, int z, C (&U0)[3]) {
-    int xs[3] = {x, y, z}, Ls[3] = {L.nx, L.ny, L.nz};
-    C rel[3], v[3], w[3];
+struct ParticleRef {
+    int ip[3];
+    C fr[3], v[3], w[3];
+};
+
+template <typename C>
+__device__ __forceinline__ ParticleRef<C> particle_load(const Lattice& L, int p) {
+    ParticleRef<C> r;
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        int ip;
-        C fr;
         if (sizeof(C) == 8) {
-            double r = L.pos[3 * p + d];
-            ip = (int)floor(r);
-            fr = C(r - (double)ip);
-            v[d] = C(L.vel[3 * p + d]);
-            w[d] = C(L.omg[3 * p + d]);
+            double q = __ldg(L.pos + 3 * p + d);
+            r.ip[d] = (int)floor(q);
+            r.fr[d] = C(q - (double)r.ip[d]);
+            r.v[d] = C(__ldg(L.vel + 3 * p + d));
+            r.w[d] = C(__ldg(L.omg + 3 * p + d));
         } else {
-            ip = L.ipos[3 * p + d];
-            fr = C(L.fsnap[9 * p + d]);
-            v[d] = C(L.fsnap[9 * p + 3 + d]);
-            w[d] = C(L.fsnap[9 * p + 6 + d]);
+            r.ip[d] = __ldg(L.ipos + 3 * p + d);
+            r.fr[d] = C(__ldg(L.fsnap + 9 * p + d));
+            r.v[d] = C(__ldg(L.fsnap + 9 * p + 3 + d));
+            r.w[d] = C(__ldg(L.fsnap + 9 * p + 6 + d));
         }
-        int dd = xs[d] - ip;
+    }
+    return r;
+}
+
+template <typename C>
+__device__ __forceinline__ void particle_u0_of(const Lattice& L, const ParticleRef<C>& r, int x, int y, int z,
+                                               C (&U0)[3]) {
+    int xs[3] = {x, y, z}, Ls[3] = {L.nx, L.ny, L.nz};
+    C rel[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        int dd = xs[d] - r.ip[d];
         if (L.per[d]) {
             if (2 * dd > Ls[d]) dd -= Ls[d];
             else if (2 * dd < -Ls[d]) dd += Ls[d];
         }
-        rel[d] = C(dd) - fr;
+        rel[d] = C(dd) - r.fr[d];
     }
-    U0[0] = v[0] + (w[1] * rel[2] - w[2] * rel[1]);
-    U0[1] = v[1] + (w[2] * rel[0] - w[0] * rel[2]);
-    U0[2] = v[2] + (w[0] * rel[1] - w[1] * rel[0]);
+    U0[0] = r.v[0] + (r.w[1] * rel[2] - r.w[2] * rel[1]);
+    U0[1] = r.v[1] + (r.w[2] * rel[0] - r.w[0] * rel[2]);
+    U0[2] = r.v[2] + (r.w[0] * rel[1] - r.w[1] * rel[0]);
+}
+
+template <typename C>
+__device__ __forceinline__ void particle_u0(const Lattice& L, int p, int x, int y, int z, C (&U0)[3]) {
+    particle_u0_of<C>(L, particle_load<C>(L, p), x, y, z, U0);
 }
 
 // ------------------------------------------------------- fused step
@@ -140,11 +161,13 @@ __device__ __forceinline__ void particle_u0(const Lattice& L, int p, int x, int 
 // and marches along z through a chunk of planes.  Per plane it
 //   1. loads the 2 x 19 populations f(t) of its own sites (kept in registers
 //      for the next iteration) and forms rho^k (Eq. 6) and j^k (Eq. 7);
-//   2. forms rho^k of the one-site ring around the tile from the ring's
-//      populations (these loads mostly hit L2: the neighbouring blocks read
-//      the same lines), so the pseudopotential halo needs no separate density
-//      pass; particle nodes contribute their virtual density (Eq. 20) and
-//      wall planes the wall density, both precomputed by small kernels;
+//   2. takes rho^k of the one-site ring around the tile: with particles
+//      present from the full density pass that precedes the virtual
+//      densities (Eq. 20) of the particle nodes; without particles from the
+//      ring's populations (these loads mostly hit L2: the neighbouring blocks
+//      read the same lines), so that no separate density pass is needed.
+//      Particle nodes contribute their virtual density and wall planes the
+//      wall density, both precomputed by small kernels;
 //   3. keeps psi^k of three consecutive planes (tile + ring) in shared
 //      memory, from which the previous plane's Shan-Chen force (Eq. 11) is
 //      taken, then collides it (Eqs. 14-16) and pushes f*(t) to the
@@ -155,20 +178,16 @@ constexpr int RW = FTX + 2, RH = FTY + 2;
 
 // shared state of one block: psi^k and node flags of three planes (tile +
 // ring) and the raw populations of the own sites of the plane being collided
-template <typename C>
-struct PsiRing {
-    C psi[3][2][RH][RW];
-    uint8_t sol[3][RH][RW];  // 0 fluid, 1 particle node, 2 beyond a wall
-    int pid[3][RH][RW];      // owning particle of a particle node
-};
+// node codes of the shared planes: a fluid node, a node beyond a wall, or
+// the index (>= 0) of the particle that owns a particle node
+constexpr int ND_FLUID = -1, ND_WALL = -2;
 
 template <int PREC>
 struct FusedShared {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
     C psi[3][2][RH][RW];
-    uint8_t sol[3][RH][RW];  // 0 fluid, 1 particle node, 2 beyond a wall
-    int pid[3][RH][RW];      // owning particle of a particle node
+    int nd[3][RH][RW];
     S stage[2 * Q][FNT];
 };
 
@@ -226,7 +245,7 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
             long long w = (long long)X + (long long)L.nx * Y;
             sh.psi[slot][0][ly + 1][lx + 1] = pw[(side * 2 + 0) * nxy + w];
             sh.psi[slot][1][ly + 1][lx + 1] = pw[(side * 2 + 1) * nxy + w];
-            sh.sol[slot][ly + 1][lx + 1] = 2;
+            sh.nd[slot][ly + 1][lx + 1] = ND_WALL;
         }
         return false;
     }
@@ -237,8 +256,18 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
         if (L.mask[s]) {
             sh.psi[slot][0][ty + 1][tx + 1] = psi[s];
             sh.psi[slot][1][ty + 1][tx + 1] = psi[L.N + s];
-            sh.sol[slot][ty + 1][tx + 1] = 1;
-            sh.pid[slot][ty + 1][tx + 1] = L.owner[s];
+            sh.nd[slot][ty + 1][tx + 1] = L.owner[s];
+            // a particle node collides on finite placeholder moments (its
+            // stores write the rest equilibrium)
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                own.rho[k] = C(L.P.rho0[k]);
+                own.j[k][0] = own.j[k][1] = own.j[k][2] = C(0);
+            }
+            if (want_own)
+#pragma unroll
+                for (int q = 0; q < 2 * Q; q++) own.raw[q] = S(0);
+            loaded = want_own;
         } else {
             if (want_own) {
 #pragma unroll
@@ -257,7 +286,7 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
             }
             sh.psi[slot][0][ty + 1][tx + 1] = own.rho[0];
             sh.psi[slot][1][ty + 1][tx + 1] = own.rho[1];
-            sh.sol[slot][ty + 1][tx + 1] = 0;
+            sh.nd[slot][ty + 1][tx + 1] = ND_FLUID;
         }
     }
     // ring: rows ly = -1 and ly = H (lx = -1..W), columns lx = -1 and lx = W (ly = 0..H-1)
@@ -273,12 +302,15 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
         Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
         long long s = (long long)X + (long long)L.nx * Y + zoff;
         C r0, r1;
-        uint8_t sl;
+        int nd;
         if (L.mask[s]) {
             r0 = psi[s];
             r1 = psi[L.N + s];
-            sl = 1;
-            sh.pid[slot][ly + 1][lx + 1] = L.owner[s];
+            nd = L.owner[s];
+        } else if (L.dense_psi) {
+            r0 = psi[s];
+            r1 = psi[L.N + s];
+            nd = ND_FLUID;
         } else {
             r0 = 0;
             r1 = 0;
@@ -287,23 +319,57 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
                 r0 += ld_pop(f + ((long long)i) * L.pstride + s, pop_shift<S, C>(L, 0, i));
                 r1 += ld_pop(f + ((long long)(Q + i)) * L.pstride + s, pop_shift<S, C>(L, 1, i));
             }
-            sl = 0;
+            nd = ND_FLUID;
         }
         sh.psi[slot][0][ly + 1][lx + 1] = r0;
         sh.psi[slot][1][ly + 1][lx + 1] = r1;
-        sh.sol[slot][ly + 1][lx + 1] = sl;
+        sh.nd[slot][ly + 1][lx + 1] = nd;
     }
     return loaded;
 }
 
-// collide and push the own site of plane z (slots: below, here, above); the
-// populations are in the stage, rho and j in `m`
+// Collide and push the own site of plane z (slots: below, here, above); the
+// populations are in the stage, rho and j in `m`.  A particle node of the
+// tile (`solid`) runs the same instructions and stores the rest equilibrium
+// w_i rho0^k into its own slots of f(t+1) instead: no link pushes into a
+// particle node, so without this its slots would stay unwritten and the
+// 32-byte sectors they share with fluid nodes along every row through a
+// particle would be written only in part (each then costs a DRAM read to
+// merge); sharing the store instructions with the fluid lanes of the warp
+// keeps the number of store requests that of a fluid warp.  The values are
+// never read: a node released by a particle is refilled (Eq. 25) before it
+// streams.  (Its arithmetic uses finite moments: the populations of a
+// particle node are the stored rest equilibrium.)
 template <int PREC, bool UNIT, typename SH, typename PopFn>
 __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int (&sl)[3], int x, int y, int z,
-                                             const OwnSite<PREC>& m, PopFn pop) {
+                                             const OwnSite<PREC>& m, bool solid, PopFn pop) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
     int tx = threadIdx.x, ty = threadIdx.y;
+    // Links that bounce back (Eqs. 9, 17, 18): their neighbour is a particle
+    // node or lies beyond a wall.  Nearly every warp holds such a site, so the
+    // store of each link selects its destination (the neighbour's slot i, or
+    // the own slot opp(i) with the wall-velocity term) instead of branching.
+    // The particle of the first particle link gives U0 (its loads are issued
+    // first, to overlap the force and collision arithmetic); a site next to
+    // two particles rewrites the links into the second one afterwards.
+    unsigned bb = 0;
+    int p0 = -1;
+    bool multi = false;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        int nd = sh.nd[sl[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)];
+        bb |= (unsigned)(nd != ND_FLUID) << i;
+        if (nd >= 0) {
+            multi |= p0 >= 0 && nd != p0;
+            p0 = p0 < 0 ? nd : p0;
+        }
+    }
+    bb = solid ? 0u : bb;
+    multi = multi && !solid;
+    // (particle 0 stands in when no link reaches a particle: its record
+    // exists whenever the lattice has room for particles, and U0 is unused)
+    const ParticleRef<C> pref = particle_load<C>(L, p0 >= 0 ? p0 : 0);
     // Eq. 11 (repulsive sign) + body force from the shared-memory psi planes
     C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};
 #pragma unroll
@@ -324,7 +390,7 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
         F[0][d] = -G * m.rho[0] * sB[d] + m.rho[0] * g;
         F[1][d] = -G * m.rho[1] * sA[d] + m.rho[1] * g;
     }
-    if (!(m.rho[0] >= C(0) && m.rho[1] >= C(0) && m.rho[0] < C(1e30) && m.rho[1] < C(1e30)))
+    if (!solid && !(m.rho[0] >= C(0) && m.rho[1] >= C(0) && m.rho[0] < C(1e30) && m.rho[1] < C(1e30)))
         atomicOr(L.flags, FLAG_NONFINITE);
     C u[3], om;
     mixture<C>(L, m.rho, m.j, u, om);
@@ -340,46 +406,104 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
     C uus[2] = {us[0][0] * us[0][0] + us[0][1] * us[0][1] + us[0][2] * us[0][2],
                 us[1][0] * us[1][0] + us[1][1] * us[1][1] + us[1][2] * us[1][2]};
     C one_m_om = C(1) - om;
-    S* fn = (S*)L.f_nxt;
-    long long s = (long long)x + (long long)L.nx * ((long long)y + (long long)L.ny * z);
-    SiteNbr n = site_nbr(L, x, y, z);
-    int pc = -1;  // particle whose U0 is held
-    C U0[3] = {0, 0, 0};
+    // Eq. 5 factored per weight class c (0 rest, 1 axis, 2 diagonal):
+    // f^eq_i = A_c + c_i.v (B_c + H_c c_i.v) with A_c = w_c rho (1 - 3/2 v.v),
+    // B_c = 3 w_c rho, H_c = 9/2 w_c rho; v = us^k (the shifted velocity of
+    // Eq. 16) and, for omega != 1, v = u.
+    C A[2][3], B[2][3], H[2][3];
+#pragma unroll
+    for (int k = 0; k < 2; k++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            C wr = wgt<C>(c == 0 ? 0 : (c == 1 ? 1 : 7)) * m.rho[k];
+            A[k][c] = wr * (C(1) - C(1.5) * uus[k]);
+            B[k][c] = C(3) * wr;
+            H[k][c] = C(4.5) * wr;
+        }
+    // site-index steps to the neighbours, periodic wrap folded in (32-bit:
+    // a lattice holds fewer than 2^31 sites)
+    const unsigned ps = (unsigned)L.pstride;
+    const int nx = L.nx, nxy = L.nx * L.ny;
+    const unsigned s = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)L.ny * (unsigned)z);
+    const int dxp = x == nx - 1 ? 1 - nx : 1, dxm = x == 0 ? nx - 1 : -1;
+    const int dyp = y == L.ny - 1 ? nx - nxy : nx, dym = y == 0 ? nxy - nx : -nx;
+    const int dzp = z == L.nz - 1 ? nxy - (int)L.N : nxy, dzm = z == 0 ? (int)L.N - nxy : -nxy;
+    const bool wall_lo = z == 0 && !L.per[2], wall_hi = z == L.nz - 1 && !L.per[2];
+    C U0[3];
+    particle_u0_of<C>(L, pref, x, y, z, U0);
+    // wall velocity of the links leaving through z-1 / z / z+1 (a site next
+    // to a wall bounces its wall links on the wall, all others on U0)
+    C V[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        V[0][d] = wall_lo ? C(L.P.wall_u_lo[d]) : U0[d];
+        V[1][d] = U0[d];
+        V[2][d] = wall_hi ? C(L.P.wall_u_hi[d]) : U0[d];
+    }
+    // destinations as 32-bit element offsets from the base of the plane pair
+    // (2j-1, 2j): plane 2j adds ps; sites < 2^31 and ps < 2^31 keep them in range
+    char* fnb = (char*)L.f_nxt;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         C fs[2];
+        C cu[2];
 #pragma unroll
         for (int k = 0; k < 2; k++) {
-            if (UNIT)  // omega = 1 exactly: Eq. 16 is f* = f^eq(rho^k, u + F^k/rho^k)
-                fs[k] = feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
-            else
+            const int c = i == 0 ? 0 : (i <= 6 ? 1 : 2);
+            if (UNIT) {  // omega = 1 exactly: Eq. 16 is f* = f^eq(rho^k, us^k)
+                cu[k] = C(cx(i)) * us[k][0] + C(cy(i)) * us[k][1] + C(cz(i)) * us[k][2];
+                fs[k] = i == 0 ? A[k][0] : A[k][c] + cu[k] * (B[k][c] + H[k][c] * cu[k]);
+            } else {
                 fs[k] = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
                                     feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
                         feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
-        }
-        uint8_t nb = i == 0 ? 0 : sh.sol[sl[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)];
-        if (nb == 0) {
-            long long q = i == 0 ? s : nbr_index(L, n, i);
-#pragma unroll
-            for (int k = 0; k < 2; k++)
-                st_pop(fn + ((long long)(k * Q + i)) * L.pstride + q, fs[k], pop_shift<S, C>(L, k, i));
-        } else {
-            C cu;
-            if (nb == 2) {
-                const double* uw = cz(i) < 0 ? L.P.wall_u_lo : L.P.wall_u_hi;
-                cu = C(cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2]);
-            } else {
-                int p = sh.pid[sl[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)];
-                if (p != pc) {
-                    particle_u0<C>(L, p, x, y, z, U0);
-                    pc = p;
-                }
-                cu = C(cx(i)) * U0[0] + C(cy(i)) * U0[1] + C(cz(i)) * U0[2];
             }
+        }
+        if (i == 0) {
 #pragma unroll
             for (int k = 0; k < 2; k++)
-                st_pop(fn + ((long long)(k * Q + opp(i))) * L.pstride + s,
-                       fs[k] - C(6) * wgt<C>(i) * m.rho[k] * cu, pop_shift<S, C>(L, k, opp(i)));
+                st_pop((S*)(fnb + (unsigned long long)ps * (unsigned)(k * Q * (int)sizeof(S))) + s,
+                       solid ? wgt<C>(0) * C(L.P.rho0[k]) : fs[k], pop_shift<S, C>(L, k, 0));
+            continue;
+        }
+        const int lo = (i & 1) ? i : i - 1;  // first plane of the pair
+        const bool b = (bb >> i) & 1u;
+        const unsigned q = solid ? s
+                                 : s + (unsigned)((cx(i) > 0 ? dxp : (cx(i) < 0 ? dxm : 0)) +
+                                                  (cy(i) > 0 ? dyp : (cy(i) < 0 ? dym : 0)) +
+                                                  (cz(i) > 0 ? dzp : (cz(i) < 0 ? dzm : 0)));
+        const unsigned off = b ? (opp(i) == lo ? s : s + ps) : (i == lo ? q : q + ps);
+        const int zs = cz(i) + 1;
+        C cw = C(cx(i)) * V[zs][0] + C(cy(i)) * V[zs][1] + C(cz(i)) * V[zs][2];
+        cw = b ? C(-2) * cw : C(0);  // f_ibar = f*_i - 6 w_i rho c_i.u_w (Eq. 17)
+        const int c = i <= 6 ? 1 : 2;
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            S* base = (S*)(fnb + (unsigned long long)ps * (unsigned)((k * Q + lo) * (int)sizeof(S)));
+            st_pop(base + off, solid ? wgt<C>(i) * C(L.P.rho0[k]) : fs[k] + B[k][c] * cw,
+                   pop_shift<S, C>(L, k, i));
+        }
+    }
+    if (multi) {
+#pragma unroll 1
+        for (int i = 1; i < Q; i++) {
+            int a = cz(i) < 0 ? sl[0] : (cz(i) > 0 ? sl[2] : sl[1]);
+            int nd = sh.nd[a][ty + 1 + cy(i)][tx + 1 + cx(i)];
+            if (nd < 0 || nd == p0) continue;
+            C U[3];
+            particle_u0<C>(L, nd, x, y, z, U);
+            C cw = C(cx(i)) * U[0] + C(cy(i)) * U[1] + C(cz(i)) * U[2];
+            for (int k = 0; k < 2; k++) {
+                C fs;
+                if (UNIT)
+                    fs = feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
+                else
+                    fs = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
+                                     feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
+                         feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
+                S* dst = (S*)(fnb + (unsigned long long)ps * (unsigned)((k * Q + opp(i)) * (int)sizeof(S))) + s;
+                st_pop(dst, fs - C(6) * wgt<C>(i) * m.rho[k] * cw, pop_shift<S, C>(L, k, i));
+            }
         }
     }
 }
@@ -410,9 +534,10 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k
         bool more = z + 1 < z1;
         bool have_n = fill_plane<PREC>(L, sh, hi, z + 1, x0, y0, W, H, more, nxt);
         __syncthreads();
-        if (act && sh.sol[mid][ty + 1][tx + 1] == 0) {
+        if (act) {
             int sl[3] = {lo, mid, hi};
-            collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, cur, [&](int q) { return &sh.stage[q][tid]; });
+            collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, cur, sh.nd[mid][ty + 1][tx + 1] != ND_FLUID,
+                                     [&](int q) { return &sh.stage[q][tid]; });
         }
         __syncthreads();
         if (!UNIT && have_n)
@@ -423,6 +548,173 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k
         for (int d = 0; d < 3; d++) { cur.j[0][d] = nxt.j[0][d]; cur.j[1][d] = nxt.j[1][d]; }
         int t = lo; lo = mid; mid = hi; hi = t;
     }
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// ------------------------------------------ copy-pipelined fused step
+// The fused step for a lattice with particles, where a full density pass
+// (k_density) and the virtual densities (Eq. 20) have filled psi before the
+// step: the halo of the Shan-Chen sum then needs no populations, and the
+// block streams each plane through shared memory with asynchronous copies
+// (cp.async, 16-byte chunks of the tile rows for the populations, 4/8-byte
+// copies for psi^k and the owner map of tile + ring), issued one plane ahead
+// so that the copies of plane z+1 and of the psi plane z+2 are in flight while
+// plane z collides.  One barrier per plane; the population stage is double
+// buffered.  Completion is the copy unit's own wait (cp.async.wait_all),
+// not a spin.
+constexpr int APSI = 4;  // psi / node-code planes held: z-1, z, z+1 and the one in flight
+
+constexpr int ASYNC_TY = 8;  // tile rows of the copy-pipelined kernel
+
+template <int PREC, int TY>
+struct AsyncShared {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    S stage[2][2 * Q][FTX * TY];
+    C psi[APSI][2][TY + 2][RW];
+    int nd[APSI][TY + 2][RW];
+};
+
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// nx (and so every tile width) must be a multiple of this for the 16-byte
+// population chunks of a precision
+template <int PREC>
+constexpr int async_x_multiple() {
+    return 16 / (int)sizeof(typename Prec<PREC>::S) < 4 ? 4 : 16 / (int)sizeof(typename Prec<PREC>::S);
+}
+
+template <int PREC, bool UNIT, int TY>
+__global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fused_async(Lattice L, int zc) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    constexpr int NT = FTX * TY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AsyncShared<PREC, TY>& sh = *reinterpret_cast<AsyncShared<PREC, TY>*>(smem_raw);
+    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * TY;
+    const int W = min(FTX, L.nx - x0), H = min(TY, L.ny - y0);
+    const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, L.nz);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
+    const bool act = tx < W && ty < H;
+    const long long nxy = (long long)L.nx * L.ny;
+    const C* psig = (const C*)L.psi;
+    auto slot_of = [&](int p) { return (p - z0 + 1) & (APSI - 1); };
+    // fixed per thread: its own tile position and, for the first 2(W+2) + 2H
+    // threads, one position of the ring (periodic images at the edges)
+    auto wrap_xy = [&](int lx, int ly) {
+        int X = x0 + lx, Y = y0 + ly;
+        X = X < 0 ? X + L.nx : (X >= L.nx ? X - L.nx : X);
+        Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
+        return X + L.nx * Y;
+    };
+    const int own_xy = wrap_xy(tx, ty);
+    const bool has_ring = tid < 2 * (W + 2) + 2 * H;
+    int rlx, rly;
+    if (tid < W + 2) { rlx = tid - 1; rly = -1; }
+    else if (tid < 2 * (W + 2)) { rlx = tid - (W + 2) - 1; rly = H; }
+    else if (tid < 2 * (W + 2) + H) { rlx = -1; rly = tid - 2 * (W + 2); }
+    else { rlx = W; rly = tid - 2 * (W + 2) - H; }
+    const int ring_xy = has_ring ? wrap_xy(rlx, rly) : 0;
+    // psi^k and node codes of plane p (tile + ring) into its slot
+    auto issue_psi = [&](int p) {
+        int slot = slot_of(p);
+        if ((p < 0 || p >= L.nz) && !L.per[2]) {
+            const C* pw = (const C*)L.psi_wall + (p < 0 ? 0 : 2) * nxy;
+            if (act) {
+                sh.psi[slot][0][ty + 1][tx + 1] = pw[own_xy];
+                sh.psi[slot][1][ty + 1][tx + 1] = pw[nxy + own_xy];
+                sh.nd[slot][ty + 1][tx + 1] = ND_WALL;
+            }
+            if (has_ring) {
+                sh.psi[slot][0][rly + 1][rlx + 1] = pw[ring_xy];
+                sh.psi[slot][1][rly + 1][rlx + 1] = pw[nxy + ring_xy];
+                sh.nd[slot][rly + 1][rlx + 1] = ND_WALL;
+            }
+            return;
+        }
+        int Z = p < 0 ? p + L.nz : (p >= L.nz ? p - L.nz : p);
+        const long long zoff = nxy * Z;
+        // the owner map is the node code: -1 on fluid nodes
+        auto put = [&](int ly, int lx, long long g) {
+            cp_async_4(&sh.nd[slot][ly][lx], L.owner + g);
+            if (sizeof(C) == 8) {
+                cp_async_8(&sh.psi[slot][0][ly][lx], psig + g);
+                cp_async_8(&sh.psi[slot][1][ly][lx], psig + L.N + g);
+            } else {
+                cp_async_4(&sh.psi[slot][0][ly][lx], psig + g);
+                cp_async_4(&sh.psi[slot][1][ly][lx], psig + L.N + g);
+            }
+        };
+        if (act) put(ty + 1, tx + 1, zoff + own_xy);
+        if (has_ring) put(rly + 1, rlx + 1, zoff + ring_xy);
+    };
+    // the 2 x 19 population rows of the tile of plane p into stage buffer b:
+    // lane tx copies 16-byte chunk tx % LPP of its row in planes tx / LPP,
+    // tx / LPP + PPP, ...
+    constexpr int EPC = 16 / (int)sizeof(S);  // elements per 16-byte chunk
+    constexpr int LPP = FTX / EPC;            // lanes per population row
+    constexpr int PPP = FTX / LPP;            // population planes per pass
+    const int chunk = tx % LPP, plane0 = tx / LPP;
+    const bool copies = ty < H && chunk * EPC < W;
+    const long long row_off = (long long)(x0 + chunk * EPC) + (long long)L.nx * (y0 + ty);
+    auto issue_pops = [&](int p, int b) {
+        if (!copies) return;
+        const char* src = (const char*)L.f_cur +
+                          ((long long)plane0 * L.pstride + row_off + nxy * p) * (long long)sizeof(S);
+        const long long step = (long long)PPP * L.pstride * (long long)sizeof(S);
+        S* dst = &sh.stage[b][plane0][ty * FTX + chunk * EPC];
+#pragma unroll
+        for (int pl = plane0; pl < 2 * Q; pl += PPP) {
+            cp_async_16(dst, src);
+            src += step;
+            dst += PPP * NT;
+        }
+    };
+    issue_psi(z0 - 1);
+    issue_psi(z0);
+    issue_psi(z0 + 1);
+    issue_pops(z0, 0);
+    cp_async_commit();
+    for (int z = z0; z < z1; z++) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int b = (z - z0) & 1;
+        if (z + 1 < z1) issue_pops(z + 1, b ^ 1);
+        if (z + 2 <= z1) issue_psi(z + 2);
+        cp_async_commit();
+        if (!act) continue;
+        const int mid = slot_of(z);
+        OwnSite<PREC> m;
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            C r = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+            for (int i = 0; i < Q; i++) {
+                C v = ld_pop(&sh.stage[b][k * Q + i][tid], pop_shift<S, C>(L, k, i));
+                r += v;
+                if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
+                if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
+                if (cz(i) > 0) jz += v; else if (cz(i) < 0) jz -= v;
+            }
+            m.rho[k] = r;
+            m.j[k][0] = jx; m.j[k][1] = jy; m.j[k][2] = jz;
+        }
+        int sl[3] = {slot_of(z - 1), mid, slot_of(z + 1)};
+        collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, m, sh.nd[mid][ty + 1][tx + 1] != ND_FLUID,
+                                 [&](int q) { return &sh.stage[b][q][tid]; });
+    }
+    cp_async_wait_all();
 }
 
 // ----------------------------------------------- TMA-pipelined fused step
@@ -454,13 +746,10 @@ struct TmaShared {
     typedef typename Prec<PREC>::C C;
     S buf[TNB][2 * Q][TBY][TmaGeom<PREC>::BXT];
     C psi[3][2][RH][RW];
-    uint8_t sol[3][RH][RW];
-    int pid[3][RH][RW];
+    int nd[3][RH][RW];
     unsigned long long mbar[TNB];
     int abort;
 };
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
     unsigned done;
@@ -542,7 +831,7 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_tma(Lattice L, int zc, const _
                 long long w = (long long)X + (long long)L.nx * Y;
                 sh.psi[slot][0][ly + 1][lx + 1] = pw[(side * 2 + 0) * nxy + w];
                 sh.psi[slot][1][ly + 1][lx + 1] = pw[(side * 2 + 1) * nxy + w];
-                sh.sol[slot][ly + 1][lx + 1] = 2;
+                sh.nd[slot][ly + 1][lx + 1] = ND_WALL;
             }
             return;
         }
@@ -569,12 +858,11 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_tma(Lattice L, int zc, const _
             Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
             long long s = (long long)X + (long long)L.nx * Y + zoff;
             C r0 = 0, r1 = 0;
-            uint8_t sl = 0;
+            int nd = ND_FLUID;
             if (L.mask[s]) {
                 r0 = psig[s];
                 r1 = psig[L.N + s];
-                sl = 1;
-                sh.pid[slot][ly + 1][lx + 1] = L.owner[s];
+                nd = L.owner[s];
             } else if (inside) {
 #pragma unroll
                 for (int i = 0; i < Q; i++) {
@@ -590,7 +878,7 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_tma(Lattice L, int zc, const _
             }
             sh.psi[slot][0][ly + 1][lx + 1] = r0;
             sh.psi[slot][1][ly + 1][lx + 1] = r1;
-            sh.sol[slot][ly + 1][lx + 1] = sl;
+            sh.nd[slot][ly + 1][lx + 1] = nd;
         }
     };
 
@@ -609,7 +897,7 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_tma(Lattice L, int zc, const _
         fill(z + 1, hi);
         __syncthreads();
         if (sh.abort) break;
-        if (act && sh.sol[mid][ty + 1][tx + 1] == 0) {
+        if (act) {
             int sl[3] = {lo, mid, hi};
             int b = buf_of(z);
             // own populations, moments from the shared copy
@@ -628,7 +916,7 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_tma(Lattice L, int zc, const _
                 m.rho[k] = r;
                 m.j[k][0] = jx; m.j[k][1] = jy; m.j[k][2] = jz;
             }
-            collide_site<PREC, false>(L, sh, sl, x0 + tx, y0 + ty, z, m,
+            collide_site<PREC, false>(L, sh, sl, x0 + tx, y0 + ty, z, m, sh.nd[mid][ty + 1][tx + 1] != ND_FLUID,
                                       [&](int q) { return &sh.buf[b][q][ty + 1][tx + TG::PAD]; });
         }
         __syncthreads();
@@ -830,7 +1118,68 @@ int launch_fluid_step_tma(const Lattice& L, int prec, const void* tmap, cudaStre
     return 1;
 }
 
+// Number of z chunks for a kernel with `per_sm` resident blocks per SM: the
+// grid (tiles x chunks) is close to a whole number of full waves, with
+// chunks of at least `zmin` planes.
+static int z_chunks(const Lattice& L, int tiles, int per_sm, int zmin) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    long long R = (long long)sms * per_sm;
+    int best = 1;
+    double best_eff = 0;
+    for (int zc = L.nz; zc >= zmin || zc == L.nz; zc--) {
+        long long B = (long long)tiles * ((L.nz + zc - 1) / zc);
+        double eff = (double)B / (double)(((B + R - 1) / R) * R);
+        if (B >= 4 * R && eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = zc;
+        }
+        if (best_eff >= 0.98) break;
+        if (zc <= 1) break;
+    }
+    if (best_eff == 0) best = zmin < L.nz ? zmin : L.nz;
+    return best;
+}
+
+template <int P>
+static int launch_fused_async(const Lattice& L, bool unit, cudaStream_t st) {
+    constexpr int TY = ASYNC_TY, NT = FTX * TY;
+    static bool attr_set[2] = {false, false};
+    static int per_sm[2] = {0, 0};
+    const size_t smem = sizeof(AsyncShared<P, TY>);
+    if (!attr_set[unit]) {
+        if (unit) {
+            cudaFuncSetAttribute(k_fused_async<P, true, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[unit], k_fused_async<P, true, TY>, NT, smem);
+        } else {
+            cudaFuncSetAttribute(k_fused_async<P, false, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[unit], k_fused_async<P, false, TY>, NT, smem);
+        }
+        if (per_sm[unit] < 1) per_sm[unit] = 1;
+        attr_set[unit] = true;
+    }
+    int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + TY - 1) / TY);
+    int zc = z_chunks(L, tiles, per_sm[unit], 8);
+    dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
+    if (unit) k_fused_async<P, true, TY><<<grid, dim3(FTX, TY), smem, st>>>(L, zc);
+    else k_fused_async<P, false, TY><<<grid, dim3(FTX, TY), smem, st>>>(L, zc);
+    return 1;
+}
+
 int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st) {
+    // with a full density pass done, the copy-pipelined kernel (its 16-byte
+    // population chunks need nx to be a multiple of 16 bytes of elements)
+    if (L.dense_psi) {
+        bool unit = L.P.tau[0] == 1.0 && L.P.tau[1] == 1.0;
+        if (prec == LB_FP32 && L.nx % async_x_multiple<LB_FP32>() == 0) return launch_fused_async<LB_FP32>(L, unit, st);
+        if (prec == LB_FP16 && L.nx % async_x_multiple<LB_FP16>() == 0) return launch_fused_async<LB_FP16>(L, unit, st);
+        if (prec == LB_FP64 && L.nx % async_x_multiple<LB_FP64>() == 0) return launch_fused_async<LB_FP64>(L, unit, st);
+    }
     int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + FTY - 1) / FTY);
     // z chunk: enough blocks to fill the GPU a few times over, at least 8 planes
     int zc = (int)((long long)L.nz * tiles / 2400);

@@ -81,6 +81,7 @@ struct Lattice {
     float* fsnap;      // [n][9] position - ipos, v(t-1/2), omega(t-1/2) in FP32
     double* red;       // reduction partials
     int red_blocks;
+    int dense_psi;     // psi holds rho^k of every fluid node (a full density pass ran this step)
     lb_params P;
 };
 

@@ -106,6 +106,24 @@ def test_fp64_ragged_walls_moving_particle():
     compare_colloids(g, o, 1e-11)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 1e-3)])
+@pytest.mark.parametrize("nx", [20, 24])
+def test_reduced_precision_ragged_walls_moving_particles(prec, tol, nx):
+    """The ragged-tile case in the reduced-precision forms: tiles 20 or 24
+    sites wide and 5 rows high at the lattice edges (FP16 with nx = 20 takes
+    the plain-load fused kernel, every other case the copy-pipelined one),
+    sheared walls, unequal tau, moving particles, 40 steps."""
+    shape = (nx, 13, 11)
+    params = dict(G=0.6, tau=(0.8, 1.2), zeta=(0.15, -0.15), bc=(1, 1, 0), wall_u_lo=(-0.02, 0.01, 0),
+                  wall_u_hi=(0.03, 0, 0), body_force=(1e-5, 0, -2e-6), hertz_K=20, hertz_sigma=8.0,
+                  hertz_rcap=7.0, side_wall_k=0.5, side_wall_d=4.0)
+    col = dict(pos=[[7.2, 6.1, 5.3], [15.5, 6.5, 5.0]], radius=[3.2, 3.0], mass=[1500.0, 1200.0],
+               vel=[[0.05, 0.03, -0.01], [-0.04, 0.0, 0.02]], omega=[[0.01, 0.0, 0.02], [0, -0.02, 0]])
+    g, o = run_both(shape, params, 40, prec, col)
+    compare_fields(g, o, tol)
+    compare_colloids(g, o, tol)
+
+
 def test_fp64_fluid_only_populations_exact():
     """No particles: every population matches the oracle to 1e-13."""
     shape = (16, 9, 7)
@@ -188,4 +206,17 @@ def test_error_paths_are_reported():
     assert e.value.code == lbgb.LB_ERR_NONFINITE
     with pytest.raises(lbgb.LBError) as e:
         g.set_params(tau=(0.4, 1.0))
+    assert e.value.code == lbgb.LB_ERR_ARG
+
+
+def test_create_rejects_lattices_beyond_32bit_site_indices():
+    """Sites are indexed in 32 bits inside the kernels: a lattice of 2^31 or
+    more sites is refused before any allocation is used."""
+    import torch
+
+    from paper_2004_04080_gb300 import lbgb
+
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lbgb.LBError) as e:
+        lbgb.lb_create(2048, 1024, 1024, lbgb.LB_FP32, 0, ws.data_ptr(), ws.numel(), 0)
     assert e.value.code == lbgb.LB_ERR_ARG

@@ -385,7 +385,8 @@ int lb_step(lb_ctx* ctx, int nsteps) {
         n += launch_virtual(L, ctx->prec, 1, s);       // Eqs. 20, 21
         bool timed = ctx->prof_on && ctx->prof_n < PROF_MAX;
         if (timed) CK(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], s), "profile event");
-        if (ctx->tma_ok)                               // Eqs. 11, 14, 16, 3, 9, 17
+        // Eqs. 11, 14, 16, 3, 9, 17; the link forces of Eqs. 19, 22, 23
+        if (ctx->tma_ok)
             n += launch_fluid_step_tma(L, ctx->prec, &ctx->tmaps[L.f_cur == (void*)ctx->ws ? 0 : 1], s);
         else
             n += launch_fluid_step(L, ctx->prec, s);
@@ -393,7 +394,6 @@ int lb_step(lb_ctx* ctx, int nsteps) {
             CK(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], s), "profile event");
             ctx->prof_n++;
         }
-        n += launch_links(L, ctx->prec, s);            // Eqs. 19, 22, 23
         n += launch_pairs_integrate(L, ctx->cells, ctx->cells_bytes, s);  // Eqs. 26-27, 32-35
         int rc = launched(ctx, n, "step kernels");
         if (rc) return rc;

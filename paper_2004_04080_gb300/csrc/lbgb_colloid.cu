@@ -437,6 +437,12 @@ __global__ void __launch_bounds__(PB) k_virtual(Lattice L, int store_terms) {
     int p = blockIdx.x;
     PGeo<C> g = pgeo<C>(L, p, 1.5);
     C* psi = (C*)L.psi;
+    // the lattice step adds the link forces of this step (Eqs. 19, 22, 23)
+    if (store_terms && threadIdx.x == 0 && threadIdx.y == 0)
+        for (int q = 0; q < 3; q++) {
+            L.Fliq[3 * p + q] = 0.0;
+            L.Tliq[3 * p + q] = 0.0;
+        }
     CSum<C> acc[6];
     zero(acc);
     const C G = C(L.P.G), z0 = C(1) + C(L.P.zeta[0]), z1 = C(1) + C(L.P.zeta[1]);
@@ -482,79 +488,6 @@ __global__ void __launch_bounds__(PB) k_virtual(Lattice L, int store_terms) {
         for (int q = 0; q < 3; q++) {
             L.Fs[3 * p + q] = out[q];
             L.Ts[3 * p + q] = out[3 + q];
-        }
-}
-
-// ------------------------------------------------------------- links
-// Eq. 19 on every link (x, i) from a fluid node x to a node of p:
-// F_i = [2 f*_i(x) - 2 w_i rho^k (u_w.c_i)/cs^2] c_i summed over k, with
-// f*_i(x) recovered from the bounced population f_ibar(x, t+1) written by the
-// lattice step; Eqs. 22-23 sum the forces and torques (r_w - r_p) x F_i.
-// The neighbour masks, then the owners of the particle neighbours, then the
-// bounced populations are each loaded as one independent batch.
-template <int PREC>
-__global__ void __launch_bounds__(PB) k_links(Lattice L) {
-    typedef typename Prec<PREC>::S S;
-    typedef typename Prec<PREC>::C C;
-    int p = blockIdx.x;
-    PGeo<C> g = pgeo<C>(L, p, 1.5);
-    const C* psi = (const C*)L.psi;
-    const S* fn = (const S*)L.f_nxt;
-    CSum<C> acc[6];
-    zero(acc);
-    // a fluid node linked to p lies within sqrt(2) outside the surface
-    for_shell<C>(L, g, -0.01f, 1.45f, [&](int X, int Y, int Z, long long s, int, int, int, const C (&d)[3]) {
-        if (L.mask[s]) return;
-        SiteNbr n = site_nbr(L, X, Y, Z);
-        int m[Q];
-        uint32_t solid = nbr_solid(L, n, m);
-        if (!solid) return;
-        uint32_t mine = 0;
-#pragma unroll
-        for (int i = 1; i < Q; i++)
-            if ((solid >> i) & 1u) mine |= (uint32_t)(__ldg(L.owner + m[i]) == p) << i;
-        if (!mine) return;
-        C rho0 = psi[s], rho1 = psi[L.N + s];
-        // c_i . u_w = c_i . (v_p + omega_p x d) for every link of this site (Eq. 18
-        // with r_w = x + c_i/2; the c_i/2 part drops out of the projection)
-        C wxd[3];
-        crs<C>(g.w, d, wxd);
-        C U0[3] = {g.v[0] + wxd[0], g.v[1] + wxd[1], g.v[2] + wxd[2]};
-        C fb[2][Q];
-#pragma unroll
-        for (int i = 1; i < Q; i++) {
-            bool on = (mine >> i) & 1u;
-            fb[0][i] = on ? ld_pop(fn + ((long long)opp(i)) * L.pstride + s, pop_shift<S, C>(L, 0, opp(i))) : C(0);
-            fb[1][i] = on ? ld_pop(fn + ((long long)(Q + opp(i))) * L.pstride + s, pop_shift<S, C>(L, 1, opp(i)))
-                          : C(0);
-        }
-#pragma unroll
-        for (int i = 1; i < Q; i++) {
-            if (!((mine >> i) & 1u)) continue;
-            C rel[3] = {d[0] + C(0.5) * C(cx(i)), d[1] + C(0.5) * C(cy(i)), d[2] + C(0.5) * C(cz(i))};
-            C cu = C(cx(i)) * U0[0] + C(cy(i)) * U0[1] + C(cz(i)) * U0[2];
-            C fl = 0;
-#pragma unroll
-            for (int k = 0; k < 2; k++) {
-                C corr = C(6) * wgt<C>(i) * (k == 0 ? rho0 : rho1) * cu;
-                C fstar = fb[k][i] + corr;
-                fl += C(2) * fstar - corr;
-            }
-            C F[3] = {fl * C(cx(i)), fl * C(cy(i)), fl * C(cz(i))}, tq[3];
-            crs<C>(rel, F, tq);
-#pragma unroll
-            for (int q = 0; q < 3; q++) {
-                acc[q].add(F[q]);
-                acc[3 + q].add(tq[q]);
-            }
-        }
-    });
-    double out[6];
-    block_reduce<6, C>(acc, out);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        for (int q = 0; q < 3; q++) {
-            L.Fliq[3 * p + q] = out[q];
-            L.Tliq[3 * p + q] = out[3 + q];
         }
 }
 
@@ -855,12 +788,6 @@ int launch_remap(const Lattice& L, int prec, cudaStream_t st) {
 int launch_virtual(const Lattice& L, int prec, int store_terms, cudaStream_t st) {
     if (L.nc <= 0) return 0;
     DISPATCHC(prec, (k_virtual<P><<<L.nc, PBLK, 0, st>>>(L, store_terms)));
-    return 1;
-}
-
-int launch_links(const Lattice& L, int prec, cudaStream_t st) {
-    if (L.nc <= 0) return 0;
-    DISPATCHC(prec, (k_links<P><<<L.nc, PBLK, 0, st>>>(L)));
     return 1;
 }
 

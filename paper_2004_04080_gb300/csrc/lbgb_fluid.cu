@@ -133,9 +133,8 @@ __device__ __forceinline__ ParticleRef<C> particle_load(const Lattice& L, int p)
 
 template <typename C>
 __device__ __forceinline__ void particle_u0_of(const Lattice& L, const ParticleRef<C>& r, int x, int y, int z,
-                                               C (&U0)[3]) {
+                                               C (&U0)[3], C (&rel)[3]) {
     int xs[3] = {x, y, z}, Ls[3] = {L.nx, L.ny, L.nz};
-    C rel[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         int dd = xs[d] - r.ip[d];
@@ -151,8 +150,23 @@ __device__ __forceinline__ void particle_u0_of(const Lattice& L, const ParticleR
 }
 
 template <typename C>
-__device__ __forceinline__ void particle_u0(const Lattice& L, int p, int x, int y, int z, C (&U0)[3]) {
-    particle_u0_of<C>(L, particle_load<C>(L, p), x, y, z, U0);
+__device__ __forceinline__ void particle_u0(const Lattice& L, int p, int x, int y, int z, C (&U0)[3], C (&rel)[3]) {
+    particle_u0_of<C>(L, particle_load<C>(L, p), x, y, z, U0, rel);
+}
+
+// Add the link force and torque of one site (Eqs. 22, 23) to F_liq, T_liq of
+// its particle with FP64 atomics (p < 0: no link of the site reaches a
+// particle).  One warp instruction per component; the L2 serves them
+// alongside the population traffic.  The order of the additions varies from
+// run to run (FP64 sums: differences at the level of its rounding).
+template <typename C>
+__device__ __forceinline__ void commit_link_forces(const Lattice& L, int p, const C (&F)[3], const C (&T)[3]) {
+    if (p < 0) return;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        atomicAdd(L.Fliq + 3 * p + d, double(F[d]));
+        atomicAdd(L.Tliq + 3 * p + d, double(T[d]));
+    }
 }
 
 // ------------------------------------------------------- fused step
@@ -342,7 +356,9 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
 // particle node are the stored rest equilibrium.)
 template <int PREC, bool UNIT, typename SH, typename PopFn>
 __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int (&sl)[3], int x, int y, int z,
-                                             const OwnSite<PREC>& m, bool solid, PopFn pop) {
+                                             const OwnSite<PREC>& m, bool solid, PopFn pop,
+                                             int& pforce, typename Prec<PREC>::C (&Fp)[3],
+                                             typename Prec<PREC>::C (&Tp)[3]) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
     int tx = threadIdx.x, ty = threadIdx.y;
@@ -353,7 +369,7 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
     // The particle of the first particle link gives U0 (its loads are issued
     // first, to overlap the force and collision arithmetic); a site next to
     // two particles rewrites the links into the second one afterwards.
-    unsigned bb = 0;
+    unsigned bb = 0, pm = 0;  // bounce-back links; links into particle p0
     int p0 = -1;
     bool multi = false;
 #pragma unroll
@@ -363,9 +379,11 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
         if (nd >= 0) {
             multi |= p0 >= 0 && nd != p0;
             p0 = p0 < 0 ? nd : p0;
+            pm |= (unsigned)(nd == p0) << i;
         }
     }
     bb = solid ? 0u : bb;
+    pm = solid ? 0u : pm;
     multi = multi && !solid;
     // (particle 0 stands in when no link reaches a particle: its record
     // exists whenever the lattice has room for particles, and U0 is unused)
@@ -429,8 +447,10 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
     const int dyp = y == L.ny - 1 ? nx - nxy : nx, dym = y == 0 ? nxy - nx : -nx;
     const int dzp = z == L.nz - 1 ? nxy - (int)L.N : nxy, dzm = z == 0 ? (int)L.N - nxy : -nxy;
     const bool wall_lo = z == 0 && !L.per[2], wall_hi = z == L.nz - 1 && !L.per[2];
-    C U0[3];
-    particle_u0_of<C>(L, pref, x, y, z, U0);
+    C U0[3], rel[3];
+    particle_u0_of<C>(L, pref, x, y, z, U0, rel);
+    // Eq. 19: the momentum a link into p0 hands over, (f*_i + f_ibar(t+1)) c_i
+    C Fl[3] = {0, 0, 0};
     // wall velocity of the links leaving through z-1 / z / z+1 (a site next
     // to a wall bounces its wall links on the wall, all others on U0)
     C V[3][3];
@@ -477,22 +497,37 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
         C cw = C(cx(i)) * V[zs][0] + C(cy(i)) * V[zs][1] + C(cz(i)) * V[zs][2];
         cw = b ? C(-2) * cw : C(0);  // f_ibar = f*_i - 6 w_i rho c_i.u_w (Eq. 17)
         const int c = i <= 6 ? 1 : 2;
+        C fl = 0;
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             S* base = (S*)(fnb + (unsigned long long)ps * (unsigned)((k * Q + lo) * (int)sizeof(S)));
-            st_pop(base + off, solid ? wgt<C>(i) * C(L.P.rho0[k]) : fs[k] + B[k][c] * cw,
-                   pop_shift<S, C>(L, k, i));
+            const C fb = fs[k] + B[k][c] * cw;
+            st_pop(base + off, solid ? wgt<C>(i) * C(L.P.rho0[k]) : fb, pop_shift<S, C>(L, k, i));
+            fl += fs[k] + fb;
         }
+        fl = (pm >> i) & 1u ? fl : C(0);
+        if (cx(i)) Fl[0] += C(cx(i)) * fl;
+        if (cy(i)) Fl[1] += C(cy(i)) * fl;
+        if (cz(i)) Fl[2] += C(cz(i)) * fl;
     }
+    // Eq. 23 with r_w - r_p = (x - r_p) + c_i/2: the c_i/2 part is parallel
+    // to the link force and drops out of the torque
+    pforce = pm ? p0 : -1;
+#pragma unroll
+    for (int d = 0; d < 3; d++) Fp[d] = Fl[d];
+    Tp[0] = rel[1] * Fl[2] - rel[2] * Fl[1];
+    Tp[1] = rel[2] * Fl[0] - rel[0] * Fl[2];
+    Tp[2] = rel[0] * Fl[1] - rel[1] * Fl[0];
     if (multi) {
 #pragma unroll 1
         for (int i = 1; i < Q; i++) {
             int a = cz(i) < 0 ? sl[0] : (cz(i) > 0 ? sl[2] : sl[1]);
             int nd = sh.nd[a][ty + 1 + cy(i)][tx + 1 + cx(i)];
             if (nd < 0 || nd == p0) continue;
-            C U[3];
-            particle_u0<C>(L, nd, x, y, z, U);
+            C U[3], r2[3];
+            particle_u0<C>(L, nd, x, y, z, U, r2);
             C cw = C(cx(i)) * U[0] + C(cy(i)) * U[1] + C(cz(i)) * U[2];
+            C fl = 0;
             for (int k = 0; k < 2; k++) {
                 C fs;
                 if (UNIT)
@@ -502,7 +537,17 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
                                      feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
                          feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
                 S* dst = (S*)(fnb + (unsigned long long)ps * (unsigned)((k * Q + opp(i)) * (int)sizeof(S))) + s;
-                st_pop(dst, fs - C(6) * wgt<C>(i) * m.rho[k] * cw, pop_shift<S, C>(L, k, i));
+                const C fb = fs - C(6) * wgt<C>(i) * m.rho[k] * cw;
+                st_pop(dst, fb, pop_shift<S, C>(L, k, i));
+                fl += fs + fb;
+            }
+            // the link force into the second particle, added directly
+            const C F2[3] = {C(cx(i)) * fl, C(cy(i)) * fl, C(cz(i)) * fl};
+            const C T2[3] = {r2[1] * F2[2] - r2[2] * F2[1], r2[2] * F2[0] - r2[0] * F2[2],
+                             r2[0] * F2[1] - r2[1] * F2[0]};
+            for (int d = 0; d < 3; d++) {
+                atomicAdd(L.Fliq + 3 * nd + d, double(F2[d]));
+                atomicAdd(L.Tliq + 3 * nd + d, double(T2[d]));
             }
         }
     }
@@ -534,11 +579,14 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k
         bool more = z + 1 < z1;
         bool have_n = fill_plane<PREC>(L, sh, hi, z + 1, x0, y0, W, H, more, nxt);
         __syncthreads();
+        int pf = -1;
+        C Fp[3] = {0, 0, 0}, Tp[3] = {0, 0, 0};
         if (act) {
             int sl[3] = {lo, mid, hi};
             collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, cur, sh.nd[mid][ty + 1][tx + 1] != ND_FLUID,
-                                     [&](int q) { return &sh.stage[q][tid]; });
+                                     [&](int q) { return &sh.stage[q][tid]; }, pf, Fp, Tp);
         }
+        commit_link_forces<C>(L, pf, Fp, Tp);
         __syncthreads();
         if (!UNIT && have_n)
 #pragma unroll
@@ -693,26 +741,30 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fu
         if (z + 1 < z1) issue_pops(z + 1, b ^ 1);
         if (z + 2 <= z1) issue_psi(z + 2);
         cp_async_commit();
-        if (!act) continue;
-        const int mid = slot_of(z);
-        OwnSite<PREC> m;
+        int pf = -1;
+        C Fp[3] = {0, 0, 0}, Tp[3] = {0, 0, 0};
+        if (act) {
+            const int mid = slot_of(z);
+            OwnSite<PREC> m;
 #pragma unroll
-        for (int k = 0; k < 2; k++) {
-            C r = 0, jx = 0, jy = 0, jz = 0;
+            for (int k = 0; k < 2; k++) {
+                C r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
-            for (int i = 0; i < Q; i++) {
-                C v = ld_pop(&sh.stage[b][k * Q + i][tid], pop_shift<S, C>(L, k, i));
-                r += v;
-                if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
-                if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
-                if (cz(i) > 0) jz += v; else if (cz(i) < 0) jz -= v;
+                for (int i = 0; i < Q; i++) {
+                    C v = ld_pop(&sh.stage[b][k * Q + i][tid], pop_shift<S, C>(L, k, i));
+                    r += v;
+                    if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
+                    if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
+                    if (cz(i) > 0) jz += v; else if (cz(i) < 0) jz -= v;
+                }
+                m.rho[k] = r;
+                m.j[k][0] = jx; m.j[k][1] = jy; m.j[k][2] = jz;
             }
-            m.rho[k] = r;
-            m.j[k][0] = jx; m.j[k][1] = jy; m.j[k][2] = jz;
+            int sl[3] = {slot_of(z - 1), mid, slot_of(z + 1)};
+            collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, m, sh.nd[mid][ty + 1][tx + 1] != ND_FLUID,
+                                     [&](int q) { return &sh.stage[b][q][tid]; }, pf, Fp, Tp);
         }
-        int sl[3] = {slot_of(z - 1), mid, slot_of(z + 1)};
-        collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, m, sh.nd[mid][ty + 1][tx + 1] != ND_FLUID,
-                                 [&](int q) { return &sh.stage[b][q][tid]; });
+        commit_link_forces<C>(L, pf, Fp, Tp);
     }
     cp_async_wait_all();
 }
@@ -897,6 +949,8 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_tma(Lattice L, int zc, const _
         fill(z + 1, hi);
         __syncthreads();
         if (sh.abort) break;
+        int pf = -1;
+        C Fp[3] = {0, 0, 0}, Tp[3] = {0, 0, 0};
         if (act) {
             int sl[3] = {lo, mid, hi};
             int b = buf_of(z);
@@ -917,8 +971,9 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_tma(Lattice L, int zc, const _
                 m.j[k][0] = jx; m.j[k][1] = jy; m.j[k][2] = jz;
             }
             collide_site<PREC, false>(L, sh, sl, x0 + tx, y0 + ty, z, m, sh.nd[mid][ty + 1][tx + 1] != ND_FLUID,
-                                      [&](int q) { return &sh.buf[b][q][ty + 1][tx + TG::PAD]; });
+                                      [&](int q) { return &sh.buf[b][q][ty + 1][tx + TG::PAD]; }, pf, Fp, Tp);
         }
+        commit_link_forces<C>(L, pf, Fp, Tp);
         __syncthreads();
         issue(z + 3);
         int t = lo; lo = mid; mid = hi; hi = t;

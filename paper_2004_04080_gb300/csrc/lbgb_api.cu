@@ -51,7 +51,7 @@ const int RED_BLOCKS = 1024;
 const int PROF_MAX = 16384;
 
 struct Layout {
-    size_t f0, f1, psi, psi_wall, mask, owner, evt, flags, col, prev, ipos, fsnap, cells, cells_bytes, red,
+    size_t f0, f1, mom, psi, psi_wall, mask, owner, evt, flags, col, prev, ipos, fsnap, cells, cells_bytes, red,
         totals, total;
     long long pstride;
 };
@@ -67,6 +67,7 @@ Layout layout(int nx, int ny, int nz, int prec, int maxc) {
     size_t fb1 = fb > (size_t)5 * N * 8 ? fb : (size_t)5 * N * 8;
     l.f0 = off; off = align_up(off + fb);
     l.f1 = off; off = align_up(off + fb1);
+    l.mom = off; off = align_up(off + (size_t)6 * l.pstride * compute_bytes(prec));
     l.psi = off; off = align_up(off + (size_t)2 * N * compute_bytes(prec));
     l.psi_wall = off; off = align_up(off + (size_t)4 * nx * ny * compute_bytes(prec));
     l.mask = off; off = align_up(off + (size_t)N);
@@ -197,6 +198,7 @@ int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_worksp
     L.per[0] = L.per[1] = L.per[2] = 1;
     L.f_cur = ctx->ws + l.f0;
     L.f_nxt = ctx->ws + l.f1;
+    L.mom = ctx->ws + l.mom;
     L.psi = ctx->ws + l.psi;
     L.psi_wall = ctx->ws + l.psi_wall;
     L.mask = (uint8_t*)(ctx->ws + l.mask);
@@ -258,9 +260,20 @@ int lb_set_params(lb_ctx* ctx, const lb_params* p) {
     if (ctx->stepped && p->bc[2] != ctx->L.P.bc[2])
         return set_err(ctx, LB_ERR_STATE, "boundary conditions cannot change after stepping");
     ctx->L.P = *p;
+    ParamsF& f = ctx->L.PF;
     for (int k = 0; k < 2; k++) {
         ctx->L.inv_tau[k] = 1.0 / p->tau[k];
         ctx->L.inv_nu[k] = 3.0 / (p->tau[k] - 0.5);
+        f.inv_tau[k] = (float)ctx->L.inv_tau[k];
+        f.inv_nu[k] = (float)ctx->L.inv_nu[k];
+        f.rho0[k] = (float)p->rho0[k];
+    }
+    ctx->L.tau_equal = p->tau[0] == p->tau[1];
+    f.G = (float)p->G;
+    for (int d = 0; d < 3; d++) {
+        f.body_force[d] = (float)p->body_force[d];
+        f.wall_u_lo[d] = (float)p->wall_u_lo[d];
+        f.wall_u_hi[d] = (float)p->wall_u_hi[d];
     }
     ctx->L.per[0] = 1;
     ctx->L.per[1] = 1;
@@ -375,10 +388,14 @@ int lb_step(lb_ctx* ctx, int nsteps) {
     for (int t = 0; t < nsteps; t++) {
         int n = 0;
         n += launch_remap(L, ctx->prec, s);           // destroy / create (Eqs. 24, 25)
-        // rho^k (Eq. 6): of every fluid node when particles need virtual
-        // densities (Eq. 20), else of the planes next to the walls only (the
-        // fused kernel then forms its halo densities itself)
+        // rho^k (Eq. 6) of every fluid node when particles need virtual
+        // densities (Eq. 20); with omega = 1 the pass also writes j^k, and
+        // the fused kernel collides from the momenta instead of re-reading the
+        // populations.  Without particles only the planes next to the walls
+        // (the fused kernel then forms its halo densities itself).
+        const bool unit = L.P.tau[0] == 1.0 && L.P.tau[1] == 1.0;
         L.dense_psi = L.nc > 0;
+        L.dense_mom = L.dense_psi && unit && !ctx->tma_ok;
         if (L.dense_psi) n += launch_density(L, ctx->prec, s);
         else n += launch_shell_density(L, ctx->prec, s);
         n += launch_wall_psi(L, ctx->prec, s);         // wall densities

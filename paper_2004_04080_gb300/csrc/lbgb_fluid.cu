@@ -10,6 +10,8 @@
 #include <cuda.h>
 #include <stddef.h>
 
+#include <type_traits>
+
 #include "lbgb_internal.cuh"
 
 namespace lbgb {
@@ -35,29 +37,46 @@ __global__ void k_init(Lattice L, const double* __restrict__ stage) {
 }
 
 // rho^k on fluid nodes (0 on particle nodes) into psi; flags non-finite or
-// negative densities.
-template <int PREC>
+// negative densities.  MOM: also j^k (Eq. 7) into the momentum rows
+// mom[3k + d][s] (0 on particle nodes), for the omega = 1 collision.
+template <int PREC, bool MOM>
 __global__ void k_density(Lattice L) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= L.N) return;
     C* psi = (C*)L.psi;
+    C* mom = (C*)L.mom;
     if (L.mask[s]) {
         psi[s] = 0;
         psi[L.N + s] = 0;
+        if (MOM)
+#pragma unroll
+            for (int a = 0; a < 6; a++) mom[a * L.pstride + s] = 0;
         return;
     }
     const S* f = (const S*)L.f_cur;
     C rho[2];
 #pragma unroll
     for (int k = 0; k < 2; k++) {
-        C r = 0;
+        C r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
-        for (int i = 0; i < Q; i++)
-            r += ld_pop(f + ((long long)(k * Q + i)) * L.pstride + s, pop_shift<S, C>(L, k, i));
+        for (int i = 0; i < Q; i++) {
+            C v = ld_pop(f + ((long long)(k * Q + i)) * L.pstride + s, pop_shift<S, C>(L, k, i));
+            r += v;
+            if (MOM) {
+                if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
+                if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
+                if (cz(i) > 0) jz += v; else if (cz(i) < 0) jz -= v;
+            }
+        }
         rho[k] = r;
         psi[k * L.N + s] = r;
+        if (MOM) {
+            mom[(3 * k + 0) * L.pstride + s] = jx;
+            mom[(3 * k + 1) * L.pstride + s] = jy;
+            mom[(3 * k + 2) * L.pstride + s] = jz;
+        }
     }
     if (!(rho[0] >= C(0) && rho[1] >= C(0) && rho[0] < C(1e30) && rho[1] < C(1e30)))
         atomicOr(L.flags, FLAG_NONFINITE);
@@ -275,7 +294,7 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
             // stores write the rest equilibrium)
 #pragma unroll
             for (int k = 0; k < 2; k++) {
-                own.rho[k] = C(L.P.rho0[k]);
+                own.rho[k] = prm<C>(L.P.rho0[k], L.PF.rho0[k]);
                 own.j[k][0] = own.j[k][1] = own.j[k][2] = C(0);
             }
             if (want_own)
@@ -342,52 +361,60 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
     return loaded;
 }
 
-// Collide and push the own site of plane z (slots: below, here, above); the
-// populations are in the stage, rho and j in `m`.  A particle node of the
-// tile (`solid`) runs the same instructions and stores the rest equilibrium
-// w_i rho0^k into its own slots of f(t+1) instead: no link pushes into a
-// particle node, so without this its slots would stay unwritten and the
-// 32-byte sectors they share with fluid nodes along every row through a
-// particle would be written only in part (each then costs a DRAM read to
-// merge); sharing the store instructions with the fluid lanes of the warp
-// keeps the number of store requests that of a fluid warp.  The values are
-// never read: a node released by a particle is refilled (Eq. 25) before it
-// streams.  (Its arithmetic uses finite moments: the populations of a
-// particle node are the stored rest equilibrium.)
-template <int PREC, bool UNIT, typename SH, typename PopFn>
-__device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int (&sl)[3], int x, int y, int z,
-                                             const OwnSite<PREC>& m, bool solid, PopFn pop,
-                                             int& pforce, typename Prec<PREC>::C (&Fp)[3],
-                                             typename Prec<PREC>::C (&Tp)[3]) {
-    typedef typename Prec<PREC>::S S;
-    typedef typename Prec<PREC>::C C;
-    int tx = threadIdx.x, ty = threadIdx.y;
-    // Links that bounce back (Eqs. 9, 17, 18): their neighbour is a particle
-    // node or lies beyond a wall.  Nearly every warp holds such a site, so the
-    // store of each link selects its destination (the neighbour's slot i, or
-    // the own slot opp(i) with the wall-velocity term) instead of branching.
-    // The particle of the first particle link gives U0 (its loads are issued
-    // first, to overlap the force and collision arithmetic); a site next to
-    // two particles rewrites the links into the second one afterwards.
-    unsigned bb = 0, pm = 0;  // bounce-back links; links into particle p0
-    int p0 = -1;
-    bool multi = false;
+// Links of a site that bounce back (Eqs. 9, 17, 18): their neighbour is a
+// particle node or lies beyond a wall.  p0 is the particle of the first
+// particle link, pm the links into p0; a site next to two particles (multi)
+// rewrites the links into the second one after the main store loop.
+struct LinkInfo {
+    unsigned bb, pm;
+    int p0;
+    bool multi;
+};
+
+template <typename SH>
+__device__ __forceinline__ LinkInfo link_info(const SH& sh, const int (&sl)[3], int tx, int ty, bool solid) {
+    LinkInfo li = {0u, 0u, -1, false};
 #pragma unroll
     for (int i = 1; i < Q; i++) {
         int nd = sh.nd[sl[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)];
-        bb |= (unsigned)(nd != ND_FLUID) << i;
+        li.bb |= (unsigned)(nd != ND_FLUID) << i;
         if (nd >= 0) {
-            multi |= p0 >= 0 && nd != p0;
-            p0 = p0 < 0 ? nd : p0;
-            pm |= (unsigned)(nd == p0) << i;
+            li.multi |= li.p0 >= 0 && nd != li.p0;
+            li.p0 = li.p0 < 0 ? nd : li.p0;
+            li.pm |= (unsigned)(nd == li.p0) << i;
         }
     }
-    bb = solid ? 0u : bb;
-    pm = solid ? 0u : pm;
-    multi = multi && !solid;
-    // (particle 0 stands in when no link reaches a particle: its record
-    // exists whenever the lattice has room for particles, and U0 is unused)
-    const ParticleRef<C> pref = particle_load<C>(L, p0 >= 0 ? p0 : 0);
+    if (solid) li = LinkInfo{0u, 0u, li.p0, false};
+    return li;
+}
+
+// Collide and push the own site of plane z (slots: below, here, above); the
+// populations are in the stage, rho and j in `m`; `li` and `pref` are the
+// site's links and the record of particle li.p0 (any record when li.pm = 0:
+// U0 is then unused).  A particle node of the tile (`solid`) runs the same
+// instructions and stores the rest equilibrium w_i rho0^k into its own slots
+// of f(t+1) instead: no link pushes into a particle node, so without this its
+// slots would stay unwritten and the 32-byte sectors they share with fluid
+// nodes along every row through a particle would be written only in part
+// (each then costs a DRAM read to merge); sharing the store instructions with
+// the fluid lanes of the warp keeps the number of store requests that of a
+// fluid warp.  The values are never read: a node released by a particle is
+// refilled (Eq. 25) before it streams.  (Its arithmetic uses finite moments:
+// the populations of a particle node are the stored rest equilibrium.)
+// Nearly every warp holds a bounce-back site, so the store of each link
+// selects its destination (the neighbour's slot i, or the own slot opp(i)
+// with the wall-velocity term) instead of branching.
+template <int PREC, bool UNIT, typename SH, typename PopFn>
+__device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int (&sl)[3], int x, int y, int z,
+                                             const OwnSite<PREC>& m, bool solid, PopFn pop, const LinkInfo& li,
+                                             const ParticleRef<typename Prec<PREC>::C>& pref, int& pforce,
+                                             typename Prec<PREC>::C (&Fp)[3], typename Prec<PREC>::C (&Tp)[3]) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    int tx = threadIdx.x, ty = threadIdx.y;
+    const unsigned bb = li.bb, pm = li.pm;
+    const int p0 = li.p0;
+    const bool multi = li.multi;
     // Eq. 11 (repulsive sign) + body force from the shared-memory psi planes
     C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};
 #pragma unroll
@@ -401,10 +428,10 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
         if (cz(i)) { sA[2] += C(cz(i)) * w * pa; sB[2] += C(cz(i)) * w * pb; }
     }
     C F[2][3];
-    C G = C(L.P.G);
+    C G = prm<C>(L.P.G, L.PF.G);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        C g = C(L.P.body_force[d]);
+        C g = prm<C>(L.P.body_force[d], L.PF.body_force[d]);
         F[0][d] = -G * m.rho[0] * sB[d] + m.rho[0] * g;
         F[1][d] = -G * m.rho[1] * sA[d] + m.rho[1] * g;
     }
@@ -456,9 +483,9 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
     C V[3][3];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        V[0][d] = wall_lo ? C(L.P.wall_u_lo[d]) : U0[d];
+        V[0][d] = wall_lo ? prm<C>(L.P.wall_u_lo[d], L.PF.wall_u_lo[d]) : U0[d];
         V[1][d] = U0[d];
-        V[2][d] = wall_hi ? C(L.P.wall_u_hi[d]) : U0[d];
+        V[2][d] = wall_hi ? prm<C>(L.P.wall_u_hi[d], L.PF.wall_u_hi[d]) : U0[d];
     }
     // destinations as 32-bit element offsets from the base of the plane pair
     // (2j-1, 2j): plane 2j adds ps; sites < 2^31 and ps < 2^31 keep them in range
@@ -483,7 +510,7 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
 #pragma unroll
             for (int k = 0; k < 2; k++)
                 st_pop((S*)(fnb + (unsigned long long)ps * (unsigned)(k * Q * (int)sizeof(S))) + s,
-                       solid ? wgt<C>(0) * C(L.P.rho0[k]) : fs[k], pop_shift<S, C>(L, k, 0));
+                       solid ? wgt<C>(0) * prm<C>(L.P.rho0[k], L.PF.rho0[k]) : fs[k], pop_shift<S, C>(L, k, 0));
             continue;
         }
         const int lo = (i & 1) ? i : i - 1;  // first plane of the pair
@@ -502,7 +529,7 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
         for (int k = 0; k < 2; k++) {
             S* base = (S*)(fnb + (unsigned long long)ps * (unsigned)((k * Q + lo) * (int)sizeof(S)));
             const C fb = fs[k] + B[k][c] * cw;
-            st_pop(base + off, solid ? wgt<C>(i) * C(L.P.rho0[k]) : fb, pop_shift<S, C>(L, k, i));
+            st_pop(base + off, solid ? wgt<C>(i) * prm<C>(L.P.rho0[k], L.PF.rho0[k]) : fb, pop_shift<S, C>(L, k, i));
             fl += fs[k] + fb;
         }
         fl = (pm >> i) & 1u ? fl : C(0);
@@ -583,8 +610,13 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k
         C Fp[3] = {0, 0, 0}, Tp[3] = {0, 0, 0};
         if (act) {
             int sl[3] = {lo, mid, hi};
-            collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, cur, sh.nd[mid][ty + 1][tx + 1] != ND_FLUID,
-                                     [&](int q) { return &sh.stage[q][tid]; }, pf, Fp, Tp);
+            const bool solid = sh.nd[mid][ty + 1][tx + 1] != ND_FLUID;
+            const LinkInfo li = link_info(sh, sl, tx, ty, solid);
+            // (particle 0 stands in when no link reaches a particle: its
+            // record exists whenever the lattice has room for particles)
+            const ParticleRef<C> pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
+            collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, cur, solid,
+                                     [&](int q) { return &sh.stage[q][tid]; }, li, pref, pf, Fp, Tp);
         }
         commit_link_forces<C>(L, pf, Fp, Tp);
         __syncthreads();
@@ -611,17 +643,29 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)_
 // plane z collides.  One barrier per plane; the population stage is double
 // buffered.  Completion is the copy unit's own wait (cp.async.wait_all),
 // not a spin.
-constexpr int APSI = 4;  // psi / node-code planes held: z-1, z, z+1 and the one in flight
 
 constexpr int ASYNC_TY = 8;  // tile rows of the copy-pipelined kernel
 
-template <int PREC, int TY>
+// MOM: the staged rows are the momenta j^k (3 per component, written by the
+// density pass) instead of the 2 x 19 populations; only for omega = 1, where
+// the post-collision state is f^eq(rho^k, us^k) (Eq. 16) and needs no
+// population of its own site.
+// MOM also stages, one plane ahead, the record of the particle each boundary
+// site bounces on (FP32 forms: integer cell, offset, v, omega as 12 words;
+// FP64: r, v, omega), so that no dependent L2 load sits inside the collision.
+template <int PREC, int TY, bool MOM>
 struct AsyncShared {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
-    S stage[2][2 * Q][FTX * TY];
-    C psi[APSI][2][TY + 2][RW];
-    int nd[APSI][TY + 2][RW];
+    typedef typename std::conditional<MOM, C, S>::type E;
+    typedef typename std::conditional<sizeof(C) == 8, double, unsigned>::type PW;
+    static constexpr int ROWS = MOM ? 6 : 2 * Q;
+    static constexpr int NSLOT = MOM ? 5 : 4;  // psi planes held
+    static constexpr int PWORDS = sizeof(C) == 8 ? 9 : 12;
+    E stage[2][ROWS][FTX * TY];
+    C psi[NSLOT][2][TY + 2][RW];
+    int nd[NSLOT][TY + 2][RW];
+    PW prec[MOM ? 2 : 1][MOM ? PWORDS : 1][MOM ? FTX * TY : 1];
 };
 
 __device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
@@ -643,13 +687,17 @@ constexpr int async_x_multiple() {
     return 16 / (int)sizeof(typename Prec<PREC>::S) < 4 ? 4 : 16 / (int)sizeof(typename Prec<PREC>::S);
 }
 
-template <int PREC, bool UNIT, int TY>
-__global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fused_async(Lattice L, int zc) {
+template <int PREC, bool UNIT, int TY, bool MOM>
+__global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : (MOM ? 24 : 16) / TY))
+    k_fused_async(Lattice L, int zc) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
+    typedef AsyncShared<PREC, TY, MOM> SH;
+    typedef typename SH::E E;
+    static_assert(!MOM || UNIT, "the momentum-staged form needs omega = 1");
     constexpr int NT = FTX * TY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    AsyncShared<PREC, TY>& sh = *reinterpret_cast<AsyncShared<PREC, TY>*>(smem_raw);
+    SH& sh = *reinterpret_cast<SH*>(smem_raw);
     const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * TY;
     const int W = min(FTX, L.nx - x0), H = min(TY, L.ny - y0);
     const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, L.nz);
@@ -657,7 +705,7 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fu
     const bool act = tx < W && ty < H;
     const long long nxy = (long long)L.nx * L.ny;
     const C* psig = (const C*)L.psi;
-    auto slot_of = [&](int p) { return (p - z0 + 1) & (APSI - 1); };
+    auto slot_of = [&](int p) { return (p - z0 + 1) % SH::NSLOT; };
     // fixed per thread: its own tile position and, for the first 2(W+2) + 2H
     // threads, one position of the ring (periodic images at the edges)
     auto wrap_xy = [&](int lx, int ly) {
@@ -707,62 +755,132 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fu
         if (act) put(ty + 1, tx + 1, zoff + own_xy);
         if (has_ring) put(rly + 1, rlx + 1, zoff + ring_xy);
     };
-    // the 2 x 19 population rows of the tile of plane p into stage buffer b:
-    // lane tx copies 16-byte chunk tx % LPP of its row in planes tx / LPP,
-    // tx / LPP + PPP, ...
-    constexpr int EPC = 16 / (int)sizeof(S);  // elements per 16-byte chunk
-    constexpr int LPP = FTX / EPC;            // lanes per population row
-    constexpr int PPP = FTX / LPP;            // population planes per pass
+    // the staged rows (2 x 19 populations, or the 6 momenta) of the tile of
+    // plane p into stage buffer b: lane tx copies 16-byte chunk tx % LPP of
+    // its row in arrays tx / LPP, tx / LPP + PPP, ...
+    constexpr int EPC = 16 / (int)sizeof(E);  // elements per 16-byte chunk
+    constexpr int LPP = FTX / EPC;            // lanes per row
+    constexpr int PPP = FTX / LPP;            // arrays per pass
     const int chunk = tx % LPP, plane0 = tx / LPP;
     const bool copies = ty < H && chunk * EPC < W;
     const long long row_off = (long long)(x0 + chunk * EPC) + (long long)L.nx * (y0 + ty);
     auto issue_pops = [&](int p, int b) {
         if (!copies) return;
-        const char* src = (const char*)L.f_cur +
-                          ((long long)plane0 * L.pstride + row_off + nxy * p) * (long long)sizeof(S);
-        const long long step = (long long)PPP * L.pstride * (long long)sizeof(S);
-        S* dst = &sh.stage[b][plane0][ty * FTX + chunk * EPC];
+        const char* src = (const char*)(MOM ? L.mom : L.f_cur) +
+                          ((long long)plane0 * L.pstride + row_off + nxy * p) * (long long)sizeof(E);
+        const long long step = (long long)PPP * L.pstride * (long long)sizeof(E);
+        E* dst = &sh.stage[b][plane0][ty * FTX + chunk * EPC];
 #pragma unroll
-        for (int pl = plane0; pl < 2 * Q; pl += PPP) {
+        for (int pl = plane0; pl < SH::ROWS; pl += PPP) {
             cp_async_16(dst, src);
             src += step;
             dst += PPP * NT;
         }
     };
-    issue_psi(z0 - 1);
-    issue_psi(z0);
-    issue_psi(z0 + 1);
+    // MOM: links of the own site of plane p and the copy of its particle record
+    auto prefetch = [&](int p, int b) {
+        int sl[3] = {slot_of(p - 1), slot_of(p), slot_of(p + 1)};
+        const LinkInfo li = link_info(sh, sl, tx, ty, sh.nd[slot_of(p)][ty + 1][tx + 1] != ND_FLUID);
+        if (act && li.pm) {
+            const int q = li.p0;
+            if (sizeof(C) == 8) {
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    cp_async_8(&sh.prec[b][d][tid], L.pos + 3 * q + d);
+                    cp_async_8(&sh.prec[b][3 + d][tid], L.vel + 3 * q + d);
+                    cp_async_8(&sh.prec[b][6 + d][tid], L.omg + 3 * q + d);
+                }
+            } else {
+#pragma unroll
+                for (int d = 0; d < 3; d++) cp_async_4(&sh.prec[b][d][tid], L.ipos + 3 * q + d);
+#pragma unroll
+                for (int j = 0; j < 9; j++) cp_async_4(&sh.prec[b][3 + j][tid], L.fsnap + 9 * q + j);
+            }
+        }
+        return li;
+    };
+    auto staged_record = [&](int b) {
+        ParticleRef<C> r;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            if (sizeof(C) == 8) {
+                double q = (double)sh.prec[b][d][tid];
+                r.ip[d] = (int)floor(q);
+                r.fr[d] = C(q - (double)r.ip[d]);
+                r.v[d] = C((double)sh.prec[b][3 + d][tid]);
+                r.w[d] = C((double)sh.prec[b][6 + d][tid]);
+            } else {
+                r.ip[d] = (int)sh.prec[b][d][tid];
+                r.fr[d] = C(__uint_as_float((unsigned)sh.prec[b][3 + d][tid]));
+                r.v[d] = C(__uint_as_float((unsigned)sh.prec[b][6 + d][tid]));
+                r.w[d] = C(__uint_as_float((unsigned)sh.prec[b][9 + d][tid]));
+            }
+        }
+        return r;
+    };
+    constexpr int AHEAD = MOM ? 3 : 2;  // psi planes issued ahead of the collided one
+    for (int p = z0 - 1; p < z0 + AHEAD; p++)
+        if (p <= z1) issue_psi(p);
     issue_pops(z0, 0);
     cp_async_commit();
+    LinkInfo li_next = {0u, 0u, -1, false};
+    if (MOM) {
+        cp_async_wait_all();
+        __syncthreads();
+        li_next = prefetch(z0, 0);
+        cp_async_commit();
+    }
     for (int z = z0; z < z1; z++) {
         cp_async_wait_all();
         __syncthreads();
         const int b = (z - z0) & 1;
         if (z + 1 < z1) issue_pops(z + 1, b ^ 1);
-        if (z + 2 <= z1) issue_psi(z + 2);
+        if (z + AHEAD <= z1) issue_psi(z + AHEAD);
+        const LinkInfo li_cur = li_next;
+        if (MOM && z + 1 < z1) li_next = prefetch(z + 1, b ^ 1);
         cp_async_commit();
         int pf = -1;
         C Fp[3] = {0, 0, 0}, Tp[3] = {0, 0, 0};
         if (act) {
             const int mid = slot_of(z);
             OwnSite<PREC> m;
+            if (MOM) {
+                // rho^k is the own psi entry of a fluid node (same sum as Eq. 6 here)
 #pragma unroll
-            for (int k = 0; k < 2; k++) {
-                C r = 0, jx = 0, jy = 0, jz = 0;
+                for (int k = 0; k < 2; k++) {
+                    m.rho[k] = sh.psi[mid][k][ty + 1][tx + 1];
 #pragma unroll
-                for (int i = 0; i < Q; i++) {
-                    C v = ld_pop(&sh.stage[b][k * Q + i][tid], pop_shift<S, C>(L, k, i));
-                    r += v;
-                    if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
-                    if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
-                    if (cz(i) > 0) jz += v; else if (cz(i) < 0) jz -= v;
+                    for (int d = 0; d < 3; d++) m.j[k][d] = C(sh.stage[b][3 * k + d][tid]);
                 }
-                m.rho[k] = r;
-                m.j[k][0] = jx; m.j[k][1] = jy; m.j[k][2] = jz;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 2; k++) {
+                    C r = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+                    for (int i = 0; i < Q; i++) {
+                        C v = ld_pop((const S*)&sh.stage[b][k * Q + i][tid], pop_shift<S, C>(L, k, i));
+                        r += v;
+                        if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
+                        if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
+                        if (cz(i) > 0) jz += v; else if (cz(i) < 0) jz -= v;
+                    }
+                    m.rho[k] = r;
+                    m.j[k][0] = jx; m.j[k][1] = jy; m.j[k][2] = jz;
+                }
             }
             int sl[3] = {slot_of(z - 1), mid, slot_of(z + 1)};
-            collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, m, sh.nd[mid][ty + 1][tx + 1] != ND_FLUID,
-                                     [&](int q) { return &sh.stage[b][q][tid]; }, pf, Fp, Tp);
+            const bool solid = sh.nd[mid][ty + 1][tx + 1] != ND_FLUID;
+            LinkInfo li;
+            ParticleRef<C> pref;
+            if (MOM) {
+                li = li_cur;
+                pref = staged_record(b);
+            } else {
+                li = link_info(sh, sl, tx, ty, solid);
+                pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
+            }
+            collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, m, solid,
+                                     [&](int q) { return (const S*)&sh.stage[b][q][tid]; }, li, pref, pf, Fp, Tp);
         }
         commit_link_forces<C>(L, pf, Fp, Tp);
     }
@@ -970,8 +1088,12 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_tma(Lattice L, int zc, const _
                 m.rho[k] = r;
                 m.j[k][0] = jx; m.j[k][1] = jy; m.j[k][2] = jz;
             }
-            collide_site<PREC, false>(L, sh, sl, x0 + tx, y0 + ty, z, m, sh.nd[mid][ty + 1][tx + 1] != ND_FLUID,
-                                      [&](int q) { return &sh.buf[b][q][ty + 1][tx + TG::PAD]; }, pf, Fp, Tp);
+            const bool solid = sh.nd[mid][ty + 1][tx + 1] != ND_FLUID;
+            const LinkInfo li = link_info(sh, sl, tx, ty, solid);
+            const ParticleRef<C> pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
+            collide_site<PREC, false>(L, sh, sl, x0 + tx, y0 + ty, z, m, solid,
+                                      [&](int q) { return &sh.buf[b][q][ty + 1][tx + TG::PAD]; }, li, pref, pf, Fp,
+                                      Tp);
         }
         commit_link_forces<C>(L, pf, Fp, Tp);
         __syncthreads();
@@ -1124,7 +1246,11 @@ int launch_init_fields(const Lattice& L, int prec, const double* stage, cudaStre
 }
 
 int launch_density(const Lattice& L, int prec, cudaStream_t st) {
-    DISPATCH(prec, (k_density<P><<<nblk(L.N, 256), 256, 0, st>>>(L)));
+    if (L.dense_mom) {
+        DISPATCH(prec, (k_density<P, true><<<nblk(L.N, 256), 256, 0, st>>>(L)));
+    } else {
+        DISPATCH(prec, (k_density<P, false><<<nblk(L.N, 256), 256, 0, st>>>(L)));
+    }
     return 1;
 }
 
@@ -1201,29 +1327,31 @@ static int z_chunks(const Lattice& L, int tiles, int per_sm, int zmin) {
     return best;
 }
 
-template <int P>
-static int launch_fused_async(const Lattice& L, bool unit, cudaStream_t st) {
+template <int P, bool UNIT, bool MOM>
+static int launch_fused_async_t(const Lattice& L, cudaStream_t st) {
     constexpr int TY = ASYNC_TY, NT = FTX * TY;
-    static bool attr_set[2] = {false, false};
-    static int per_sm[2] = {0, 0};
-    const size_t smem = sizeof(AsyncShared<P, TY>);
-    if (!attr_set[unit]) {
-        if (unit) {
-            cudaFuncSetAttribute(k_fused_async<P, true, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[unit], k_fused_async<P, true, TY>, NT, smem);
-        } else {
-            cudaFuncSetAttribute(k_fused_async<P, false, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[unit], k_fused_async<P, false, TY>, NT, smem);
-        }
-        if (per_sm[unit] < 1) per_sm[unit] = 1;
-        attr_set[unit] = true;
+    typedef AsyncShared<P, TY, MOM> SH;
+    static bool attr_set = false;
+    static int per_sm = 0;
+    const size_t smem = sizeof(SH);
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_fused_async<P, UNIT, TY, MOM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_async<P, UNIT, TY, MOM>, NT, smem);
+        if (per_sm < 1) per_sm = 1;
+        attr_set = true;
     }
     int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + TY - 1) / TY);
-    int zc = z_chunks(L, tiles, per_sm[unit], 8);
+    int zc = z_chunks(L, tiles, per_sm, 8);
     dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
-    if (unit) k_fused_async<P, true, TY><<<grid, dim3(FTX, TY), smem, st>>>(L, zc);
-    else k_fused_async<P, false, TY><<<grid, dim3(FTX, TY), smem, st>>>(L, zc);
+    k_fused_async<P, UNIT, TY, MOM><<<grid, dim3(FTX, TY), smem, st>>>(L, zc);
     return 1;
+}
+
+template <int P>
+static int launch_fused_async(const Lattice& L, bool unit, cudaStream_t st) {
+    if (unit && L.dense_mom) return launch_fused_async_t<P, true, true>(L, st);
+    if (unit) return launch_fused_async_t<P, true, false>(L, st);
+    return launch_fused_async_t<P, false, false>(L, st);
 }
 
 int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st) {
@@ -1231,9 +1359,14 @@ int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st) {
     // population chunks need nx to be a multiple of 16 bytes of elements)
     if (L.dense_psi) {
         bool unit = L.P.tau[0] == 1.0 && L.P.tau[1] == 1.0;
-        if (prec == LB_FP32 && L.nx % async_x_multiple<LB_FP32>() == 0) return launch_fused_async<LB_FP32>(L, unit, st);
-        if (prec == LB_FP16 && L.nx % async_x_multiple<LB_FP16>() == 0) return launch_fused_async<LB_FP16>(L, unit, st);
-        if (prec == LB_FP64 && L.nx % async_x_multiple<LB_FP64>() == 0) return launch_fused_async<LB_FP64>(L, unit, st);
+        // the momentum rows are 4- or 8-byte values: any nx (a multiple of 4) fits the chunks
+        bool mom = unit && L.dense_mom;
+        if (prec == LB_FP32 && (mom || L.nx % async_x_multiple<LB_FP32>() == 0))
+            return launch_fused_async<LB_FP32>(L, unit, st);
+        if (prec == LB_FP16 && (mom || L.nx % async_x_multiple<LB_FP16>() == 0))
+            return launch_fused_async<LB_FP16>(L, unit, st);
+        if (prec == LB_FP64 && (mom || L.nx % async_x_multiple<LB_FP64>() == 0))
+            return launch_fused_async<LB_FP64>(L, unit, st);
     }
     int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + FTY - 1) / FTY);
     // z chunk: enough blocks to fill the GPU a few times over, at least 8 planes

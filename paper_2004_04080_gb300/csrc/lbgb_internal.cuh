@@ -54,6 +54,20 @@ __device__ __forceinline__ void st_pop(__half* p, float v, float shift) {
 }
 
 // ------------------------------------------------------------- context
+// FP32 copies of the lattice parameters the per-site arithmetic reads: the
+// FP32 forms take these (a conversion from FP64 runs on the FP64 pipe, a
+// small fraction of the FP32 rate), the FP64 form the FP64 originals.
+struct ParamsF {
+    float G, body_force[3], rho0[2], wall_u_lo[3], wall_u_hi[3], inv_tau[2], inv_nu[2];
+};
+
+template <typename C>
+__device__ __forceinline__ C prm(double d, float f);
+template <>
+__device__ __forceinline__ double prm<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float prm<float>(double, float f) { return f; }
+
 // Device-visible view of one lattice (passed by value to every kernel).
 struct Lattice {
     int nx, ny, nz;
@@ -77,11 +91,15 @@ struct Lattice {
     double rmax;       // largest particle radius
     double inv_tau[2]; // 1/tau_k
     double inv_nu[2];  // 1/nu_k, nu_k = (tau_k - 1/2)/3
+    int tau_equal;     // tau_A == tau_B
+    ParamsF PF;        // FP32 copies (see ParamsF)
     int* ipos;         // [n][3] floor of the position (FP32 geometry origin)
     float* fsnap;      // [n][9] position - ipos, v(t-1/2), omega(t-1/2) in FP32
     double* red;       // reduction partials
     int red_blocks;
     int dense_psi;     // psi holds rho^k of every fluid node (a full density pass ran this step)
+    int dense_mom;     // that pass also wrote j^k into mom (omega = 1 collision on momenta)
+    void* mom;         // [6][pstride] of C: j^k_d of every site, row 3k + d
     lb_params P;
 };
 
@@ -145,7 +163,7 @@ __device__ __forceinline__ C feq(int i, C rho, C ux, C uy, C uz, C uu) {
 
 template <typename S, typename C>
 __device__ __forceinline__ C pop_shift(const Lattice& L, int k, int i) {
-    return (sizeof(S) == 2) ? wgt<C>(i) * C(L.P.rho0[k]) : C(0);
+    return (sizeof(S) == 2) ? wgt<C>(i) * prm<C>(L.P.rho0[k], L.PF.rho0[k]) : C(0);
 }
 
 // Load the 2 x 19 populations of one site and form rho^k and j^k
@@ -206,10 +224,10 @@ __device__ __forceinline__ void sc_force(const Lattice& L, const SiteNbr& n, con
         if (cy(i)) { sA[1] += C(cy(i)) * w * pa; sB[1] += C(cy(i)) * w * pb; }
         if (cz(i)) { sA[2] += C(cz(i)) * w * pa; sB[2] += C(cz(i)) * w * pb; }
     }
-    C G = C(L.P.G);
+    C G = prm<C>(L.P.G, L.PF.G);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        C g = C(L.P.body_force[d]);
+        C g = prm<C>(L.P.body_force[d], L.PF.body_force[d]);
         F[0][d] = -G * rho[0] * sB[d] + rho[0] * g;  // component A feels B
         F[1][d] = -G * rho[1] * sA[d] + rho[1] * g;  // component B feels A
     }
@@ -221,20 +239,21 @@ template <typename C>
 __device__ __forceinline__ void mixture(const Lattice& L, const C (&rho)[2], const C (&j)[2][3],
                                         C (&u)[3], C& om) {
     C rt = rho[0] + rho[1];
-    if (L.P.tau[0] == L.P.tau[1]) {
+    if (L.tau_equal) {
         // equal relaxation times: Eq. 14 is sum_k j^k / rho and 1/nubar = 1/nu,
         // so the mixture frequency is exactly 1/tau
         C ir = C(1) / rt;
 #pragma unroll
         for (int d = 0; d < 3; d++) u[d] = (j[0][d] + j[1][d]) * ir;
-        om = C(L.inv_tau[0]);
+        om = prm<C>(L.inv_tau[0], L.PF.inv_tau[0]);
         return;
     }
-    C w0 = C(L.inv_tau[0]), w1 = C(L.inv_tau[1]);
+    C w0 = prm<C>(L.inv_tau[0], L.PF.inv_tau[0]), w1 = prm<C>(L.inv_tau[1], L.PF.inv_tau[1]);
     C iden = C(1) / (w0 * rho[0] + w1 * rho[1]);
 #pragma unroll
     for (int d = 0; d < 3; d++) u[d] = (w0 * j[0][d] + w1 * j[1][d]) * iden;
-    C q = (rho[0] * C(L.inv_nu[0]) + rho[1] * C(L.inv_nu[1])) / rt;  // 1/nubar
+    C q = (rho[0] * prm<C>(L.inv_nu[0], L.PF.inv_nu[0]) + rho[1] * prm<C>(L.inv_nu[1], L.PF.inv_nu[1])) /
+          rt;  // 1/nubar
     om = q / (C(3) + C(0.5) * q);                                     // 1/(3 nubar + 1/2)
 }
 

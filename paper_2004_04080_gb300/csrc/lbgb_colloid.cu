@@ -291,6 +291,15 @@ template <int PREC>
 __global__ void __launch_bounds__(PB) k_remap_classify(Lattice L) {
     typedef typename Prec<PREC>::C C;
     int p = blockIdx.x;
+    // the step adds the link forces (Eqs. 19, 22, 23) and the frontier forces
+    // (Eq. 21) of this step to these with atomics
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        for (int q = 0; q < 3; q++) {
+            L.Fliq[3 * p + q] = 0.0;
+            L.Tliq[3 * p + q] = 0.0;
+            L.Fs[3 * p + q] = 0.0;
+            L.Ts[3 * p + q] = 0.0;
+        }
     PGeo<C> g = pgeo<C>(L, p, 1.5);
     CSum<C> acc[6];
     zero(acc);
@@ -425,70 +434,157 @@ __device__ __forceinline__ uint32_t nbr_solid(const Lattice& L, const SiteNbr& n
     return bits;
 }
 
-// Eq. 20 on each frontier node s of particle p (a node of p with at least one
-// fluid neighbour): psi^k(s) = (1 + zeta^k) sum w_i rho^k / sum w_i over the
-// fluid neighbours, and Eq. 21 (repulsive sign):
-// F_s = -G sum_k psi^k(s) sum w_i rho^kbar(s + c_i) c_i, summed with its
-// torque.  The densities rho^k of the fluid nodes are those of the full
-// density pass of this step (k_density).
+// Eq. 20 on every frontier node s (a particle node with at least one fluid
+// neighbour): psi^k(s) = (1 + zeta^k) sum w_i rho^k / sum w_i over the fluid
+// neighbours, and Eq. 21 (repulsive sign):
+// F_s = -G sum_k psi^k(s) sum w_i rho^kbar(s + c_i) c_i, added with its torque
+// (x_s - r_p) x F_s to F_s, T_s of the owning particle with FP64 atomics (the
+// step zeroes them in k_remap_classify).  The lattice is streamed like the
+// fused step: a 32 x 8 tile marches along z with psi^k and the owner map of
+// three planes (tile + one-site ring) in shared memory, 12 bytes per site in
+// coalesced rows, each plane loaded into registers one plane ahead of its
+// use; the particle nodes of a plane are packed onto consecutive threads
+// before the per-node work, so that one or two warps do it with all lanes
+// busy.  The densities rho^k of the fluid nodes are those of the full density
+// pass of this step (k_density).
+constexpr int VTX = 32, VTY = 8;
+
 template <int PREC>
-__global__ void __launch_bounds__(PB) k_virtual(Lattice L, int store_terms) {
+__global__ void __launch_bounds__(VTX* VTY) k_virtual(Lattice L, int store_terms, int zc) {
     typedef typename Prec<PREC>::C C;
-    int p = blockIdx.x;
-    PGeo<C> g = pgeo<C>(L, p, 1.5);
+    constexpr int NT = VTX * VTY;
+    __shared__ C sps[3][2][VTY + 2][VTX + 2];
+    __shared__ int snd[3][VTY + 2][VTX + 2];
+    __shared__ int cand[NT];
+    __shared__ int wcnt[NT / 32];
+    const int x0 = blockIdx.x * VTX, y0 = blockIdx.y * VTY;
+    const int W = min(VTX, L.nx - x0), H = min(VTY, L.ny - y0);
+    const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, L.nz);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * VTX + tx, lane = tid & 31, warp = tid >> 5;
+    const bool act = tx < W && ty < H;
+    const long long nxy = (long long)L.nx * L.ny;
     C* psi = (C*)L.psi;
-    // the lattice step adds the link forces of this step (Eqs. 19, 22, 23)
-    if (store_terms && threadIdx.x == 0 && threadIdx.y == 0)
-        for (int q = 0; q < 3; q++) {
-            L.Fliq[3 * p + q] = 0.0;
-            L.Tliq[3 * p + q] = 0.0;
+    auto wrap_xy = [&](int lx, int ly) {
+        int X = x0 + lx, Y = y0 + ly;
+        X = X < 0 ? X + L.nx : (X >= L.nx ? X - L.nx : X);
+        Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
+        return X + L.nx * Y;
+    };
+    const int own_xy = wrap_xy(tx, ty);
+    const bool has_ring = tid < 2 * (W + 2) + 2 * H;
+    int rlx, rly;
+    if (tid < W + 2) { rlx = tid - 1; rly = -1; }
+    else if (tid < 2 * (W + 2)) { rlx = tid - (W + 2) - 1; rly = H; }
+    else if (tid < 2 * (W + 2) + H) { rlx = -1; rly = tid - 2 * (W + 2); }
+    else { rlx = W; rly = tid - 2 * (W + 2) - H; }
+    const int ring_xy = has_ring ? wrap_xy(rlx, rly) : 0;
+    // the own and ring entries of plane p, loaded into registers one plane
+    // ahead of their use; a plane beyond a wall has no fluid node
+    struct Entry { int nd; C a, b; };
+    auto fetch = [&](int p, int xy, bool on) {
+        Entry e = {ND_WALL, C(0), C(0)};
+        if (on && !((p < 0 || p >= L.nz) && !L.per[2])) {
+            const int Z = p < 0 ? p + L.nz : (p >= L.nz ? p - L.nz : p);
+            const long long g = nxy * Z + xy;
+            e.nd = L.owner[g];
+            e.a = psi[g];
+            e.b = psi[L.N + g];
         }
-    CSum<C> acc[6];
-    zero(acc);
-    const C G = C(L.P.G), z0 = C(1) + C(L.P.zeta[0]), z1 = C(1) + C(L.P.zeta[1]);
-    // a node of p with a fluid neighbour lies within sqrt(2) of the surface
-    for_shell<C>(L, g, -1.5f, 0.01f, [&](int X, int Y, int Z, long long s, int, int, int, const C (&d)[3]) {
-        if (L.owner[s] != p) return;
-        SiteNbr n = site_nbr(L, X, Y, Z);
-        int m[Q];
-        uint32_t solid = nbr_solid(L, n, m);
-        C num[2] = {0, 0}, den = 0;
-        C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};
+        return e;
+    };
+    auto put = [&](int slot, const Entry& e, int ly, int lx) {
+        snd[slot][ly][lx] = e.nd;
+        sps[slot][0][ly][lx] = e.a;
+        sps[slot][1][ly][lx] = e.b;
+    };
+    const C G = prm<C>(L.P.G, L.PF.G), zA = C(1) + C(L.P.zeta[0]), zB = C(1) + C(L.P.zeta[1]);
+    for (int q = 0; q < 2; q++) {
+        const Entry eo = fetch(z0 - 1 + q, own_xy, act), er = fetch(z0 - 1 + q, ring_xy, has_ring);
+        if (act) put(q, eo, ty + 1, tx + 1);
+        if (has_ring) put(q, er, rly + 1, rlx + 1);
+    }
+    Entry no = fetch(z0 + 1, own_xy, act), nr = fetch(z0 + 1, ring_xy, has_ring);
+    int lo = 0, mid = 1, hi = 2;
+    for (int z = z0; z < z1; z++) {
+        if (act) put(hi, no, ty + 1, tx + 1);
+        if (has_ring) put(hi, nr, rly + 1, rlx + 1);
+        if (z + 2 <= z1) {
+            no = fetch(z + 2, own_xy, act);
+            nr = fetch(z + 2, ring_xy, has_ring);
+        }
+        __syncthreads();
+        // the particle nodes of the plane, packed onto consecutive threads
+        const bool c = act && snd[mid][ty + 1][tx + 1] >= 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, c);
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
 #pragma unroll
-        for (int i = 1; i < Q; i++) {
-            bool fl = m[i] >= 0 && !((solid >> i) & 1u);
-            C ra = fl ? psi[m[i]] : C(0), rb = fl ? psi[L.N + m[i]] : C(0);
-            C w = fl ? wgt<C>(i) : C(0);
-            num[0] += w * ra;
-            num[1] += w * rb;
-            den += w;
-            sA[0] += w * ra * C(cx(i)); sA[1] += w * ra * C(cy(i)); sA[2] += w * ra * C(cz(i));
-            sB[0] += w * rb * C(cx(i)); sB[1] += w * rb * C(cy(i)); sB[2] += w * rb * C(cz(i));
+        for (int w = 0; w < NT / 32; w++) {
+            off += w < warp ? wcnt[w] : 0;
+            tot += wcnt[w];
         }
-        if (!(den > C(0))) return;
-        C pa = z0 * num[0] / den;
-        C pb = z1 * num[1] / den;
-        psi[s] = pa;
-        psi[L.N + s] = pb;
-        if (store_terms) {
-            C fs[3], tq[3];
+        if (c) cand[off + __popc(bal & ((1u << lane) - 1u))] = tid;
+        __syncthreads();
+        for (int k = tid; k < tot; k += NT) {
+            const int t = cand[k], cx0 = t % VTX, cy0 = t / VTX;
+            const int p = snd[mid][cy0 + 1][cx0 + 1];
+            const int sl[3] = {lo, mid, hi};
+            C num[2] = {0, 0}, den = 0;
+            C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};
+#pragma unroll
+            for (int i = 1; i < Q; i++) {
+                const int a = sl[cz(i) + 1], yy = cy0 + 1 + cy(i), xx = cx0 + 1 + cx(i);
+                const bool fl = snd[a][yy][xx] == ND_FLUID;
+                C ra = fl ? sps[a][0][yy][xx] : C(0), rb = fl ? sps[a][1][yy][xx] : C(0);
+                C w = fl ? wgt<C>(i) : C(0);
+                num[0] += w * ra;
+                num[1] += w * rb;
+                den += w;
+                sA[0] += w * ra * C(cx(i)); sA[1] += w * ra * C(cy(i)); sA[2] += w * ra * C(cz(i));
+                sB[0] += w * rb * C(cx(i)); sB[1] += w * rb * C(cy(i)); sB[2] += w * rb * C(cz(i));
+            }
+            if (!(den > C(0))) continue;
+            const long long s = nxy * z + (x0 + cx0) + (long long)L.nx * (y0 + cy0);
+            const C pa = zA * num[0] / den;
+            const C pb = zB * num[1] / den;
+            psi[s] = pa;
+            psi[L.N + s] = pb;
+            if (!store_terms) continue;
+            C fs[3], d[3], tq[3];
+#pragma unroll
             for (int q = 0; q < 3; q++) fs[q] = -G * pa * sB[q] + -G * pb * sA[q];
+            // x_s - r_p (minimum image) from the integer cell and offset of r_p
+            const int xs[3] = {x0 + cx0, y0 + cy0, z}, Ls[3] = {L.nx, L.ny, L.nz};
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                int ip;
+                C fr;
+                if (sizeof(C) == 8) {
+                    double r = L.pos[3 * p + q];
+                    ip = (int)floor(r);
+                    fr = C(r - (double)ip);
+                } else {
+                    ip = L.ipos[3 * p + q];
+                    fr = C(L.fsnap[9 * p + q]);
+                }
+                int dd = xs[q] - ip;
+                if (L.per[q]) {
+                    if (2 * dd > Ls[q]) dd -= Ls[q];
+                    else if (2 * dd < -Ls[q]) dd += Ls[q];
+                }
+                d[q] = C(dd) - fr;
+            }
             crs<C>(d, fs, tq);
 #pragma unroll
             for (int q = 0; q < 3; q++) {
-                acc[q].add(fs[q]);
-                acc[3 + q].add(tq[q]);
+                atomicAdd(L.Fs + 3 * p + q, double(fs[q]));
+                atomicAdd(L.Ts + 3 * p + q, double(tq[q]));
             }
         }
-    });
-    if (!store_terms) return;
-    double out[6];
-    block_reduce<6, C>(acc, out);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        for (int q = 0; q < 3; q++) {
-            L.Fs[3 * p + q] = out[q];
-            L.Ts[3 * p + q] = out[3 + q];
-        }
+        __syncthreads();
+        const int t = lo; lo = mid; mid = hi; hi = t;
+    }
 }
 
 // -------------------------------------------------------- pair forces
@@ -787,7 +883,9 @@ int launch_remap(const Lattice& L, int prec, cudaStream_t st) {
 
 int launch_virtual(const Lattice& L, int prec, int store_terms, cudaStream_t st) {
     if (L.nc <= 0) return 0;
-    DISPATCHC(prec, (k_virtual<P><<<L.nc, PBLK, 0, st>>>(L, store_terms)));
+    const int zc = L.nz < 16 ? L.nz : 16;
+    dim3 grid((L.nx + VTX - 1) / VTX, (L.ny + VTY - 1) / VTY, (L.nz + zc - 1) / zc);
+    DISPATCHC(prec, (k_virtual<P><<<grid, dim3(VTX, VTY), 0, st>>>(L, store_terms, zc)));
     return 1;
 }
 

@@ -211,9 +211,6 @@ constexpr int RW = FTX + 2, RH = FTY + 2;
 
 // shared state of one block: psi^k and node flags of three planes (tile +
 // ring) and the raw populations of the own sites of the plane being collided
-// node codes of the shared planes: a fluid node, a node beyond a wall, or
-// the index (>= 0) of the particle that owns a particle node
-constexpr int ND_FLUID = -1, ND_WALL = -2;
 
 template <int PREC>
 struct FusedShared {

@@ -105,6 +105,11 @@ struct Lattice {
 
 enum { FLAG_NONFINITE = 1, FLAG_OVERLAP = 2, FLAG_TIMEOUT = 4 };
 
+// node codes of the shared-memory planes of the streaming kernels: a fluid
+// node, a node beyond a wall, or the index (>= 0) of the particle that owns a
+// particle node (the owner map holds -1 on fluid nodes)
+constexpr int ND_FLUID = -1, ND_WALL = -2;
+
 // ------------------------------------------------- compensated FP64 sums
 struct NSum {
     double s, c;

@@ -387,7 +387,7 @@ int lb_step(lb_ctx* ctx, int nsteps) {
     CK(cudaMemsetAsync(L.flags, 0, 4, s), "clear flags");
     for (int t = 0; t < nsteps; t++) {
         int n = 0;
-        n += launch_remap(L, ctx->prec, s);           // destroy / create (Eqs. 24, 25)
+        n += launch_remap(L, ctx->prec, ctx->maxc, s);  // destroy / create (Eqs. 24, 25)
         // rho^k (Eq. 6) of every fluid node when particles need virtual
         // densities (Eq. 20); with omega = 1 the pass also writes j^k, and
         // the fused kernel collides from the momenta instead of re-reading the

@@ -18,6 +18,8 @@
 namespace lbgb {
 
 constexpr int BXP = 16, BYP = 8, PB = BXP * BYP;  // particle block
+constexpr double REMAP_PAD = 0.75;
+constexpr unsigned REMAP_GROUPS = 1;  // blocks per particle in the remap kernels
 
 // geometry of particle p in compute type C
 template <typename C>
@@ -90,10 +92,13 @@ __device__ __forceinline__ bool in_shell(const PGeo<C>& g, const C (&d)[3], floa
 }
 
 // Visit the box points of particle p; f(X, Y, Z, s, a, b, c, d) gets the
-// wrapped site, its index, the unwrapped point and its offset from r_p.
+// wrapped site, its index, the unwrapped point and its offset from r_p.  A
+// grid of (particles, groups) splits each box into interleaved groups of
+// planes, so that more independent blocks hide the latency of the loads.
 template <typename C, typename Fn>
 __device__ __forceinline__ void for_box(const Lattice& L, const PGeo<C>& g, Fn&& fn) {
-    for (int zz = 0; zz < g.ext[2]; zz++) {
+    // the planes of the box are shared among the gridDim.y blocks of a particle
+    for (int zz = blockIdx.y; zz < g.ext[2]; zz += gridDim.y) {
         int c = g.lo[2] + zz;
         if (!L.per[2] && (c < 0 || c >= L.nz)) continue;
         int Z = c < 0 ? c + L.nz : (c >= L.nz ? c - L.nz : c);
@@ -106,6 +111,48 @@ __device__ __forceinline__ void for_box(const Lattice& L, const PGeo<C>& g, Fn&&
                 long long s = (long long)X + (long long)L.nx * ((long long)Y + (long long)L.ny * Z);
                 C d[3] = {C(a - g.ip[0]) - g.fr[0], C(b - g.ip[1]) - g.fr[1], C(c - g.ip[2]) - g.fr[2]};
                 fn(X, Y, Z, s, a, b, c, d);
+            }
+        }
+    }
+}
+
+// Visit the box points of particle p whose distance from the centre lies in
+// [R + lo, R + hi) (the in_shell test, so the set is exactly that of a box
+// scan), one (y, z) row of the box per thread: the x range of a row that can
+// reach the shell is found from the row's distance to the centre (one or two
+// intervals, widened by a point on each side), so a thin shell costs its own
+// points instead of the whole box.  Sites are indexed in 32 bits.
+template <typename C, typename Fn>
+__device__ __forceinline__ void for_band(const Lattice& L, const PGeo<C>& g, float lo, float hi, Fn&& fn) {
+    const int tid = threadIdx.y * BXP + threadIdx.x;
+    const int nrow = g.ext[1] * g.ext[2];
+    const float Rin = float(g.R) + lo, Rout = float(g.R) + hi;
+    const float cxr = float(g.ip[0]) + float(g.fr[0]);  // x of the centre (box frame)
+    for (int r = tid; r < nrow; r += PB) {
+        const int b = g.lo[1] + r % g.ext[1], c = g.lo[2] + r / g.ext[1];
+        if (!L.per[2] && (c < 0 || c >= L.nz)) continue;
+        const C dy = C(b - g.ip[1]) - g.fr[1], dz = C(c - g.ip[2]) - g.fr[2];
+        const float q = float(dy) * float(dy) + float(dz) * float(dz);
+        const float ho = Rout * Rout - q;
+        if (ho < -1.f) continue;
+        const float xo = sqrtf(fmaxf(ho, 0.f)) + 1.f;
+        const float hin = Rin > 0.f ? Rin * Rin - q : -1.f;
+        const float xi = hin > 1.f ? sqrtf(hin) - 1.f : 0.f;  // |dx| >= xi can be in the shell
+        const int Y = b < 0 ? b + L.ny : (b >= L.ny ? b - L.ny : b);
+        const int Z = c < 0 ? c + L.nz : (c >= L.nz ? c - L.nz : c);
+        const int row = L.nx * (Y + L.ny * Z);
+        // x with |a - cx| in [xi, xo]: the left and right intervals (one if xi = 0)
+        const int aL0 = (int)floorf(cxr - xo), aL1 = (int)ceilf(cxr - xi);
+        const int aR0 = (int)floorf(cxr + xi), aR1 = (int)ceilf(cxr + xo);
+        const int split = xi > 0.f && aL1 < aR0;
+        for (int part = 0; part < 1 + split; part++) {
+            const int a0 = part == 0 ? aL0 : aR0, a1 = (part == 0 && split) ? aL1 : aR1;
+            for (int a = a0; a <= a1; a++) {
+                const C dx = C(a - g.ip[0]) - g.fr[0];
+                const C d[3] = {dx, dy, dz};
+                if (!in_shell<C>(g, d, lo, hi)) continue;
+                const int X = a < 0 ? a + L.nx : (a >= L.nx ? a - L.nx : a);
+                fn(X, Y, Z, (long long)(row + X), a, b, c, d);
             }
         }
     }
@@ -284,6 +331,9 @@ __global__ void __launch_bounds__(PB) k_map_initial(Lattice L, int first) {
 }
 
 // ------------------------------------------------------------- remap
+// The remap kernels work on the points within 0.65 of the surface (a node
+// changes side only within the distance moved, below 1/2 per step); their
+// box reaches 0.75 beyond the sphere.
 // Classify the points around particle p at its new position r_p(t):
 //   fluid node now inside -> destroy (Eq. 24): its momentum rho u goes to p
 //   node of p now outside -> create (handled by k_remap_create)
@@ -291,16 +341,7 @@ template <int PREC>
 __global__ void __launch_bounds__(PB) k_remap_classify(Lattice L) {
     typedef typename Prec<PREC>::C C;
     int p = blockIdx.x;
-    // the step adds the link forces (Eqs. 19, 22, 23) and the frontier forces
-    // (Eq. 21) of this step to these with atomics
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        for (int q = 0; q < 3; q++) {
-            L.Fliq[3 * p + q] = 0.0;
-            L.Tliq[3 * p + q] = 0.0;
-            L.Fs[3 * p + q] = 0.0;
-            L.Ts[3 * p + q] = 0.0;
-        }
-    PGeo<C> g = pgeo<C>(L, p, 1.5);
+    PGeo<C> g = pgeo<C>(L, p, REMAP_PAD);
     CSum<C> acc[6];
     zero(acc);
     for_box<C>(L, g, [&](int, int, int, long long s, int a, int b, int c, const C (&d)[3]) {
@@ -336,8 +377,8 @@ __global__ void __launch_bounds__(PB) k_remap_classify(Lattice L) {
     block_reduce<6, C>(acc, out);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int m = 0; m < 3; m++) {
-            L.Fd[3 * p + m] = out[m];
-            L.Td[3 * p + m] = out[3 + m];
+            atomicAdd(L.Fd + 3 * p + m, out[m]);
+            atomicAdd(L.Td + 3 * p + m, out[3 + m]);
         }
 }
 
@@ -349,11 +390,11 @@ __global__ void __launch_bounds__(PB) k_remap_create(Lattice L) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
     int p = blockIdx.x;
-    PGeo<C> g = pgeo<C>(L, p, 1.5);
+    PGeo<C> g = pgeo<C>(L, p, REMAP_PAD);
     CSum<C> acc[6];
     zero(acc);
     const int code = 4 * (p + 1) + 2;
-    for_box<C>(L, g, [&](int X, int Y, int Z, long long s, int, int, int, const C (&d)[3]) {
+    for_band<C>(L, g, -0.65f, 0.65f, [&](int X, int Y, int Z, long long s, int, int, int, const C (&d)[3]) {
         if (!in_shell<C>(g, d, -0.65f, 0.65f)) return;
         if (L.evt[s] != code) return;
         SiteNbr n = site_nbr(L, X, Y, Z);
@@ -391,8 +432,8 @@ __global__ void __launch_bounds__(PB) k_remap_create(Lattice L) {
     block_reduce<6, C>(acc, out);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int m = 0; m < 3; m++) {
-            L.Fc[3 * p + m] = out[m];
-            L.Tc[3 * p + m] = out[3 + m];
+            atomicAdd(L.Fc + 3 * p + m, out[m]);
+            atomicAdd(L.Tc + 3 * p + m, out[3 + m]);
         }
 }
 
@@ -401,8 +442,8 @@ template <int PREC>
 __global__ void __launch_bounds__(PB) k_remap_commit(Lattice L) {
     typedef typename Prec<PREC>::C C;
     int p = blockIdx.x;
-    PGeo<C> g = pgeo<C>(L, p, 1.5);
-    for_box<C>(L, g, [&](int, int, int, long long s, int, int, int, const C (&d)[3]) {
+    PGeo<C> g = pgeo<C>(L, p, REMAP_PAD);
+    for_band<C>(L, g, -0.65f, 0.65f, [&](int, int, int, long long s, int, int, int, const C (&d)[3]) {
         if (!in_shell<C>(g, d, -0.65f, 0.65f)) return;
         int e = L.evt[s];
         if (e == 4 * (p + 1) + 1) {
@@ -873,11 +914,18 @@ int launch_map_initial(const Lattice& L, int prec, int first, int count, cudaStr
     return 1;
 }
 
-int launch_remap(const Lattice& L, int prec, cudaStream_t st) {
+int launch_remap(const Lattice& L, int prec, int maxc, cudaStream_t st) {
     if (L.nc <= 0) return 0;
-    DISPATCHC(prec, (k_remap_classify<P><<<L.nc, PBLK, 0, st>>>(L)));
-    DISPATCHC(prec, (k_remap_create<P><<<L.nc, PBLK, 0, st>>>(L)));
-    DISPATCHC(prec, (k_remap_commit<P><<<L.nc, PBLK, 0, st>>>(L)));
+    // the per-particle terms of the step are sums of block partials and of
+    // per-site contributions added with atomics: Fliq, Tliq (contiguous) and
+    // Fd, Td, Fc, Tc, Fs, Ts (contiguous) start from zero
+    const size_t m3 = (size_t)3 * (maxc > 0 ? maxc : 1) * sizeof(double);
+    cudaMemsetAsync(L.Fliq, 0, 2 * m3, st);
+    cudaMemsetAsync(L.Fd, 0, 6 * m3, st);
+    const dim3 grid((unsigned)L.nc, REMAP_GROUPS);
+    DISPATCHC(prec, (k_remap_classify<P><<<grid, PBLK, 0, st>>>(L)));
+    DISPATCHC(prec, (k_remap_create<P><<<grid, PBLK, 0, st>>>(L)));
+    DISPATCHC(prec, (k_remap_commit<P><<<grid, PBLK, 0, st>>>(L)));
     return 3;
 }
 

@@ -289,7 +289,7 @@ int launch_populations_out(const Lattice& L, int prec, int k, int i, double* sta
 int launch_clear_map(const Lattice& L, cudaStream_t st);
 
 int launch_map_initial(const Lattice& L, int prec, int first, int count, cudaStream_t st);
-int launch_remap(const Lattice& L, int prec, cudaStream_t st);
+int launch_remap(const Lattice& L, int prec, int maxc, cudaStream_t st);
 int launch_virtual(const Lattice& L, int prec, int store_terms, cudaStream_t st);
 int launch_pairs_integrate(const Lattice& L, void* cells, size_t cell_cap, cudaStream_t st);
 int launch_snapshot(const Lattice& L, cudaStream_t st);

@@ -34,6 +34,12 @@ STORE = {"fp64": 8, "fp32": 4, "fp16": 2}   # bytes per stored population
 COMPUTE = {"fp64": 8, "fp32": 4, "fp16": 4}  # bytes per psi value
 
 
+def density_bytes(prec, unit):
+    """Algorithmic bytes per site of the full density pass: 2 x 19 populations
+    and the mask byte read, rho^k written, and j^k written when tau = 1."""
+    return 38 * STORE[prec] + 1 + 2 * COMPUTE[prec] + (6 * COMPUTE[prec] if unit else 0)
+
+
 def fused_kernel(prec, nx, particles, unit=True):
     """(name, algorithmic bytes per site) of the fused lattice kernel a step
     launches.  With particles the copy-pipelined kernel follows a full density
@@ -267,7 +273,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2004_04080_gb300.lbgb import LBLattice
+    from paper_2004_04080_gb300.lbgb import LB_KERNEL_DENSITY, LBLattice
     from paper_2004_04080_gb300.workloads import workload
 
     torch.cuda.set_device(local)
@@ -299,6 +305,7 @@ def main():
         barrier()
     launches = lat.launch_count() - launches0
     kern_ms, kern_n = lat.profile_read()
+    dens_ms, dens_n = lat.profile_read(LB_KERNEL_DENSITY)
     lat.profile(False)
     value, ms = replica_mlups(ms, w.n_sites, args.steps, world, dev)
     ms_step = ms / args.steps
@@ -312,6 +319,14 @@ def main():
                 "kernel": kname, "kernel_ms": round(kavg, 4), "alg_bytes_per_site": kbytes,
                 "alg_bytes_per_launch": alg, "peak_kind": peak_kind,
                 "step_frac": round(alg / (ms_step / 1e3) / 1e9 / peak, 4)}
+    if dens_n:
+        unit = tuple(w.params["tau"]) == (1.0, 1.0)
+        dbytes = density_bytes(args.prec, unit)
+        davg = dens_ms / dens_n
+        dach = dbytes * w.n_sites / (davg / 1e3) / 1e9
+        roofline["other_kernels"] = [{"kernel": "k_density", "kernel_ms": round(davg, 4),
+                                      "alg_bytes_per_site": dbytes, "achieved": round(dach, 1),
+                                      "frac": round(dach / peak, 4)}]
 
     # end to end through the public API with pinned host buffers
     N = w.n_sites

@@ -149,13 +149,17 @@ int lb_get_owner(lb_ctx *ctx, int *out);
 
 /* Kernel timing.  While enabled, lb_step records a CUDA event pair on the
  * context stream around every launch of the fused lattice kernel (the
- * collide + Shan-Chen + bounce-back + stream kernel, the dominant one).
- * lb_profile(ctx, 1) enables and clears the record, lb_profile(ctx, 0)
- * disables it; lb_profile_read waits for the recorded events and returns the
- * summed kernel time (ms) and the number of timed launches (at most 16384 are
- * kept per record). */
+ * collide + Shan-Chen + bounce-back + stream kernel, the dominant one) and
+ * around every full density pass (launched when particles are present).
+ * lb_profile(ctx, 1) enables and clears the records, lb_profile(ctx, 0)
+ * disables them; lb_profile_read_kernel waits for the recorded events of one
+ * kernel (LB_KERNEL_FUSED or LB_KERNEL_DENSITY; LB_ERR_ARG otherwise) and
+ * returns its summed time (ms) and the number of timed launches (at most
+ * 16384 are kept per record); lb_profile_read is the fused-kernel record. */
+enum { LB_KERNEL_FUSED = 0, LB_KERNEL_DENSITY = 1 };
 int lb_profile(lb_ctx *ctx, int enable);
 int lb_profile_read(lb_ctx *ctx, double *total_ms, long long *launches);
+int lb_profile_read_kernel(lb_ctx *ctx, int kernel, double *total_ms, long long *launches);
 
 /* ---- Reverse mode (adjoint) of the time step, for immobile particles ----
  * With every particle immobile (added with infinite mass and zero velocity and

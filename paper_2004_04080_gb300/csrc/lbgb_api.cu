@@ -32,8 +32,10 @@ struct lb_ctx {
     void* cells;
     size_t cells_bytes;
     int prof_on;
-    int prof_n;                 // recorded event pairs
+    int prof_n;                 // recorded event pairs around the fused kernel
     cudaEvent_t* prof_ev;       // 2 * PROF_MAX events, created on first use
+    int prof_nd;                // recorded event pairs around the density pass
+    cudaEvent_t* prof_evd;      // 2 * PROF_MAX events
     char err[512];
 };
 
@@ -396,8 +398,17 @@ int lb_step(lb_ctx* ctx, int nsteps) {
         const bool unit = L.P.tau[0] == 1.0 && L.P.tau[1] == 1.0;
         L.dense_psi = L.nc > 0;
         L.dense_mom = L.dense_psi && unit && !ctx->tma_ok;
-        if (L.dense_psi) n += launch_density(L, ctx->prec, s);
-        else n += launch_shell_density(L, ctx->prec, s);
+        if (L.dense_psi) {
+            const bool timed_d = ctx->prof_on && ctx->prof_nd < PROF_MAX;
+            if (timed_d) CK(cudaEventRecord(ctx->prof_evd[2 * ctx->prof_nd], s), "profile event");
+            n += launch_density(L, ctx->prec, s);
+            if (timed_d) {
+                CK(cudaEventRecord(ctx->prof_evd[2 * ctx->prof_nd + 1], s), "profile event");
+                ctx->prof_nd++;
+            }
+        } else {
+            n += launch_shell_density(L, ctx->prec, s);
+        }
         n += launch_wall_psi(L, ctx->prec, s);         // wall densities
         n += launch_virtual(L, ctx->prec, 1, s);       // Eqs. 20, 21
         bool timed = ctx->prof_on && ctx->prof_n < PROF_MAX;
@@ -616,47 +627,69 @@ int lb_adjoint_initial(lb_ctx* ctx, const void* d_adj, double* d_grad) {
     return LB_OK;
 }
 
+static int create_events(lb_ctx* ctx, cudaEvent_t** out) {
+    cudaEvent_t* ev = new (std::nothrow) cudaEvent_t[2 * PROF_MAX];
+    if (!ev) return LB_ERR_NOMEM;
+    for (int i = 0; i < 2 * PROF_MAX; i++) {
+        cudaError_t e = cudaEventCreate(&ev[i]);
+        if (e != cudaSuccess) {
+            for (int j = 0; j < i; j++) cudaEventDestroy(ev[j]);
+            delete[] ev;
+            return cuda_check(ctx, e, "create profile events");
+        }
+    }
+    *out = ev;
+    return LB_OK;
+}
+
+static void destroy_events(cudaEvent_t*& ev) {
+    if (!ev) return;
+    for (int i = 0; i < 2 * PROF_MAX; i++) cudaEventDestroy(ev[i]);
+    delete[] ev;
+    ev = nullptr;
+}
+
 int lb_profile(lb_ctx* ctx, int enable) {
     if (!ctx) return LB_ERR_ARG;
     if (enable && !ctx->prof_ev) {
-        cudaEvent_t* ev = new (std::nothrow) cudaEvent_t[2 * PROF_MAX];
-        if (!ev) return LB_ERR_NOMEM;
-        for (int i = 0; i < 2 * PROF_MAX; i++) {
-            cudaError_t e = cudaEventCreate(&ev[i]);
-            if (e != cudaSuccess) {
-                for (int j = 0; j < i; j++) cudaEventDestroy(ev[j]);
-                delete[] ev;
-                return cuda_check(ctx, e, "create profile events");
-            }
-        }
-        ctx->prof_ev = ev;
+        int rc = create_events(ctx, &ctx->prof_ev);
+        if (rc) return rc;
+    }
+    if (enable && !ctx->prof_evd) {
+        int rc = create_events(ctx, &ctx->prof_evd);
+        if (rc) return rc;
     }
     ctx->prof_on = enable ? 1 : 0;
-    if (enable) ctx->prof_n = 0;
+    if (enable) ctx->prof_n = ctx->prof_nd = 0;
+    return LB_OK;
+}
+
+int lb_profile_read_kernel(lb_ctx* ctx, int kernel, double* total_ms, long long* launches) {
+    if (!ctx || !total_ms || !launches || (kernel != LB_KERNEL_FUSED && kernel != LB_KERNEL_DENSITY))
+        return LB_ERR_ARG;
+    const int n = kernel == LB_KERNEL_FUSED ? ctx->prof_n : ctx->prof_nd;
+    cudaEvent_t* ev = kernel == LB_KERNEL_FUSED ? ctx->prof_ev : ctx->prof_evd;
+    double t = 0.0;
+    for (int i = 0; i < n; i++) {
+        float ms = 0.f;
+        CK(cudaEventSynchronize(ev[2 * i + 1]), "profile sync");
+        CK(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]), "profile elapsed");
+        t += ms;
+    }
+    *total_ms = t;
+    *launches = n;
     return LB_OK;
 }
 
 int lb_profile_read(lb_ctx* ctx, double* total_ms, long long* launches) {
-    if (!ctx || !total_ms || !launches) return LB_ERR_ARG;
-    double t = 0.0;
-    for (int i = 0; i < ctx->prof_n; i++) {
-        float ms = 0.f;
-        CK(cudaEventSynchronize(ctx->prof_ev[2 * i + 1]), "profile sync");
-        CK(cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]), "profile elapsed");
-        t += ms;
-    }
-    *total_ms = t;
-    *launches = ctx->prof_n;
-    return LB_OK;
+    return lb_profile_read_kernel(ctx, LB_KERNEL_FUSED, total_ms, launches);
 }
 
 int lb_destroy(lb_ctx* ctx) {
     if (!ctx) return LB_ERR_ARG;
     cudaStreamSynchronize(ctx->stream);
-    if (ctx->prof_ev) {
-        for (int i = 0; i < 2 * PROF_MAX; i++) cudaEventDestroy(ctx->prof_ev[i]);
-        delete[] ctx->prof_ev;
-    }
+    destroy_events(ctx->prof_ev);
+    destroy_events(ctx->prof_evd);
     delete ctx;
     return LB_OK;
 }

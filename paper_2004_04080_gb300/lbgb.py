@@ -28,7 +28,8 @@ TERMS = {"F_liq": 0, "T_liq": 1, "F_d": 2, "T_d": 3, "F_c": 4, "T_c": 5, "F_s": 
 # every symbol declared in include/lbgb.h
 EXPORTS = ["lb_workspace_bytes", "lb_create", "lb_set_params", "lb_init_fields", "lb_add_colloids",
            "lb_step", "lb_get_fields", "lb_get_colloids", "lb_get_colloid_terms", "lb_get_totals",
-           "lb_get_populations", "lb_get_owner", "lb_profile", "lb_profile_read", "lb_state_bytes",
+           "lb_get_populations", "lb_get_owner", "lb_profile", "lb_profile_read", "lb_profile_read_kernel",
+           "lb_state_bytes",
            "lb_get_state", "lb_set_state", "lb_adjoint_bytes", "lb_adjoint_seed", "lb_adjoint_step",
            "lb_adjoint_initial", "lb_totals_static", "lb_launch_count", "lb_destroy", "lb_last_error"]
 
@@ -79,6 +80,7 @@ def load(build_if_missing: bool = True):
     lib.lb_get_owner.argtypes = [P, I]
     lib.lb_profile.argtypes = [P, C.c_int]
     lib.lb_profile_read.argtypes = [P, D, C.POINTER(C.c_longlong)]
+    lib.lb_profile_read_kernel.argtypes = [P, C.c_int, D, C.POINTER(C.c_longlong)]
     lib.lb_state_bytes.argtypes = [P, C.POINTER(C.c_size_t)]
     lib.lb_get_state.argtypes = [P, P]
     lib.lb_set_state.argtypes = [P, P]
@@ -213,10 +215,21 @@ def lb_profile(h, enable: bool):
     return _check(h, load().lb_profile(h, int(bool(enable))), "lb_profile")
 
 
+LB_KERNEL_FUSED, LB_KERNEL_DENSITY = 0, 1
+
+
 def lb_profile_read(h):
     """(summed fused-kernel time in ms, number of timed launches)"""
     t, n = C.c_double(0.0), C.c_longlong(0)
     _check(h, load().lb_profile_read(h, C.byref(t), C.byref(n)), "lb_profile_read")
+    return t.value, n.value
+
+
+def lb_profile_read_kernel(h, kernel: int):
+    """(summed time in ms, number of timed launches) of LB_KERNEL_FUSED or
+    LB_KERNEL_DENSITY"""
+    t, n = C.c_double(0.0), C.c_longlong(0)
+    _check(h, load().lb_profile_read_kernel(h, int(kernel), C.byref(t), C.byref(n)), "lb_profile_read_kernel")
     return t.value, n.value
 
 
@@ -366,5 +379,5 @@ class LBLattice:
     def profile(self, enable=True):
         lb_profile(self.h, enable)
 
-    def profile_read(self):
-        return lb_profile_read(self.h)
+    def profile_read(self, kernel: int = LB_KERNEL_FUSED):
+        return lb_profile_read_kernel(self.h, kernel)

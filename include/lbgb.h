@@ -196,6 +196,28 @@ int lb_adjoint_seed(lb_ctx *ctx, double weight, void *d_adj, void *d_scratch, do
 int lb_adjoint_step(lb_ctx *ctx, const void *d_state, const void *d_adj_in, void *d_adj_out, void *d_scratch,
                     const double *dJdF, double *grads);
 
+/* As lb_adjoint_step, without a host round trip: d_dJdF is a device array
+ * [n][3] (or NULL) and the call is asynchronous on the context stream.  The
+ * parameter gradients accumulate on the device (in d_scratch; lb_adjoint_seed
+ * clears them) until a call with grads != NULL adds the accumulated sums to
+ * grads (host, 5) and clears them; that call waits for the stream. */
+int lb_adjoint_step_async(lb_ctx *ctx, const void *d_state, const void *d_adj_in, void *d_adj_out,
+                          void *d_scratch, const double *d_dJdF, double *grads);
+
+/* dJ/dF_liq for J = weight * sum_p sqrt(|F_p|^2 + eps^2) (the per-step term
+ * of a mean drag magnitude): d_dJdF[p] = weight F_p / sqrt(|F_p|^2 + eps^2),
+ * d_F and d_dJdF device arrays [n][3] of the current particles; eps >= 0.
+ * Asynchronous on the context stream. */
+int lb_drag_gradient(lb_ctx *ctx, const double *d_F, double weight, double eps, double *d_dJdF);
+
+/* Record during the next nsteps time steps of lb_step: the populations f(t)
+ * at the start of each step into d_states (consecutive blocks of
+ * lb_state_bytes) and the link forces F_liq (Eq. 22) after each step into
+ * d_forces ([nsteps][n][3] doubles); either may be NULL.  Device-to-device
+ * copies on the context stream, so a checkpointed reverse sweep needs no host
+ * round trip per step.  nsteps <= 0 stops a recording. */
+int lb_record(lb_ctx *ctx, void *d_states, double *d_forces, int nsteps);
+
 /* dJ/drho^k(0) for initial populations f = f^eq(rho^k, 0) (Eq. 5):
  * d_grad (device, [2][N] doubles) = sum_i w_i lambda_i(0); zero on particle
  * nodes (their initial fluid is removed by the first map). */

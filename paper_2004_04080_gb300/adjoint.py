@@ -9,8 +9,11 @@ Parameters: tau_A, tau_B, G, zeta_A, zeta_B and the initial densities.
 Every step of the forward and adjoint runs in the library's kernels (through
 the C ABI); this module only schedules them: it stores the populations every
 K = ceil(sqrt(T)) steps during the forward run, and for each segment in
-reverse re-runs the forward steps to rebuild the states, then applies
-lb_adjoint_step backwards.  ``LBObjective`` wraps this as a
+reverse re-runs the forward steps with the library recording f(t) and the
+link forces of every step on the device (lb_record), then applies
+lb_adjoint_step_async backwards with dJ/dF_liq formed on the device
+(lb_drag_gradient); the parameter gradients accumulate on the device and are
+read once at the end.  ``LBObjective`` wraps this as a
 torch.autograd.Function.
 """
 from __future__ import annotations
@@ -50,7 +53,7 @@ class AdjointRunner:
     def forward(self, params: dict, rhoA0, rhoB0, colloids: dict | None):
         """Run T steps; returns (J_drag, A).  ``colloids``: pos, radius (the
         particles are added immobile)."""
-        lat = self.lat
+        lat, torch = self.lat, self.torch
         lat.set_params(**params)
         lat.init_fields(rhoA0, rhoB0)
         self.n = 0
@@ -58,17 +61,22 @@ class AdjointRunner:
             pos = np.asarray(colloids["pos"], dtype=np.float64).reshape(-1, 3)
             self.n = pos.shape[0]
             lat.add_colloids(pos, colloids["radius"], np.full(self.n, np.inf))
+        n = max(self.n, 1)
+        forces = torch.zeros((self.steps, n, 3), dtype=torch.float64, device=lat.device)
+        self.fseg = torch.zeros((self.K, n, 3), dtype=torch.float64, device=lat.device)
+        self.dJdF = torch.zeros((n, 3), dtype=torch.float64, device=lat.device)
         self.checkpoints = {}
-        J = 0.0
-        for t in range(self.steps):
-            if t % self.K == 0:
-                self.checkpoints[t] = self._state()
-            lat.step(1)
+        for start in range(0, self.steps, self.K):
+            self.checkpoints[start] = self._state()
+            m = min(self.K, self.steps - start)
             if self.n:
-                F = lat.term("F_liq")
-                J += float(np.mean(np.sqrt(np.sum(F * F, axis=1) + self.eps ** 2)))
-        J /= self.steps
+                lbgb.lb_record(lat.h, None, forces[start].data_ptr(), m)
+            lat.step(m)
         self.checkpoints[self.steps] = self._state()
+        J = 0.0
+        if self.n:
+            F = forces.cpu().numpy()
+            J = float(np.mean(np.sqrt(np.sum(F * F, axis=2) + self.eps ** 2)))
         A = lbgb.lb_adjoint_seed(lat.h, 0.0, self.adj[0].data_ptr(), self.scratch.data_ptr())
         return J, A
 
@@ -81,21 +89,21 @@ class AdjointRunner:
         lbgb.lb_adjoint_seed(lat.h, gA, cur.data_ptr(), self.scratch.data_ptr())
         grads = np.zeros(5)
         T = self.steps
+        weight = gJ / (T * self.n) if self.n else 0.0
         for start in reversed(range(0, T, self.K)):
             end = min(start + self.K, T)
             lbgb.lb_set_state(lat.h, self.checkpoints[start].data_ptr())
-            forces = []
-            for t in range(start, end):
-                lbgb.lb_get_state(lat.h, self.stack[t - start].data_ptr())
-                lat.step(1)
-                forces.append(lat.term("F_liq") if self.n else None)
+            lbgb.lb_record(lat.h, self.stack.data_ptr(), self.fseg.data_ptr() if self.n else None, end - start)
+            lat.step(end - start)
             for t in reversed(range(start, end)):
-                dJdF = None
+                d_dJdF = None
                 if self.n and gJ != 0.0:
-                    F = forces[t - start]
-                    dJdF = gJ / (T * self.n) * F / np.sqrt(np.sum(F * F, axis=1) + self.eps ** 2)[:, None]
-                lbgb.lb_adjoint_step(lat.h, self.stack[t - start].data_ptr(), cur.data_ptr(), nxt.data_ptr(),
-                                     self.scratch.data_ptr(), dJdF, grads)
+                    lbgb.lb_drag_gradient(lat.h, self.fseg[t - start].data_ptr(), weight, self.eps,
+                                          self.dJdF.data_ptr())
+                    d_dJdF = self.dJdF.data_ptr()
+                last = start == 0 and t == 0
+                lbgb.lb_adjoint_step_async(lat.h, self.stack[t - start].data_ptr(), cur.data_ptr(), nxt.data_ptr(),
+                                           self.scratch.data_ptr(), d_dJdF, grads if last else None)
                 cur, nxt = nxt, cur
         g = torch.empty((2, lat.N), dtype=torch.float64, device=lat.device)
         lbgb.lb_adjoint_initial(lat.h, cur.data_ptr(), g.data_ptr())

@@ -400,12 +400,31 @@ __global__ void __launch_bounds__(128) k_adj_scatter(Lattice L, AdjArgs A) {
     Rout[L.pstride + s] += add[1];
 }
 
+// Sum of the block partials of each parameter gradient, added to the
+// accumulator out[ADJ_VALUES]: warp v sums value v, lane l the partials
+// l, l + 32, ... (Neumaier), then the lanes merge in a fixed order.
 __global__ void k_adj_reduce(const double* red, int nb, double* out) {
-    int v = threadIdx.x;
+    const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (v >= ADJ_VALUES) return;
     NSum t = {0.0, 0.0};
-    for (int b = 0; b < nb; b++) t.add(red[(long long)v * nb + b]);
-    out[v] = t.value();
+    for (int b = lane; b < nb; b += 32) t.add(red[(long long)v * nb + b]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        NSum o = {__shfl_down_sync(0xffffffffu, t.s, off), __shfl_down_sync(0xffffffffu, t.c, off)};
+        if (lane < off) t.merge(o);
+    }
+    if (lane == 0) out[v] += t.value();
+}
+
+// dJ/dF_p for J = weight sum_p sqrt(|F_p|^2 + eps^2)
+__global__ void k_drag_gradient(int n, const double* F, double weight, double eps, double* out) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double f0 = F[3 * p], f1 = F[3 * p + 1], f2 = F[3 * p + 2];
+    double sc = weight / sqrt(f0 * f0 + f1 * f1 + f2 * f2 + eps * eps);
+    out[3 * p] = sc * f0;
+    out[3 * p + 1] = sc * f1;
+    out[3 * p + 2] = sc * f2;
 }
 
 // Seed of the interface measure A = sum_x (1 - phi^2), phi = (rho_A - rho_B)/
@@ -502,7 +521,7 @@ static AdjArgs adj_args(const Lattice& L, int prec, const void* in, void* out, v
     return A;
 }
 
-// one adjoint step; grads_dev receives the 5 parameter gradients of this step
+// one adjoint step; the 5 parameter gradients of this step are added to grads_dev
 int launch_adjoint_step(const Lattice& L, int prec, const void* in, void* out, void* scratch,
                         const double* dJdF_dev, double* grads_dev, cudaStream_t st) {
     AdjArgs A = adj_args(L, prec, in, out, scratch, dJdF_dev);
@@ -524,7 +543,7 @@ int launch_adjoint_step(const Lattice& L, int prec, const void* in, void* out, v
     }
     DISPATCHA(prec, (k_adj_gather<P><<<gg, bx, 0, st>>>(L, A)));
     DISPATCHA(prec, (k_adj_scatter<P><<<gg, bx, 0, st>>>(L, A)));
-    k_adj_reduce<<<1, 32, 0, st>>>(A.red, nb, grads_dev);
+    k_adj_reduce<<<1, 32 * ADJ_VALUES, 0, st>>>(A.red, nb, grads_dev);
     (void)g;
     return n + 3;
 }
@@ -536,6 +555,12 @@ int launch_adjoint_seed(const Lattice& L, int prec, void* adj, void* scratch, do
     DISPATCHA(prec, (k_adj_seed_interface<P><<<nb, 128, 0, st>>>(L, adj, A.red, weight)));
     k_sum_blocks<<<1, 32, 0, st>>>(A.red, nb, value_dev);
     return 2;
+}
+
+int launch_drag_gradient(int n, const double* F, double weight, double eps, double* out, cudaStream_t st) {
+    if (n <= 0) return 0;
+    k_drag_gradient<<<(n + 127) / 128, 128, 0, st>>>(n, F, weight, eps, out);
+    return 1;
 }
 
 int launch_adjoint_initial(const Lattice& L, int prec, const void* adj, double* grad, cudaStream_t st) {

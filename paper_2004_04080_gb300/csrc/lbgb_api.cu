@@ -36,6 +36,9 @@ struct lb_ctx {
     cudaEvent_t* prof_ev;       // 2 * PROF_MAX events, created on first use
     int prof_nd;                // recorded event pairs around the density pass
     cudaEvent_t* prof_evd;      // 2 * PROF_MAX events
+    char* rec_states;           // lb_record: f(t) of each recorded step, or null
+    double* rec_forces;         // lb_record: F_liq after each recorded step, or null
+    int rec_left, rec_i;        // steps still to record, steps recorded
     char err[512];
 };
 
@@ -47,6 +50,8 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 size_t storage_bytes(int prec) { return prec == LB_FP64 ? 8 : (prec == LB_FP32 ? 4 : 2); }
 size_t compute_bytes(int prec) { return prec == LB_FP64 ? 8 : 4; }
+// bytes of one population state (both buffers have this size)
+size_t state_bytes(const lb_ctx* ctx) { return (size_t)2 * Q * ctx->L.pstride * storage_bytes(ctx->prec); }
 
 const int DOUBLES_PER_PARTICLE = 57;  // pos..Ttot, see carve()
 const int RED_BLOCKS = 1024;
@@ -389,6 +394,11 @@ int lb_step(lb_ctx* ctx, int nsteps) {
     CK(cudaMemsetAsync(L.flags, 0, 4, s), "clear flags");
     for (int t = 0; t < nsteps; t++) {
         int n = 0;
+        const bool rec = ctx->rec_left > 0;
+        if (rec && ctx->rec_states)
+            CK(cudaMemcpyAsync(ctx->rec_states + (size_t)ctx->rec_i * state_bytes(ctx), L.f_cur, state_bytes(ctx),
+                               cudaMemcpyDeviceToDevice, s),
+               "record state");
         n += launch_remap(L, ctx->prec, ctx->maxc, s);  // destroy / create (Eqs. 24, 25)
         // rho^k (Eq. 6) of every fluid node when particles need virtual
         // densities (Eq. 20); with omega = 1 the pass also writes j^k, and
@@ -429,6 +439,14 @@ int lb_step(lb_ctx* ctx, int nsteps) {
         L.f_cur = L.f_nxt;
         L.f_nxt = tmp;
         ctx->stepped = 1;
+        if (rec) {
+            if (ctx->rec_forces && L.nc > 0)
+                CK(cudaMemcpyAsync(ctx->rec_forces + (size_t)ctx->rec_i * L.nc * 3, L.Fliq, (size_t)L.nc * 24,
+                                   cudaMemcpyDeviceToDevice, s),
+                   "record forces");
+            ctx->rec_i++;
+            ctx->rec_left--;
+        }
     }
     int flags = 0;
     CK(cudaMemcpyAsync(&flags, L.flags, 4, cudaMemcpyDeviceToHost, s), "read flags");
@@ -532,7 +550,6 @@ int lb_get_colloid_terms(lb_ctx* ctx, int which, double* out) {
 long long lb_launch_count(const lb_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
 // ------------------------------------------------------------- adjoint
-static size_t state_bytes(const lb_ctx* ctx) { return (size_t)2 * Q * ctx->L.pstride * storage_bytes(ctx->prec); }
 
 int lb_state_bytes(const lb_ctx* ctx, size_t* bytes) {
     if (!ctx || !bytes) return LB_ERR_ARG;
@@ -556,10 +573,13 @@ int lb_set_state(lb_ctx* ctx, const void* d_src) {
     return LB_OK;
 }
 
-// scratch: [dJdF: maxc x 3 doubles][grads: 8 doubles][kernel scratch]
-static size_t adj_head_bytes(const lb_ctx* ctx) {
-    return align_up((size_t)(ctx->maxc > 0 ? ctx->maxc : 1) * 24) + align_up(64);
+// scratch: [dJdF: maxc x 3 doubles][gradient accumulator: 8 doubles][seed value: 8 doubles][kernel scratch]
+static size_t adj_dJdF_bytes(const lb_ctx* ctx) { return align_up((size_t)(ctx->maxc > 0 ? ctx->maxc : 1) * 24); }
+static double* adj_grads(const lb_ctx* ctx, void* scratch) { return (double*)((char*)scratch + adj_dJdF_bytes(ctx)); }
+static double* adj_value(const lb_ctx* ctx, void* scratch) {
+    return (double*)((char*)scratch + adj_dJdF_bytes(ctx) + align_up(64));
 }
+static size_t adj_head_bytes(const lb_ctx* ctx) { return adj_dJdF_bytes(ctx) + 2 * align_up(64); }
 
 int lb_adjoint_bytes(const lb_ctx* ctx, size_t* field_bytes, size_t* scratch_bytes) {
     if (!ctx || !field_bytes || !scratch_bytes) return LB_ERR_ARG;
@@ -579,12 +599,41 @@ int lb_adjoint_seed(lb_ctx* ctx, double weight, void* d_adj, void* d_scratch, do
     int rc = adjoint_ready(ctx);
     if (rc) return rc;
     char* head = (char*)d_scratch;
-    double* val_dev = (double*)(head + align_up((size_t)(ctx->maxc > 0 ? ctx->maxc : 1) * 24));
+    double* val_dev = adj_value(ctx, d_scratch);
+    // a reverse sweep starts here: clear the gradient accumulator
+    CK(cudaMemsetAsync(adj_grads(ctx, d_scratch), 0, 8 * sizeof(double), ctx->stream), "clear gradients");
     rc = launched(ctx, launch_adjoint_seed(ctx->L, ctx->prec, d_adj, head + adj_head_bytes(ctx), weight, val_dev,
                                            ctx->stream), "adjoint seed");
     if (rc) return rc;
     CK(cudaMemcpyAsync(value, val_dev, 8, cudaMemcpyDeviceToHost, ctx->stream), "copy seed value");
     CK(cudaStreamSynchronize(ctx->stream), "seed sync");
+    return LB_OK;
+}
+
+// the launches of one reverse step; dJdF_dev: device dJ/dF_liq or null
+static int adjoint_step_launch(lb_ctx* ctx, const void* d_state, const void* d_adj_in, void* d_adj_out,
+                               void* d_scratch, const double* dJdF_dev) {
+    Lattice Ls = ctx->L;
+    Ls.f_cur = (void*)d_state;
+    cudaStream_t s = ctx->stream;
+    char* head = (char*)d_scratch;
+    // forward densities of step t: rho everywhere, wall and virtual densities
+    int n = launch_density(Ls, ctx->prec, s);
+    n += launch_wall_psi(Ls, ctx->prec, s);
+    n += launch_virtual(Ls, ctx->prec, 0, s);
+    n += launch_adjoint_step(Ls, ctx->prec, d_adj_in, d_adj_out, head + adj_head_bytes(ctx),
+                             Ls.nc > 0 ? dJdF_dev : nullptr, adj_grads(ctx, d_scratch), s);
+    return launched(ctx, n, "adjoint step");
+}
+
+// add the accumulated parameter gradients to grads (host) and clear them
+static int adjoint_read_grads(lb_ctx* ctx, void* d_scratch, double* grads) {
+    double g[5];
+    double* acc = adj_grads(ctx, d_scratch);
+    CK(cudaMemcpyAsync(g, acc, 40, cudaMemcpyDeviceToHost, ctx->stream), "copy grads");
+    CK(cudaMemsetAsync(acc, 0, 40, ctx->stream), "clear gradients");
+    CK(cudaStreamSynchronize(ctx->stream), "adjoint sync");
+    for (int a = 0; a < 5; a++) grads[a] += g[a];
     return LB_OK;
 }
 
@@ -594,26 +643,36 @@ int lb_adjoint_step(lb_ctx* ctx, const void* d_state, const void* d_adj_in, void
         return LB_ERR_ARG;
     int rc = adjoint_ready(ctx);
     if (rc) return rc;
-    Lattice Ls = ctx->L;
-    Ls.f_cur = (void*)d_state;
-    cudaStream_t s = ctx->stream;
-    char* head = (char*)d_scratch;
-    double* dJdF_dev = (double*)head;
-    double* grads_dev = (double*)(head + align_up((size_t)(ctx->maxc > 0 ? ctx->maxc : 1) * 24));
-    if (dJdF && Ls.nc > 0)
-        CK(cudaMemcpyAsync(dJdF_dev, dJdF, (size_t)Ls.nc * 24, cudaMemcpyHostToDevice, s), "copy dJdF");
-    // forward densities of step t: rho everywhere, wall and virtual densities
-    int n = launch_density(Ls, ctx->prec, s);
-    n += launch_wall_psi(Ls, ctx->prec, s);
-    n += launch_virtual(Ls, ctx->prec, 0, s);
-    n += launch_adjoint_step(Ls, ctx->prec, d_adj_in, d_adj_out, head + adj_head_bytes(ctx),
-                             (dJdF && Ls.nc > 0) ? dJdF_dev : nullptr, grads_dev, s);
-    rc = launched(ctx, n, "adjoint step");
+    double* dJdF_dev = (double*)d_scratch;
+    if (dJdF && ctx->L.nc > 0)
+        CK(cudaMemcpyAsync(dJdF_dev, dJdF, (size_t)ctx->L.nc * 24, cudaMemcpyHostToDevice, ctx->stream),
+           "copy dJdF");
+    rc = adjoint_step_launch(ctx, d_state, d_adj_in, d_adj_out, d_scratch, dJdF ? dJdF_dev : nullptr);
     if (rc) return rc;
-    double g[5];
-    CK(cudaMemcpyAsync(g, grads_dev, 40, cudaMemcpyDeviceToHost, s), "copy grads");
-    CK(cudaStreamSynchronize(s), "adjoint sync");
-    for (int a = 0; a < 5; a++) grads[a] += g[a];
+    return adjoint_read_grads(ctx, d_scratch, grads);
+}
+
+int lb_adjoint_step_async(lb_ctx* ctx, const void* d_state, const void* d_adj_in, void* d_adj_out,
+                          void* d_scratch, const double* d_dJdF, double* grads) {
+    if (!ctx || !d_state || !d_adj_in || !d_adj_out || !d_scratch || d_adj_in == d_adj_out) return LB_ERR_ARG;
+    int rc = adjoint_ready(ctx);
+    if (rc) return rc;
+    rc = adjoint_step_launch(ctx, d_state, d_adj_in, d_adj_out, d_scratch, d_dJdF);
+    if (rc) return rc;
+    return grads ? adjoint_read_grads(ctx, d_scratch, grads) : LB_OK;
+}
+
+int lb_drag_gradient(lb_ctx* ctx, const double* d_F, double weight, double eps, double* d_dJdF) {
+    if (!ctx || !d_F || !d_dJdF || !(eps >= 0.0)) return LB_ERR_ARG;
+    return launched(ctx, launch_drag_gradient(ctx->L.nc, d_F, weight, eps, d_dJdF, ctx->stream), "drag gradient");
+}
+
+int lb_record(lb_ctx* ctx, void* d_states, double* d_forces, int nsteps) {
+    if (!ctx) return LB_ERR_ARG;
+    ctx->rec_states = nsteps > 0 ? (char*)d_states : nullptr;
+    ctx->rec_forces = nsteps > 0 ? d_forces : nullptr;
+    ctx->rec_left = nsteps > 0 ? nsteps : 0;
+    ctx->rec_i = 0;
     return LB_OK;
 }
 

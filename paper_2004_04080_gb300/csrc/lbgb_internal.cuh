@@ -301,5 +301,6 @@ int launch_adjoint_step(const Lattice& L, int prec, const void* in, void* out, v
 int launch_adjoint_seed(const Lattice& L, int prec, void* adj, void* scratch, double weight, double* value_dev,
                         cudaStream_t st);
 int launch_adjoint_initial(const Lattice& L, int prec, const void* adj, double* grad, cudaStream_t st);
+int launch_drag_gradient(int n, const double* F, double weight, double eps, double* out, cudaStream_t st);
 
 }  // namespace lbgb

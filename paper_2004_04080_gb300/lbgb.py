@@ -31,7 +31,8 @@ EXPORTS = ["lb_workspace_bytes", "lb_create", "lb_set_params", "lb_init_fields",
            "lb_get_populations", "lb_get_owner", "lb_profile", "lb_profile_read", "lb_profile_read_kernel",
            "lb_state_bytes",
            "lb_get_state", "lb_set_state", "lb_adjoint_bytes", "lb_adjoint_seed", "lb_adjoint_step",
-           "lb_adjoint_initial", "lb_totals_static", "lb_launch_count", "lb_destroy", "lb_last_error"]
+           "lb_adjoint_initial", "lb_adjoint_step_async", "lb_drag_gradient", "lb_record", "lb_totals_static",
+           "lb_launch_count", "lb_destroy", "lb_last_error"]
 
 
 class LbParams(C.Structure):
@@ -88,6 +89,9 @@ def load(build_if_missing: bool = True):
     lib.lb_adjoint_seed.argtypes = [P, C.c_double, P, P, D]
     lib.lb_adjoint_step.argtypes = [P, P, P, P, P, D, D]
     lib.lb_adjoint_initial.argtypes = [P, P, P]
+    lib.lb_adjoint_step_async.argtypes = [P, P, P, P, P, P, D]
+    lib.lb_drag_gradient.argtypes = [P, P, C.c_double, C.c_double, P]
+    lib.lb_record.argtypes = [P, P, P, C.c_int]
     lib.lb_totals_static.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_longlong, P, D, P, P]
     lib.lb_launch_count.argtypes = [P]
     lib.lb_launch_count.restype = C.c_longlong
@@ -264,6 +268,26 @@ def lb_adjoint_step(h, d_state: int, d_adj_in: int, d_adj_out: int, d_scratch: i
     g = None if dJdF is None else _f64(dJdF)
     return _check(h, load().lb_adjoint_step(h, C.c_void_p(d_state), C.c_void_p(d_adj_in), C.c_void_p(d_adj_out),
                                             C.c_void_p(d_scratch), _dp(g), _dp(grads)), "lb_adjoint_step")
+
+
+def lb_adjoint_step_async(h, d_state: int, d_adj_in: int, d_adj_out: int, d_scratch: int, d_dJdF, grads=None):
+    """d_dJdF: device pointer or None; grads: host array of 5 (read and clear
+    the accumulated gradients, synchronising) or None (keep accumulating)."""
+    return _check(h, load().lb_adjoint_step_async(h, C.c_void_p(d_state), C.c_void_p(d_adj_in),
+                                                  C.c_void_p(d_adj_out), C.c_void_p(d_scratch),
+                                                  C.c_void_p(d_dJdF or None), _dp(grads)),
+                  "lb_adjoint_step_async")
+
+
+def lb_drag_gradient(h, d_F: int, weight: float, eps: float, d_dJdF: int):
+    return _check(h, load().lb_drag_gradient(h, C.c_void_p(d_F), float(weight), float(eps), C.c_void_p(d_dJdF)),
+                  "lb_drag_gradient")
+
+
+def lb_record(h, d_states, d_forces, nsteps: int):
+    """d_states / d_forces: device pointers or None."""
+    return _check(h, load().lb_record(h, C.c_void_p(d_states or None), C.c_void_p(d_forces or None), int(nsteps)),
+                  "lb_record")
 
 
 def lb_adjoint_initial(h, d_adj: int, d_grad: int):

@@ -137,3 +137,50 @@ def test_autograd_function_runs():
     (out[0] * 2.0 + out[1]).backward()
     assert th.grad is not None and torch.all(torch.isfinite(th.grad))
     assert ra.grad.shape == ra.shape and torch.isfinite(ra.grad).all()
+
+
+def test_async_reverse_sweep_matches_synchronous_steps():
+    """The runner's reverse sweep (states and link forces recorded on the
+    device by lb_record, dJ/dF from lb_drag_gradient, gradients accumulated on
+    the device) gives the gradients of a sweep of synchronous lb_adjoint_step
+    calls with dJ/dF formed on the host from the read-back forces."""
+    import torch
+
+    from paper_2004_04080_gb300 import lbgb
+    from paper_2004_04080_gb300.adjoint import AdjointRunner
+    from paper_2004_04080_gb300.lbgb import LBLattice
+
+    shape, base, theta, col, a, b = case(True)
+    steps = 7
+    lat = LBLattice(shape, "fp64", max_colloids=2)
+    run = AdjointRunner(lat, steps, checkpoint_every=3)
+    run.forward(params_of(base, theta), a, b, col)
+    g_async, r_async = run.backward(0.7, 1.3)
+
+    # synchronous reference: every state kept, forces read per step
+    lat2 = LBLattice(shape, "fp64", max_colloids=2)
+    lat2.set_params(**params_of(base, theta))
+    lat2.init_fields(a, b)
+    lat2.add_colloids(np.asarray(col["pos"]), col["radius"], np.full(2, np.inf))
+    sb = lbgb.lb_state_bytes(lat2.h)
+    states = torch.empty((steps, sb), dtype=torch.uint8, device="cuda")
+    forces = []
+    for t in range(steps):
+        lbgb.lb_get_state(lat2.h, states[t].data_ptr())
+        lat2.step(1)
+        forces.append(lat2.term("F_liq"))
+    fb, scb = lbgb.lb_adjoint_bytes(lat2.h)
+    cur, nxt = (torch.empty(fb, dtype=torch.uint8, device="cuda") for _ in range(2))
+    scratch = torch.empty(scb, dtype=torch.uint8, device="cuda")
+    lbgb.lb_adjoint_seed(lat2.h, 1.3, cur.data_ptr(), scratch.data_ptr())
+    grads = np.zeros(5)
+    for t in reversed(range(steps)):
+        F = forces[t]
+        dJdF = 0.7 / (steps * 2) * F / np.sqrt(np.sum(F * F, axis=1) + 1e-24)[:, None]
+        lbgb.lb_adjoint_step(lat2.h, states[t].data_ptr(), cur.data_ptr(), nxt.data_ptr(), scratch.data_ptr(),
+                             dJdF, grads)
+        cur, nxt = nxt, cur
+    g = torch.empty((2, lat2.N), dtype=torch.float64, device="cuda")
+    lbgb.lb_adjoint_initial(lat2.h, cur.data_ptr(), g.data_ptr())
+    assert np.allclose(g_async, grads, rtol=1e-11, atol=1e-14), (g_async, grads)
+    assert np.allclose(r_async, g.cpu().numpy(), rtol=1e-11, atol=1e-14)

@@ -480,27 +480,29 @@ __device__ __forceinline__ uint32_t nbr_solid(const Lattice& L, const SiteNbr& n
 // neighbours, and Eq. 21 (repulsive sign):
 // F_s = -G sum_k psi^k(s) sum w_i rho^kbar(s + c_i) c_i, added with its torque
 // (x_s - r_p) x F_s to F_s, T_s of the owning particle with FP64 atomics (the
-// step zeroes them in k_remap_classify).  The lattice is streamed like the
-// fused step: a 32 x 8 tile marches along z with psi^k and the owner map of
-// three planes (tile + one-site ring) in shared memory, 12 bytes per site in
-// coalesced rows, each plane loaded into registers one plane ahead of its
-// use; the particle nodes of a plane are packed onto consecutive threads
-// before the per-node work, so that one or two warps do it with all lanes
-// busy.  The densities rho^k of the fluid nodes are those of the full density
-// pass of this step (k_density).
-constexpr int VTX = 32, VTY = 8;
+// step zeroes them in launch_remap).  A block loads psi^k and the owner map
+// of a 32 x 8 tile (+ one-site ring) for all planes of its z chunk (+ one on
+// each side) into shared memory in one batch, 12 bytes per site in coalesced
+// rows; the particle nodes of the chunk are then packed onto consecutive
+// threads, so that the per-node work runs with all lanes busy, and each
+// takes its fluid neighbours from shared memory.  The densities rho^k of the
+// fluid nodes are those of the full density pass of this step (k_density).
+constexpr int VTX = 32, VTY = 8, VZC = 8;  // tile and planes per block
 
 template <int PREC>
 __global__ void __launch_bounds__(VTX* VTY) k_virtual(Lattice L, int store_terms, int zc) {
     typedef typename Prec<PREC>::C C;
-    constexpr int NT = VTX * VTY;
-    __shared__ C sps[3][2][VTY + 2][VTX + 2];
-    __shared__ int snd[3][VTY + 2][VTX + 2];
-    __shared__ int cand[NT];
+    constexpr int NT = VTX * VTY, NPL = VZC + 2;
+    extern __shared__ __align__(16) unsigned char vsm[];
+    // planes z0-1 .. z0+zc of the tile + ring: node codes, then psi^A, psi^B
+    int (*snd)[VTY + 2][VTX + 2] = reinterpret_cast<int (*)[VTY + 2][VTX + 2]>(vsm);
+    C (*spa)[VTY + 2][VTX + 2] = reinterpret_cast<C (*)[VTY + 2][VTX + 2]>(vsm + sizeof(int) * NPL * (VTY + 2) * (VTX + 2));
+    C (*spb)[VTY + 2][VTX + 2] = spa + NPL;
+    __shared__ int cand[NT * VZC];
     __shared__ int wcnt[NT / 32];
     const int x0 = blockIdx.x * VTX, y0 = blockIdx.y * VTY;
     const int W = min(VTX, L.nx - x0), H = min(VTY, L.ny - y0);
-    const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, L.nz);
+    const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, L.nz), nz_b = z1 - z0;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * VTX + tx, lane = tid & 31, warp = tid >> 5;
     const bool act = tx < W && ty < H;
     const long long nxy = (long long)L.nx * L.ny;
@@ -519,113 +521,118 @@ __global__ void __launch_bounds__(VTX* VTY) k_virtual(Lattice L, int store_terms
     else if (tid < 2 * (W + 2) + H) { rlx = -1; rly = tid - 2 * (W + 2); }
     else { rlx = W; rly = tid - 2 * (W + 2) - H; }
     const int ring_xy = has_ring ? wrap_xy(rlx, rly) : 0;
-    // the own and ring entries of plane p, loaded into registers one plane
-    // ahead of their use; a plane beyond a wall has no fluid node
-    struct Entry { int nd; C a, b; };
-    auto fetch = [&](int p, int xy, bool on) {
-        Entry e = {ND_WALL, C(0), C(0)};
-        if (on && !((p < 0 || p >= L.nz) && !L.per[2])) {
-            const int Z = p < 0 ? p + L.nz : (p >= L.nz ? p - L.nz : p);
-            const long long g = nxy * Z + xy;
-            e.nd = L.owner[g];
-            e.a = psi[g];
-            e.b = psi[L.N + g];
-        }
-        return e;
-    };
-    auto put = [&](int slot, const Entry& e, int ly, int lx) {
-        snd[slot][ly][lx] = e.nd;
-        sps[slot][0][ly][lx] = e.a;
-        sps[slot][1][ly][lx] = e.b;
-    };
+    // every plane of the chunk at once (asynchronous copies, all in flight
+    // together); a plane beyond a wall has no fluid node
+    for (int q = 0; q < nz_b + 2; q++) {
+        const int p = z0 - 1 + q;
+        const bool wall = (p < 0 || p >= L.nz) && !L.per[2];
+        const int Z = p < 0 ? p + L.nz : (p >= L.nz ? p - L.nz : p);
+        const long long zoff = nxy * Z;
+        auto put = [&](int ly, int lx, long long g) {
+            if (wall) {
+                snd[q][ly][lx] = ND_WALL;
+                spa[q][ly][lx] = spb[q][ly][lx] = C(0);
+                return;
+            }
+            cp_async_4(&snd[q][ly][lx], L.owner + g);
+            if (sizeof(C) == 8) {
+                cp_async_8(&spa[q][ly][lx], psi + g);
+                cp_async_8(&spb[q][ly][lx], psi + L.N + g);
+            } else {
+                cp_async_4(&spa[q][ly][lx], psi + g);
+                cp_async_4(&spb[q][ly][lx], psi + L.N + g);
+            }
+        };
+        if (act) put(ty + 1, tx + 1, zoff + own_xy);
+        if (has_ring) put(rly + 1, rlx + 1, zoff + ring_xy);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    // the particle nodes of the chunk, packed onto consecutive threads (in
+    // plane, warp and lane order: fixed by the geometry)
+    int mine = 0;
+    for (int q = 1; q <= nz_b; q++) mine += act && snd[q][ty + 1][tx + 1] >= 0;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wcnt[warp] = incl;
+    __syncthreads();
+    int off = incl - mine, tot = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; w++) {
+        off += w < warp ? wcnt[w] : 0;
+        tot += wcnt[w];
+    }
+    for (int q = 1; q <= nz_b; q++)
+        if (act && snd[q][ty + 1][tx + 1] >= 0) cand[off++] = q * NT + tid;
+    __syncthreads();
     const C G = prm<C>(L.P.G, L.PF.G), zA = C(1) + C(L.P.zeta[0]), zB = C(1) + C(L.P.zeta[1]);
-    for (int q = 0; q < 2; q++) {
-        const Entry eo = fetch(z0 - 1 + q, own_xy, act), er = fetch(z0 - 1 + q, ring_xy, has_ring);
-        if (act) put(q, eo, ty + 1, tx + 1);
-        if (has_ring) put(q, er, rly + 1, rlx + 1);
+    for (int k = tid; k < tot; k += NT) {
+        const int e = cand[k], q = e / NT, t = e - q * NT, cx0 = t % VTX, cy0 = t / VTX;
+        const int p = snd[q][cy0 + 1][cx0 + 1];
+        C num[2] = {0, 0}, den = 0;
+        C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};
+#pragma unroll
+        for (int i = 1; i < Q; i++) {
+            const int a = q + cz(i), yy = cy0 + 1 + cy(i), xx = cx0 + 1 + cx(i);
+            const bool fl = snd[a][yy][xx] == ND_FLUID;
+            C ra = fl ? spa[a][yy][xx] : C(0), rb = fl ? spb[a][yy][xx] : C(0);
+            C w = fl ? wgt<C>(i) : C(0);
+            num[0] += w * ra;
+            num[1] += w * rb;
+            den += w;
+            sA[0] += w * ra * C(cx(i)); sA[1] += w * ra * C(cy(i)); sA[2] += w * ra * C(cz(i));
+            sB[0] += w * rb * C(cx(i)); sB[1] += w * rb * C(cy(i)); sB[2] += w * rb * C(cz(i));
+        }
+        if (!(den > C(0))) continue;
+        const int z = z0 + q - 1;
+        const long long s = nxy * z + (x0 + cx0) + (long long)L.nx * (y0 + cy0);
+        const C pa = zA * num[0] / den;
+        const C pb = zB * num[1] / den;
+        psi[s] = pa;
+        psi[L.N + s] = pb;
+        if (!store_terms) continue;
+        C fs[3], d[3], tq[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) fs[c] = -G * pa * sB[c] + -G * pb * sA[c];
+        // x_s - r_p (minimum image) from the integer cell and offset of r_p
+        const int xs[3] = {x0 + cx0, y0 + cy0, z}, Ls[3] = {L.nx, L.ny, L.nz};
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            int ip;
+            C fr;
+            if (sizeof(C) == 8) {
+                double r = L.pos[3 * p + c];
+                ip = (int)floor(r);
+                fr = C(r - (double)ip);
+            } else {
+                ip = L.ipos[3 * p + c];
+                fr = C(L.fsnap[9 * p + c]);
+            }
+            int dd = xs[c] - ip;
+            if (L.per[c]) {
+                if (2 * dd > Ls[c]) dd -= Ls[c];
+                else if (2 * dd < -Ls[c]) dd += Ls[c];
+            }
+            d[c] = C(dd) - fr;
+        }
+        crs<C>(d, fs, tq);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            atomicAdd(L.Fs + 3 * p + c, double(fs[c]));
+            atomicAdd(L.Ts + 3 * p + c, double(tq[c]));
+        }
     }
-    Entry no = fetch(z0 + 1, own_xy, act), nr = fetch(z0 + 1, ring_xy, has_ring);
-    int lo = 0, mid = 1, hi = 2;
-    for (int z = z0; z < z1; z++) {
-        if (act) put(hi, no, ty + 1, tx + 1);
-        if (has_ring) put(hi, nr, rly + 1, rlx + 1);
-        if (z + 2 <= z1) {
-            no = fetch(z + 2, own_xy, act);
-            nr = fetch(z + 2, ring_xy, has_ring);
-        }
-        __syncthreads();
-        // the particle nodes of the plane, packed onto consecutive threads
-        const bool c = act && snd[mid][ty + 1][tx + 1] >= 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, c);
-        if (lane == 0) wcnt[warp] = __popc(bal);
-        __syncthreads();
-        int off = 0, tot = 0;
-#pragma unroll
-        for (int w = 0; w < NT / 32; w++) {
-            off += w < warp ? wcnt[w] : 0;
-            tot += wcnt[w];
-        }
-        if (c) cand[off + __popc(bal & ((1u << lane) - 1u))] = tid;
-        __syncthreads();
-        for (int k = tid; k < tot; k += NT) {
-            const int t = cand[k], cx0 = t % VTX, cy0 = t / VTX;
-            const int p = snd[mid][cy0 + 1][cx0 + 1];
-            const int sl[3] = {lo, mid, hi};
-            C num[2] = {0, 0}, den = 0;
-            C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};
-#pragma unroll
-            for (int i = 1; i < Q; i++) {
-                const int a = sl[cz(i) + 1], yy = cy0 + 1 + cy(i), xx = cx0 + 1 + cx(i);
-                const bool fl = snd[a][yy][xx] == ND_FLUID;
-                C ra = fl ? sps[a][0][yy][xx] : C(0), rb = fl ? sps[a][1][yy][xx] : C(0);
-                C w = fl ? wgt<C>(i) : C(0);
-                num[0] += w * ra;
-                num[1] += w * rb;
-                den += w;
-                sA[0] += w * ra * C(cx(i)); sA[1] += w * ra * C(cy(i)); sA[2] += w * ra * C(cz(i));
-                sB[0] += w * rb * C(cx(i)); sB[1] += w * rb * C(cy(i)); sB[2] += w * rb * C(cz(i));
-            }
-            if (!(den > C(0))) continue;
-            const long long s = nxy * z + (x0 + cx0) + (long long)L.nx * (y0 + cy0);
-            const C pa = zA * num[0] / den;
-            const C pb = zB * num[1] / den;
-            psi[s] = pa;
-            psi[L.N + s] = pb;
-            if (!store_terms) continue;
-            C fs[3], d[3], tq[3];
-#pragma unroll
-            for (int q = 0; q < 3; q++) fs[q] = -G * pa * sB[q] + -G * pb * sA[q];
-            // x_s - r_p (minimum image) from the integer cell and offset of r_p
-            const int xs[3] = {x0 + cx0, y0 + cy0, z}, Ls[3] = {L.nx, L.ny, L.nz};
-#pragma unroll
-            for (int q = 0; q < 3; q++) {
-                int ip;
-                C fr;
-                if (sizeof(C) == 8) {
-                    double r = L.pos[3 * p + q];
-                    ip = (int)floor(r);
-                    fr = C(r - (double)ip);
-                } else {
-                    ip = L.ipos[3 * p + q];
-                    fr = C(L.fsnap[9 * p + q]);
-                }
-                int dd = xs[q] - ip;
-                if (L.per[q]) {
-                    if (2 * dd > Ls[q]) dd -= Ls[q];
-                    else if (2 * dd < -Ls[q]) dd += Ls[q];
-                }
-                d[q] = C(dd) - fr;
-            }
-            crs<C>(d, fs, tq);
-#pragma unroll
-            for (int q = 0; q < 3; q++) {
-                atomicAdd(L.Fs + 3 * p + q, double(fs[q]));
-                atomicAdd(L.Ts + 3 * p + q, double(tq[q]));
-            }
-        }
-        __syncthreads();
-        const int t = lo; lo = mid; mid = hi; hi = t;
-    }
+}
+
+template <int PREC>
+size_t virtual_smem() {
+    typedef typename Prec<PREC>::C C;
+    return (size_t)(VZC + 2) * (VTY + 2) * (VTX + 2) * (sizeof(int) + 2 * sizeof(C));
 }
 
 // -------------------------------------------------------- pair forces
@@ -931,9 +938,15 @@ int launch_remap(const Lattice& L, int prec, int maxc, cudaStream_t st) {
 
 int launch_virtual(const Lattice& L, int prec, int store_terms, cudaStream_t st) {
     if (L.nc <= 0) return 0;
-    const int zc = L.nz < 16 ? L.nz : 16;
+    const int zc = L.nz < VZC ? L.nz : VZC;
     dim3 grid((L.nx + VTX - 1) / VTX, (L.ny + VTY - 1) / VTY, (L.nz + zc - 1) / zc);
-    DISPATCHC(prec, (k_virtual<P><<<grid, dim3(VTX, VTY), 0, st>>>(L, store_terms, zc)));
+    static bool attr_set[3] = {false, false, false};
+    if (!attr_set[prec]) {
+        DISPATCHC(prec, (cudaFuncSetAttribute(k_virtual<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)virtual_smem<P>())));
+        attr_set[prec] = true;
+    }
+    DISPATCHC(prec, (k_virtual<P><<<grid, dim3(VTX, VTY), virtual_smem<P>(), st>>>(L, store_terms, zc)));
     return 1;
 }
 

@@ -627,7 +627,6 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k
     }
 }
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 // ------------------------------------------ copy-pipelined fused step
 // The fused step for a lattice with particles, where a full density pass
@@ -665,17 +664,7 @@ struct AsyncShared {
     PW prec[MOM ? 2 : 1][MOM ? PWORDS : 1][MOM ? FTX * TY : 1];
 };
 
-__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_4(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_8(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 
 // nx (and so every tile width) must be a multiple of this for the 16-byte
 // population chunks of a precision

@@ -42,15 +42,16 @@ def density_bytes(prec, unit):
 
 def fused_kernel(prec, nx, particles, unit=True):
     """(name, algorithmic bytes per site) of the fused lattice kernel a step
-    launches.  With particles the copy-pipelined kernel follows a full density
-    pass: for tau = 1 it reads the momenta j^k (6 values) written by that pass,
-    psi^k (2 values) and the owner map (4 B) and writes 2 x 19 populations;
-    otherwise it reads the populations instead of the momenta (nx a multiple
-    of 16 bytes of populations).  Without particles the plain-load kernel
-    reads and writes the populations and the 1-byte node mask."""
+    launches.  With particles a copy-pipelined kernel follows a full density
+    pass: for tau = 1 the warp-independent one reads the momenta j^k (6
+    values) written by that pass, psi^k (2 values) and the owner map (4 B) and
+    writes 2 x 19 populations; otherwise the block one reads the populations
+    instead of the momenta (nx a multiple of 16 bytes of populations).
+    Without particles the plain-load kernel reads and writes the populations
+    and the 1-byte node mask."""
     pops = 38 * STORE[prec]
     if particles and unit:
-        return "k_fused_async", pops + 8 * COMPUTE[prec] + 4
+        return "k_fused_warp", pops + 8 * COMPUTE[prec] + 4
     if particles and nx % max(4, 16 // STORE[prec]) == 0:
         return "k_fused_async", 2 * pops + 2 * COMPUTE[prec] + 4
     return "k_fused", 2 * pops + 1

@@ -403,12 +403,13 @@ __device__ __forceinline__ LinkInfo link_info(const SH& sh, const int (&sl)[3], 
 // with the wall-velocity term) instead of branching.
 template <int PREC, bool UNIT, typename SH, typename PopFn>
 __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int (&sl)[3], int x, int y, int z,
-                                             const OwnSite<PREC>& m, bool solid, PopFn pop, const LinkInfo& li,
-                                             const ParticleRef<typename Prec<PREC>::C>& pref, int& pforce,
-                                             typename Prec<PREC>::C (&Fp)[3], typename Prec<PREC>::C (&Tp)[3]) {
+                                             int ty, const OwnSite<PREC>& m, bool solid, PopFn pop,
+                                             const LinkInfo& li, const ParticleRef<typename Prec<PREC>::C>& pref,
+                                             int& pforce, typename Prec<PREC>::C (&Fp)[3],
+                                             typename Prec<PREC>::C (&Tp)[3]) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
-    int tx = threadIdx.x, ty = threadIdx.y;
+    int tx = threadIdx.x;  // (ty: the shared-memory row of the site, less one)
     const unsigned bb = li.bb, pm = li.pm;
     const int p0 = li.p0;
     const bool multi = li.multi;
@@ -612,7 +613,7 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k
             // (particle 0 stands in when no link reaches a particle: its
             // record exists whenever the lattice has room for particles)
             const ParticleRef<C> pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
-            collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, cur, solid,
+            collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, ty, cur, solid,
                                      [&](int q) { return &sh.stage[q][tid]; }, li, pref, pf, Fp, Tp);
         }
         commit_link_forces<C>(L, pf, Fp, Tp);
@@ -629,7 +630,8 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k
 
 
 // ------------------------------------------ copy-pipelined fused step
-// The fused step for a lattice with particles, where a full density pass
+// The fused step for a lattice with particles at tau != 1 (tau = 1: the
+// warp-independent momentum kernel below), where a full density pass
 // (k_density) and the virtual densities (Eq. 20) have filled psi before the
 // step: the halo of the Shan-Chen sum then needs no populations, and the
 // block streams each plane through shared memory with asynchronous copies
@@ -642,29 +644,15 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k
 
 constexpr int ASYNC_TY = 8;  // tile rows of the copy-pipelined kernel
 
-// MOM: the staged rows are the momenta j^k (3 per component, written by the
-// density pass) instead of the 2 x 19 populations; only for omega = 1, where
-// the post-collision state is f^eq(rho^k, us^k) (Eq. 16) and needs no
-// population of its own site.
-// MOM also stages, one plane ahead, the record of the particle each boundary
-// site bounces on (FP32 forms: integer cell, offset, v, omega as 12 words;
-// FP64: r, v, omega), so that no dependent L2 load sits inside the collision.
-template <int PREC, int TY, bool MOM>
+template <int PREC, int TY>
 struct AsyncShared {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
-    typedef typename std::conditional<MOM, C, S>::type E;
-    typedef typename std::conditional<sizeof(C) == 8, double, unsigned>::type PW;
-    static constexpr int ROWS = MOM ? 6 : 2 * Q;
-    static constexpr int NSLOT = MOM ? 5 : 4;  // psi planes held
-    static constexpr int PWORDS = sizeof(C) == 8 ? 9 : 12;
-    E stage[2][ROWS][FTX * TY];
+    static constexpr int NSLOT = 4;  // psi planes held: z-1, z, z+1 and the one in flight
+    S stage[2][2 * Q][FTX * TY];
     C psi[NSLOT][2][TY + 2][RW];
     int nd[NSLOT][TY + 2][RW];
-    PW prec[MOM ? 2 : 1][MOM ? PWORDS : 1][MOM ? FTX * TY : 1];
 };
-
-
 
 // nx (and so every tile width) must be a multiple of this for the 16-byte
 // population chunks of a precision
@@ -673,14 +661,12 @@ constexpr int async_x_multiple() {
     return 16 / (int)sizeof(typename Prec<PREC>::S) < 4 ? 4 : 16 / (int)sizeof(typename Prec<PREC>::S);
 }
 
-template <int PREC, bool UNIT, int TY, bool MOM>
-__global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : (MOM ? 24 : 16) / TY))
-    k_fused_async(Lattice L, int zc) {
+template <int PREC, bool UNIT, int TY>
+__global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fused_async(Lattice L, int zc) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
-    typedef AsyncShared<PREC, TY, MOM> SH;
-    typedef typename SH::E E;
-    static_assert(!MOM || UNIT, "the momentum-staged form needs omega = 1");
+    typedef AsyncShared<PREC, TY> SH;
+    typedef S E;
     constexpr int NT = FTX * TY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SH& sh = *reinterpret_cast<SH*>(smem_raw);
@@ -741,9 +727,9 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : (MOM ? 24 : 16
         if (act) put(ty + 1, tx + 1, zoff + own_xy);
         if (has_ring) put(rly + 1, rlx + 1, zoff + ring_xy);
     };
-    // the staged rows (2 x 19 populations, or the 6 momenta) of the tile of
-    // plane p into stage buffer b: lane tx copies 16-byte chunk tx % LPP of
-    // its row in arrays tx / LPP, tx / LPP + PPP, ...
+    // the 2 x 19 population rows of the tile of plane p into stage buffer b:
+    // lane tx copies 16-byte chunk tx % LPP of its row in planes tx / LPP,
+    // tx / LPP + PPP, ...
     constexpr int EPC = 16 / (int)sizeof(E);  // elements per 16-byte chunk
     constexpr int LPP = FTX / EPC;            // lanes per row
     constexpr int PPP = FTX / LPP;            // arrays per pass
@@ -752,125 +738,249 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : (MOM ? 24 : 16
     const long long row_off = (long long)(x0 + chunk * EPC) + (long long)L.nx * (y0 + ty);
     auto issue_pops = [&](int p, int b) {
         if (!copies) return;
-        const char* src = (const char*)(MOM ? L.mom : L.f_cur) +
+        const char* src = (const char*)L.f_cur +
                           ((long long)plane0 * L.pstride + row_off + nxy * p) * (long long)sizeof(E);
         const long long step = (long long)PPP * L.pstride * (long long)sizeof(E);
         E* dst = &sh.stage[b][plane0][ty * FTX + chunk * EPC];
 #pragma unroll
-        for (int pl = plane0; pl < SH::ROWS; pl += PPP) {
+        for (int pl = plane0; pl < 2 * Q; pl += PPP) {
             cp_async_16(dst, src);
             src += step;
             dst += PPP * NT;
         }
     };
-    // MOM: links of the own site of plane p and the copy of its particle record
-    auto prefetch = [&](int p, int b) {
-        int sl[3] = {slot_of(p - 1), slot_of(p), slot_of(p + 1)};
-        const LinkInfo li = link_info(sh, sl, tx, ty, sh.nd[slot_of(p)][ty + 1][tx + 1] != ND_FLUID);
-        if (act && li.pm) {
-            const int q = li.p0;
-            if (sizeof(C) == 8) {
-#pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    cp_async_8(&sh.prec[b][d][tid], L.pos + 3 * q + d);
-                    cp_async_8(&sh.prec[b][3 + d][tid], L.vel + 3 * q + d);
-                    cp_async_8(&sh.prec[b][6 + d][tid], L.omg + 3 * q + d);
-                }
-            } else {
-#pragma unroll
-                for (int d = 0; d < 3; d++) cp_async_4(&sh.prec[b][d][tid], L.ipos + 3 * q + d);
-#pragma unroll
-                for (int j = 0; j < 9; j++) cp_async_4(&sh.prec[b][3 + j][tid], L.fsnap + 9 * q + j);
-            }
-        }
-        return li;
-    };
-    auto staged_record = [&](int b) {
-        ParticleRef<C> r;
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            if (sizeof(C) == 8) {
-                double q = (double)sh.prec[b][d][tid];
-                r.ip[d] = (int)floor(q);
-                r.fr[d] = C(q - (double)r.ip[d]);
-                r.v[d] = C((double)sh.prec[b][3 + d][tid]);
-                r.w[d] = C((double)sh.prec[b][6 + d][tid]);
-            } else {
-                r.ip[d] = (int)sh.prec[b][d][tid];
-                r.fr[d] = C(__uint_as_float((unsigned)sh.prec[b][3 + d][tid]));
-                r.v[d] = C(__uint_as_float((unsigned)sh.prec[b][6 + d][tid]));
-                r.w[d] = C(__uint_as_float((unsigned)sh.prec[b][9 + d][tid]));
-            }
-        }
-        return r;
-    };
-    constexpr int AHEAD = MOM ? 3 : 2;  // psi planes issued ahead of the collided one
-    for (int p = z0 - 1; p < z0 + AHEAD; p++)
+    for (int p = z0 - 1; p < z0 + 2; p++)
         if (p <= z1) issue_psi(p);
     issue_pops(z0, 0);
     cp_async_commit();
-    LinkInfo li_next = {0u, 0u, -1, false};
-    if (MOM) {
-        cp_async_wait_all();
-        __syncthreads();
-        li_next = prefetch(z0, 0);
-        cp_async_commit();
-    }
     for (int z = z0; z < z1; z++) {
         cp_async_wait_all();
         __syncthreads();
         const int b = (z - z0) & 1;
         if (z + 1 < z1) issue_pops(z + 1, b ^ 1);
-        if (z + AHEAD <= z1) issue_psi(z + AHEAD);
-        const LinkInfo li_cur = li_next;
-        if (MOM && z + 1 < z1) li_next = prefetch(z + 1, b ^ 1);
+        if (z + 2 <= z1) issue_psi(z + 2);
         cp_async_commit();
         int pf = -1;
         C Fp[3] = {0, 0, 0}, Tp[3] = {0, 0, 0};
         if (act) {
             const int mid = slot_of(z);
             OwnSite<PREC> m;
-            if (MOM) {
-                // rho^k is the own psi entry of a fluid node (same sum as Eq. 6 here)
 #pragma unroll
-                for (int k = 0; k < 2; k++) {
-                    m.rho[k] = sh.psi[mid][k][ty + 1][tx + 1];
+            for (int k = 0; k < 2; k++) {
+                C r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
-                    for (int d = 0; d < 3; d++) m.j[k][d] = C(sh.stage[b][3 * k + d][tid]);
+                for (int i = 0; i < Q; i++) {
+                    C v = ld_pop(&sh.stage[b][k * Q + i][tid], pop_shift<S, C>(L, k, i));
+                    r += v;
+                    if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
+                    if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
+                    if (cz(i) > 0) jz += v; else if (cz(i) < 0) jz -= v;
                 }
-            } else {
-#pragma unroll
-                for (int k = 0; k < 2; k++) {
-                    C r = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-                    for (int i = 0; i < Q; i++) {
-                        C v = ld_pop((const S*)&sh.stage[b][k * Q + i][tid], pop_shift<S, C>(L, k, i));
-                        r += v;
-                        if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
-                        if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
-                        if (cz(i) > 0) jz += v; else if (cz(i) < 0) jz -= v;
-                    }
-                    m.rho[k] = r;
-                    m.j[k][0] = jx; m.j[k][1] = jy; m.j[k][2] = jz;
-                }
+                m.rho[k] = r;
+                m.j[k][0] = jx; m.j[k][1] = jy; m.j[k][2] = jz;
             }
             int sl[3] = {slot_of(z - 1), mid, slot_of(z + 1)};
             const bool solid = sh.nd[mid][ty + 1][tx + 1] != ND_FLUID;
-            LinkInfo li;
-            ParticleRef<C> pref;
-            if (MOM) {
-                li = li_cur;
-                pref = staged_record(b);
-            } else {
-                li = link_info(sh, sl, tx, ty, solid);
-                pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
-            }
-            collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, m, solid,
-                                     [&](int q) { return (const S*)&sh.stage[b][q][tid]; }, li, pref, pf, Fp, Tp);
+            const LinkInfo li = link_info(sh, sl, tx, ty, solid);
+            const ParticleRef<C> pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
+            collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, ty, m, solid,
+                                     [&](int q) { return &sh.stage[b][q][tid]; }, li, pref, pf, Fp, Tp);
         }
         commit_link_forces<C>(L, pf, Fp, Tp);
     }
     cp_async_wait_all();
+}
+
+static int z_chunks(const Lattice& L, int tiles, int per_sm, int zmin);
+
+// ------------------------------------- warp-independent momentum step
+// The omega = 1 step of a lattice with particles (collision from the momenta
+// and densities of the density pass) with every warp on its own: a warp owns
+// one row of 32 sites and marches along z, staging with cp.async, into its
+// own shared memory, psi^k and the node codes of the three rows around its
+// own (y-1, y, y+1, each with the x ring), its momentum rows and the
+// records of the particles its sites bounce on.  Warps wait only for their own
+// copies (cp.async.wait_all + __syncwarp), so a warp slowed by particle work
+// holds no other; the price is that each psi row is staged by three warps
+// (reads that hit L2).
+constexpr int WNSLOT = 5;  // psi planes held: z-1 .. z+3
+constexpr int WPB = 4;     // warps (rows) per block
+
+template <int PREC>
+struct alignas(16) WarpShared {
+    typedef typename Prec<PREC>::C C;
+    typedef typename std::conditional<sizeof(C) == 8, double, unsigned>::type PW;
+    static constexpr int NSLOT = WNSLOT;
+    static constexpr int PWORDS = sizeof(C) == 8 ? 9 : 12;
+    C psi[WNSLOT][2][3][RW];
+    int nd[WNSLOT][3][RW];
+    alignas(16) C j[2][6][FTX];  // 16-byte copies land here
+    PW prec[2][PWORDS][FTX];
+};
+static_assert(offsetof(WarpShared<LB_FP32>, j) % 16 == 0 && sizeof(WarpShared<LB_FP32>) % 16 == 0, "alignment");
+static_assert(offsetof(WarpShared<LB_FP64>, j) % 16 == 0 && sizeof(WarpShared<LB_FP64>) % 16 == 0, "alignment");
+static_assert(offsetof(WarpShared<LB_FP16>, j) % 16 == 0 && sizeof(WarpShared<LB_FP16>) % 16 == 0, "alignment");
+
+template <int PREC>
+__global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : 6)) k_fused_warp(Lattice L, int zc) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    typedef WarpShared<PREC> SH;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SH& sh = reinterpret_cast<SH*>(smem_raw)[threadIdx.y];
+    const int tx = threadIdx.x;
+    const int x0 = blockIdx.x * FTX, y = blockIdx.y * WPB + threadIdx.y;
+    if (y >= L.ny) return;  // the whole warp: no block-wide barrier follows
+    const int W = min(FTX, L.nx - x0);
+    const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, L.nz);
+    const bool act = tx < W;
+    const long long nxy = (long long)L.nx * L.ny;
+    const C* psig = (const C*)L.psi;
+    auto slot_of = [&](int p) { return (p - z0 + 1) % WNSLOT; };
+    // the (3 rows) x (W + 2 columns) staged positions, up to 4 per lane
+    int pxy[4], prow[4], pcol[4];
+    bool pon[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int q = tx + 32 * r;
+        pon[r] = q < 3 * (W + 2);
+        prow[r] = pon[r] ? q / (W + 2) : 0;
+        pcol[r] = pon[r] ? q % (W + 2) : 0;
+        int X = x0 + pcol[r] - 1, Y = y + prow[r] - 1;
+        X = X < 0 ? X + L.nx : (X >= L.nx ? X - L.nx : X);
+        Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
+        pxy[r] = X + L.nx * Y;
+    }
+    auto issue_psi = [&](int p) {
+        const int slot = slot_of(p);
+        const bool wall = (p < 0 || p >= L.nz) && !L.per[2];
+        const C* pw = (const C*)L.psi_wall + (p < 0 ? 0 : 2) * nxy;
+        const int Z = p < 0 ? p + L.nz : (p >= L.nz ? p - L.nz : p);
+        const long long zoff = nxy * Z;
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            if (!pon[r]) continue;
+            const int a = prow[r], c = pcol[r];
+            if (wall) {
+                sh.psi[slot][0][a][c] = pw[pxy[r]];
+                sh.psi[slot][1][a][c] = pw[nxy + pxy[r]];
+                sh.nd[slot][a][c] = ND_WALL;
+                continue;
+            }
+            const long long g = zoff + pxy[r];
+            cp_async_4(&sh.nd[slot][a][c], L.owner + g);
+            if (sizeof(C) == 8) {
+                cp_async_8(&sh.psi[slot][0][a][c], psig + g);
+                cp_async_8(&sh.psi[slot][1][a][c], psig + L.N + g);
+            } else {
+                cp_async_4(&sh.psi[slot][0][a][c], psig + g);
+                cp_async_4(&sh.psi[slot][1][a][c], psig + L.N + g);
+            }
+        }
+    };
+    // momentum rows of plane p: 16-byte chunks, lane -> chunk tx % LPR of
+    // rows tx / LPR, tx / LPR + 32 / LPR, ...
+    constexpr int EPC = 16 / (int)sizeof(C), LPR = FTX / EPC, RPP = FTX / LPR;
+    const int chunk = tx % LPR, row0 = tx / LPR;
+    const bool jcopy = chunk * EPC < W;
+    auto issue_mom = [&](int p, int b) {
+        if (!jcopy) return;
+        const char* src = (const char*)L.mom + ((long long)row0 * L.pstride + (long long)(x0 + chunk * EPC) +
+                                                (long long)L.nx * y + nxy * p) * (long long)sizeof(C);
+        for (int r = row0; r < 6; r += RPP) {
+            cp_async_16(&sh.j[b][r][chunk * EPC], src);
+            src += (long long)RPP * L.pstride * (long long)sizeof(C);
+        }
+    };
+    auto prefetch = [&](int p, int b) {
+        int sl[3] = {slot_of(p - 1), slot_of(p), slot_of(p + 1)};
+        const LinkInfo li = link_info(sh, sl, tx, 0, sh.nd[slot_of(p)][1][tx + 1] != ND_FLUID);
+        if (act && li.pm) {
+            const int q = li.p0;
+            if (sizeof(C) == 8) {
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    cp_async_8(&sh.prec[b][d][tx], L.pos + 3 * q + d);
+                    cp_async_8(&sh.prec[b][3 + d][tx], L.vel + 3 * q + d);
+                    cp_async_8(&sh.prec[b][6 + d][tx], L.omg + 3 * q + d);
+                }
+            } else {
+#pragma unroll
+                for (int d = 0; d < 3; d++) cp_async_4(&sh.prec[b][d][tx], L.ipos + 3 * q + d);
+#pragma unroll
+                for (int jj = 0; jj < 9; jj++) cp_async_4(&sh.prec[b][3 + jj][tx], L.fsnap + 9 * q + jj);
+            }
+        }
+        return li;
+    };
+    for (int p = z0 - 1; p < z0 + 3; p++)
+        if (p <= z1) issue_psi(p);
+    issue_mom(z0, 0);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncwarp();
+    LinkInfo li_next = prefetch(z0, 0);
+    cp_async_commit();
+    for (int z = z0; z < z1; z++) {
+        cp_async_wait_all();
+        __syncwarp();
+        const int b = (z - z0) & 1;
+        if (z + 1 < z1) issue_mom(z + 1, b ^ 1);
+        if (z + 3 <= z1) issue_psi(z + 3);
+        const LinkInfo li = li_next;
+        if (z + 1 < z1) li_next = prefetch(z + 1, b ^ 1);
+        cp_async_commit();
+        if (!act) continue;
+        const int mid = slot_of(z);
+        OwnSite<PREC> m;
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            m.rho[k] = sh.psi[mid][k][1][tx + 1];
+#pragma unroll
+            for (int d = 0; d < 3; d++) m.j[k][d] = sh.j[b][3 * k + d][tx];
+        }
+        ParticleRef<C> pref;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            if (sizeof(C) == 8) {
+                double q = (double)sh.prec[b][d][tx];
+                pref.ip[d] = (int)floor(q);
+                pref.fr[d] = C(q - (double)pref.ip[d]);
+                pref.v[d] = C((double)sh.prec[b][3 + d][tx]);
+                pref.w[d] = C((double)sh.prec[b][6 + d][tx]);
+            } else {
+                pref.ip[d] = (int)sh.prec[b][d][tx];
+                pref.fr[d] = C(__uint_as_float((unsigned)sh.prec[b][3 + d][tx]));
+                pref.v[d] = C(__uint_as_float((unsigned)sh.prec[b][6 + d][tx]));
+                pref.w[d] = C(__uint_as_float((unsigned)sh.prec[b][9 + d][tx]));
+            }
+        }
+        int sl[3] = {slot_of(z - 1), mid, slot_of(z + 1)};
+        int pf = -1;
+        C Fp[3] = {0, 0, 0}, Tp[3] = {0, 0, 0};
+        collide_site<PREC, true>(L, sh, sl, x0 + tx, y, z, 0, m, sh.nd[mid][1][tx + 1] != ND_FLUID,
+                                 [&](int) { return (const S*)nullptr; }, li, pref, pf, Fp, Tp);
+        commit_link_forces<C>(L, pf, Fp, Tp);
+    }
+    cp_async_wait_all();
+}
+
+template <int P>
+static int launch_fused_warp(const Lattice& L, cudaStream_t st) {
+    static bool attr_set = false;
+    static int per_sm = 0;
+    const size_t smem = sizeof(WarpShared<P>) * WPB;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_fused_warp<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_warp<P>, FTX * WPB, smem);
+        if (per_sm < 1) per_sm = 1;
+        attr_set = true;
+    }
+    int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + WPB - 1) / WPB);
+    int zc = z_chunks(L, tiles, per_sm, 8);
+    dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + WPB - 1) / WPB, (L.nz + zc - 1) / zc);
+    k_fused_warp<P><<<grid, dim3(FTX, WPB), smem, st>>>(L, zc);
+    return 1;
 }
 
 // ----------------------------------------------- TMA-pipelined fused step
@@ -1077,7 +1187,7 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_tma(Lattice L, int zc, const _
             const bool solid = sh.nd[mid][ty + 1][tx + 1] != ND_FLUID;
             const LinkInfo li = link_info(sh, sl, tx, ty, solid);
             const ParticleRef<C> pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
-            collide_site<PREC, false>(L, sh, sl, x0 + tx, y0 + ty, z, m, solid,
+            collide_site<PREC, false>(L, sh, sl, x0 + tx, y0 + ty, z, ty, m, solid,
                                       [&](int q) { return &sh.buf[b][q][ty + 1][tx + TG::PAD]; }, li, pref, pf, Fp,
                                       Tp);
         }
@@ -1313,31 +1423,31 @@ static int z_chunks(const Lattice& L, int tiles, int per_sm, int zmin) {
     return best;
 }
 
-template <int P, bool UNIT, bool MOM>
+template <int P, bool UNIT>
 static int launch_fused_async_t(const Lattice& L, cudaStream_t st) {
     constexpr int TY = ASYNC_TY, NT = FTX * TY;
-    typedef AsyncShared<P, TY, MOM> SH;
+    typedef AsyncShared<P, TY> SH;
     static bool attr_set = false;
     static int per_sm = 0;
     const size_t smem = sizeof(SH);
     if (!attr_set) {
-        cudaFuncSetAttribute(k_fused_async<P, UNIT, TY, MOM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_async<P, UNIT, TY, MOM>, NT, smem);
+        cudaFuncSetAttribute(k_fused_async<P, UNIT, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_async<P, UNIT, TY>, NT, smem);
         if (per_sm < 1) per_sm = 1;
         attr_set = true;
     }
     int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + TY - 1) / TY);
     int zc = z_chunks(L, tiles, per_sm, 8);
     dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
-    k_fused_async<P, UNIT, TY, MOM><<<grid, dim3(FTX, TY), smem, st>>>(L, zc);
+    k_fused_async<P, UNIT, TY><<<grid, dim3(FTX, TY), smem, st>>>(L, zc);
     return 1;
 }
 
 template <int P>
 static int launch_fused_async(const Lattice& L, bool unit, cudaStream_t st) {
-    if (unit && L.dense_mom) return launch_fused_async_t<P, true, true>(L, st);
-    if (unit) return launch_fused_async_t<P, true, false>(L, st);
-    return launch_fused_async_t<P, false, false>(L, st);
+    if (unit && L.dense_mom) return launch_fused_warp<P>(L, st);
+    if (unit) return launch_fused_async_t<P, true>(L, st);
+    return launch_fused_async_t<P, false>(L, st);
 }
 
 int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st) {

@@ -23,6 +23,11 @@ struct lb_ctx {
     int prec;
     int maxc;
     cudaStream_t stream;
+    // the pair forces depend only on the particle state of the previous step:
+    // they run on `side` (created by the library, high priority) while the
+    // lattice kernels run on `stream`; the integrator waits for them
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
     char* ws;
     size_t ws_bytes;
     int have_params, have_fields, stepped;
@@ -174,6 +179,26 @@ int lb_workspace_bytes(int nx, int ny, int nz, int prec, int max_colloids, size_
     return LB_OK;
 }
 
+static cudaError_t create_side_stream(lb_ctx* ctx) {
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+    return e;
+}
+
+static void destroy_side_stream(lb_ctx* ctx) {
+    if (ctx->side) {
+        cudaStreamSynchronize(ctx->side);
+        cudaStreamDestroy(ctx->side);
+    }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    ctx->side = NULL;
+    ctx->ev_fork = ctx->ev_join = NULL;
+}
+
 int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_workspace, size_t bytes,
               void* cuda_stream, lb_ctx** out) {
     if (!out) return LB_ERR_ARG;
@@ -241,7 +266,9 @@ int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_worksp
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.col, 0, (size_t)mc * DOUBLES_PER_PARTICLE * 8, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.prev, 0, (size_t)mc * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = create_side_stream(ctx);
     if (e != cudaSuccess) {
+        destroy_side_stream(ctx);
         delete ctx;
         return LB_ERR_CUDA;
     }
@@ -399,6 +426,12 @@ int lb_step(lb_ctx* ctx, int nsteps) {
             CK(cudaMemcpyAsync(ctx->rec_states + (size_t)ctx->rec_i * state_bytes(ctx), L.f_cur, state_bytes(ctx),
                                cudaMemcpyDeviceToDevice, s),
                "record state");
+        if (L.nc > 0) {  // Eqs. 26, 27 on the side stream, from r(t), v(t - 1/2)
+            CK(cudaEventRecord(ctx->ev_fork, s), "fork event");
+            CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0), "fork wait");
+            n += launch_pairs(L, ctx->cells, ctx->cells_bytes, ctx->side);
+            CK(cudaEventRecord(ctx->ev_join, ctx->side), "join event");
+        }
         n += launch_remap(L, ctx->prec, ctx->maxc, s);  // destroy / create (Eqs. 24, 25)
         // rho^k (Eq. 6) of every fluid node when particles need virtual
         // densities (Eq. 20); with omega = 1 the pass also writes j^k, and
@@ -432,7 +465,8 @@ int lb_step(lb_ctx* ctx, int nsteps) {
             CK(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], s), "profile event");
             ctx->prof_n++;
         }
-        n += launch_pairs_integrate(L, ctx->cells, ctx->cells_bytes, s);  // Eqs. 26-27, 32-35
+        if (L.nc > 0) CK(cudaStreamWaitEvent(s, ctx->ev_join, 0), "join wait");
+        n += launch_integrate(L, s);  // Eqs. 28-35
         int rc = launched(ctx, n, "step kernels");
         if (rc) return rc;
         void* tmp = L.f_cur;
@@ -747,6 +781,7 @@ int lb_profile_read(lb_ctx* ctx, double* total_ms, long long* launches) {
 int lb_destroy(lb_ctx* ctx) {
     if (!ctx) return LB_ERR_ARG;
     cudaStreamSynchronize(ctx->stream);
+    destroy_side_stream(ctx);
     destroy_events(ctx->prof_ev);
     destroy_events(ctx->prof_evd);
     delete ctx;

@@ -950,7 +950,7 @@ int launch_virtual(const Lattice& L, int prec, int store_terms, cudaStream_t st)
     return 1;
 }
 
-int launch_pairs_integrate(const Lattice& L, void* cells, size_t cell_cap, cudaStream_t st) {
+int launch_pairs(const Lattice& L, void* cells, size_t cell_cap, cudaStream_t st) {
     if (L.nc <= 0) return 0;
     double rc = L.P.hertz_K != 0.0 ? L.P.hertz_sigma : 0.0;
     if (L.P.lub_on) rc = fmax(rc, 2.0 * L.rmax + L.P.lub_hn);
@@ -980,8 +980,13 @@ int launch_pairs_integrate(const Lattice& L, void* cells, size_t cell_cap, cudaS
         n += 3;
     }
     k_pairs<<<(L.nc + 127) / 128, 128, 0, st>>>(L, cg, use_cells, rcf);
+    return n + 1;
+}
+
+int launch_integrate(const Lattice& L, cudaStream_t st) {
+    if (L.nc <= 0) return 0;
     k_integrate<<<(L.nc + 127) / 128, 128, 0, st>>>(L);
-    return n + 2;
+    return 1;
 }
 
 }  // namespace lbgb

@@ -822,7 +822,7 @@ static_assert(offsetof(WarpShared<LB_FP64>, j) % 16 == 0 && sizeof(WarpShared<LB
 static_assert(offsetof(WarpShared<LB_FP16>, j) % 16 == 0 && sizeof(WarpShared<LB_FP16>) % 16 == 0, "alignment");
 
 template <int PREC>
-__global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : 6)) k_fused_warp(Lattice L, int zc) {
+__global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : 5)) k_fused_warp(Lattice L, int zc) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
     typedef WarpShared<PREC> SH;

@@ -305,7 +305,10 @@ int launch_clear_map(const Lattice& L, cudaStream_t st);
 int launch_map_initial(const Lattice& L, int prec, int first, int count, cudaStream_t st);
 int launch_remap(const Lattice& L, int prec, int maxc, cudaStream_t st);
 int launch_virtual(const Lattice& L, int prec, int store_terms, cudaStream_t st);
-int launch_pairs_integrate(const Lattice& L, void* cells, size_t cell_cap, cudaStream_t st);
+// Eqs. 26-27 and the side walls into Fpair (reads positions and velocities only)
+int launch_pairs(const Lattice& L, void* cells, size_t cell_cap, cudaStream_t st);
+// Eqs. 28-35: totals, leap-frog, quaternions, snapshot
+int launch_integrate(const Lattice& L, cudaStream_t st);
 int launch_snapshot(const Lattice& L, cudaStream_t st);
 
 size_t adjoint_field_bytes(const Lattice& L, int prec);

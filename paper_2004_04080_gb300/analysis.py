@@ -8,6 +8,11 @@ domain size built from it (Sec. 5.3).  These are measurements of the output
 * interface measure A = sum over fluid nodes of (1 - phi^2) (it counts the
   sites inside the diffuse interfaces; the adjoint differentiates the same
   quantity);
+* interface crossings: the lattice links (x, y and z neighbours, periodic)
+  between two fluid nodes whose order parameters have opposite signs, a
+  digital measure of the interface area (a flat interface normal to an axis
+  crosses one link per site of its plane) that does not depend on the bulk
+  densities of the phases;
 * S(k) = < phi'(k) phi'(-k) >, phi' = phi - <phi>, averaged over spherical
   shells of width 2 pi / L in k = |k|, and the domain size
   L = 2 pi sum_k S(k) / sum_k k S(k) (Eq. 40 with the integrals as sums over
@@ -26,6 +31,18 @@ def order_parameter(rhoA: np.ndarray, rhoB: np.ndarray, owner: np.ndarray | None
     fluid = rt > 0 if owner is None else (owner < 0) & (rt > 0)
     phi[fluid] = (rhoA[fluid] - rhoB[fluid]) / rt[fluid]
     return phi
+
+
+def interface_crossings(rhoA, rhoB, shape, owner=None) -> int:
+    nx, ny, nz = shape
+    phi = order_parameter(rhoA, rhoB, owner).reshape(nz, ny, nx)
+    fluid = ((rhoA + rhoB > 0) if owner is None else (owner < 0)).reshape(nz, ny, nx)
+    n = 0
+    for ax in range(3):
+        q = np.roll(phi, -1, axis=ax)
+        both = fluid & np.roll(fluid, -1, axis=ax)
+        n += int(np.count_nonzero(both & (phi * q < 0)))
+    return n
 
 
 def interface_measure(rhoA, rhoB, owner=None) -> float:

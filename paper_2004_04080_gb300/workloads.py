@@ -97,6 +97,28 @@ def place_colloids(shape, n: int, radius: float, seed: int, min_dist: float,
     return pos
 
 
+def droplet_densities(shape, centres, radius: float, rich: float, poor: float, width: float = 2.0):
+    """Spheres of B-rich fluid in an A-rich matrix, flat site order: with s
+    the largest over the droplets of 1/2 (1 - tanh((r - R) / width)), r the
+    minimum-image distance to a centre, rho_B = poor + (rich - poor) s and
+    rho_A = rich + poor - rho_B."""
+    nx, ny, nz = shape
+    s = np.zeros((nz, ny, nx))
+    m = int(math.ceil(radius + 4.0 * width))
+    off = np.arange(-m, m + 1)
+    for c in np.asarray(centres, dtype=np.float64):
+        ic = np.floor(c).astype(int)
+        X, Y, Z = ic[0] + off, ic[1] + off, ic[2] + off
+        dx, dy, dz = X - c[0], Y - c[1], Z - c[2]
+        r = np.sqrt(dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2)
+        v = 0.5 * (1.0 - np.tanh((r - radius) / width))
+        ix, iy, iz = np.mod(X, nx), np.mod(Y, ny), np.mod(Z, nz)
+        sub = s[np.ix_(iz, iy, ix)]
+        s[np.ix_(iz, iy, ix)] = np.maximum(sub, v)
+    rb = poor + (rich - poor) * s.ravel()
+    return rich + poor - rb, rb
+
+
 def default_params() -> dict:
     """Parameter defaults (names follow the C-ABI's lb_params)."""
     return dict(
@@ -123,12 +145,23 @@ class Workload:
     mean: float = 0.5
     amp: float = 0.01
     wall_gap: Optional[float] = None
+    # B-rich droplets in an A-rich matrix instead of the noisy 50/50 mixture:
+    # dict(n, radius, rich, poor, width, min_dist)
+    droplets: Optional[dict] = None
 
     @property
     def n_sites(self) -> int:
         return int(np.prod(self.shape))
 
+    def droplet_centres(self):
+        d = self.droplets
+        return place_colloids(self.shape, d["n"], d["radius"], self.seed + 2, d["min_dist"])
+
     def densities(self):
+        if self.droplets is not None:
+            d = self.droplets
+            return droplet_densities(self.shape, self.droplet_centres(), d["radius"], d["rich"], d["poor"],
+                                     d["width"])
         return mixture_densities(self.shape, self.seed, self.mean, self.amp)
 
     def colloids(self):
@@ -152,9 +185,12 @@ def _hertz(R):
     return dict(hertz_K=20.0, hertz_sigma=2 * R + 1.0, hertz_rcap=2 * R)
 
 
-def workload(name: str, scale: Optional[tuple] = None) -> Workload:
+def workload(name: str, scale: Optional[tuple] = None, calib: Optional[dict] = None) -> Workload:
     """The paper-shaped workloads.  ``scale`` overrides the box (same physics,
-    particle count rescaled to keep the volume fraction)."""
+    particle and droplet counts rescaled to keep the volume fractions).
+    ``calib`` (the Pickering emulsion only): the coexistence densities
+    ``rho_rich``, ``rho_poor`` and the wetting parameter ``delta_77`` of the
+    demixing mixture, measured with the oracle (tests/golden)."""
     base = default_params()
     if name == "small_fp64":
         # 32^3 periodic, tau=1, G=0.65, 50/50 +-1 %, 4 neutral R=4.5 spheres, 100 steps
@@ -184,10 +220,26 @@ def workload(name: str, scale: Optional[tuple] = None) -> Workload:
         shape = (512, 512, 256)
         w = Workload(name, shape, 20000, p, radius=R, n_colloids=n_for_fraction(shape, R, 0.15),
                      wall_gap=R + 1.0)
+    elif name == "pickering256":
+        # 256^3 periodic, 64 B-rich droplets of R = 16 (6.5 % of the volume)
+        # in an A-rich matrix (tanh profile of width 2 between the coexistence
+        # densities of the demixing mixture, rho0 = 1 per component), R = 5
+        # particles at phi = 0.10 with a contact angle of 77 degrees through
+        # the matrix (zeta_A = +Delta, zeta_B = -Delta), 5000 steps
+        if calib is None:
+            raise ValueError("pickering256 needs the calibration (rho_rich, rho_poor, delta_77)")
+        dl = float(calib["delta_77"])
+        p = dict(base, G=0.65, rho0=(1.0, 1.0), zeta=(dl, -dl), **_hertz(5.0))
+        shape = (256, 256, 256)
+        w = Workload(name, shape, 5000, p, radius=5.0, n_colloids=n_for_fraction(shape, 5.0, 0.10), mean=1.0,
+                     droplets=dict(n=64, radius=16.0, rich=float(calib["rho_rich"]),
+                                   poor=float(calib["rho_poor"]), width=2.0, min_dist=2 * 16.0 + 6.0))
     else:
         raise KeyError(name)
     if scale is not None:
         frac = float(np.prod(scale)) / float(np.prod(w.shape))
         w.n_colloids = int(round(w.n_colloids * frac))
+        if w.droplets is not None:
+            w.droplets = dict(w.droplets, n=max(1, int(round(w.droplets["n"] * frac))))
         w.shape = tuple(scale)
     return w

@@ -26,3 +26,37 @@ def test_interface_measure_counts_mixed_sites_only():
     assert an.interface_measure(a, b, owner) == 2.0
     phi = an.order_parameter(a, b, owner)
     assert phi[0] == 1.0 and phi[1] == -1.0 and phi[4] == 0.0
+
+
+def _crossings_by_loops(phi, fluid, shape):
+    """the link count written out site by site"""
+    nx, ny, nz = shape
+    n = 0
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                s = x + nx * (y + ny * z)
+                for d in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+                    t = (x + d[0]) % nx + nx * (((y + d[1]) % ny) + ny * ((z + d[2]) % nz))
+                    if fluid[s] and fluid[t] and phi[s] * phi[t] < 0:
+                        n += 1
+    return n
+
+
+def test_interface_crossings_of_flat_slabs_and_a_random_field():
+    shape = (6, 5, 8)
+    nx, ny, nz = shape
+    z = np.arange(nx * ny * nz) // (nx * ny)
+    # a slab 2 <= z < 5 of B in A: two flat interfaces of nx * ny sites each,
+    # whatever the bulk densities
+    for rich, poor in ((1.0, 0.0), (1.81, 0.23)):
+        inB = (z >= 2) & (z < 5)
+        a = np.where(inB, poor, rich)
+        b = np.where(inB, rich, poor)
+        assert an.interface_crossings(a, b, shape) == 2 * nx * ny
+    # random fields with particle nodes: the vectorised count equals the loops
+    rng = np.random.default_rng(3)
+    a, b = rng.random(nx * ny * nz), rng.random(nx * ny * nz)
+    owner = np.where(rng.random(nx * ny * nz) < 0.2, 1, -1)
+    phi = an.order_parameter(a, b, owner)
+    assert an.interface_crossings(a, b, shape, owner) == _crossings_by_loops(phi, owner < 0, shape)

@@ -9,7 +9,8 @@ Measured on a GB300 (seed 1): FP32 stays within 3e-4 of FP64 in A and 6e-4
 in L up to 5000 steps.  FP16 deviation storage (shift w_i rho0) is within
 1e-3 on the fields at 100 steps, within 0.3 % in A and 0.05 % in L at 2000
 steps, and at 5000 steps keeps L within 0.7 % and the same peak, while A
-drifts to 1.8 %: A is dominated by the bulk phases (1 - phi^2 = 0.4 per site
+drifts to 1.8 % (the count of interface link crossings to 1.4 %, FP32 0.2 %):
+A is dominated by the bulk phases (1 - phi^2 = 0.4 per site
 at the coexistence densities 1.81 / 0.23), and round-to-nearest storage
 rounds the minor-phase populations (about 0.8 w_i below the shift) the same
 way every step, a bias of about 0.3 % per population."""
@@ -40,6 +41,7 @@ def observables(prec, w, a, b, c):
         phi = an.order_parameter(ra, rb, own)
         k, S = an.structure_factor(phi, w.shape)
         out[s] = dict(A=an.interface_measure(ra, rb, own), L=an.domain_size(k, S),
+                      X=an.interface_crossings(ra, rb, w.shape, own),
                       kp=an.peak_wavenumber(k, S), rho=(ra, rb))
     return out
 
@@ -79,5 +81,14 @@ def test_fp16_fields_then_morphology(runs):
     for s in CHECKS:
         assert r16[s]["kp"] == r64[s]["kp"], s
     assert rel(r16[5000]["L"], r64[5000]["L"]) < 1e-2
+    # the interface itself (its link crossings, insensitive to the bulk
+    # values): within 1 % up to 2000 steps; at 5000 steps, after the domains
+    # have coarsened sevenfold along chaotic paths, FP16 is 1.4 % off
+    # (FP32: 0.2 %), beyond the 1 % target
+    print("interface crossings", {p: {s: runs[p][s]["X"] for s in CHECKS} for p in runs})
+    for s in CHECKS[:2]:
+        assert rel(r16[s]["X"], r64[s]["X"]) < 1e-2, s
+    assert rel(r16[5000]["X"], r64[5000]["X"]) < 2e-2
+    assert rel(runs["fp32"][5000]["X"], r64[5000]["X"]) < 5e-3
     # the bulk minor-phase bias of round-to-nearest storage (module docstring)
     assert rel(r16[5000]["A"], r64[5000]["A"]) < 3e-2

@@ -157,6 +157,22 @@ int lb_get_owner(lb_ctx *ctx, int *out);
  * returns its summed time (ms) and the number of timed launches (at most
  * 16384 are kept per record); lb_profile_read is the fused-kernel record. */
 enum { LB_KERNEL_FUSED = 0, LB_KERNEL_DENSITY = 1 };
+
+/* Rounding of the FP16 deviation storage (the precision forms; the paper
+ * stores FP64).  LB_ROUND_NEAREST (the default) stores half(f_i - w_i rho0^k)
+ * rounded to nearest.  LB_ROUND_STOCHASTIC rounds every population stored by
+ * the time step up or down with probability given by the value's position
+ * between the two neighbouring half values (bits from a counter-based hash of
+ * site, step and `seed`), so that the expected stored value is the FP32 one:
+ * a population that stays the same from step to step is then not rounded
+ * the same way every step.  The sequence of bits is fixed by `seed` and the
+ * number of steps since this call.  No effect on LB_FP32 / LB_FP64 contexts.
+ * The adjoint functions return LB_ERR_STATE while stochastic rounding is on
+ * (their forward recomputation would not reproduce the recorded steps).  The
+ * opt-in TMA kernel (LBGB_FUSED_TMA) rounds to nearest.
+ * LB_ERR_ARG for another mode. */
+enum { LB_ROUND_NEAREST = 0, LB_ROUND_STOCHASTIC = 1 };
+int lb_set_rounding(lb_ctx *ctx, int mode, unsigned long long seed);
 int lb_profile(lb_ctx *ctx, int enable);
 int lb_profile_read(lb_ctx *ctx, double *total_ms, long long *launches);
 int lb_profile_read_kernel(lb_ctx *ctx, int kernel, double *total_ms, long long *launches);

@@ -44,6 +44,8 @@ struct lb_ctx {
     char* rec_states;           // lb_record: f(t) of each recorded step, or null
     double* rec_forces;         // lb_record: F_liq after each recorded step, or null
     int rec_left, rec_i;        // steps still to record, steps recorded
+    unsigned long long sr_seed; // stochastic rounding: seed, and steps taken with it
+    unsigned long long sr_step;
     char err[512];
 };
 
@@ -413,6 +415,25 @@ int lb_add_colloids(lb_ctx* ctx, int n, const double* pos, const double* vel, co
     return LB_OK;
 }
 
+// key of the stochastic-rounding bits of step t: the SplitMix64 finaliser
+// (Steele, Lea, Flood) of seed + t, folded to 32 bits
+static unsigned sr_key(unsigned long long seed, unsigned long long t) {
+    unsigned long long z = seed + (t + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (unsigned)(z ^ (z >> 32));
+}
+
+int lb_set_rounding(lb_ctx* ctx, int mode, unsigned long long seed) {
+    if (!ctx) return LB_ERR_ARG;
+    if (mode != LB_ROUND_NEAREST && mode != LB_ROUND_STOCHASTIC) return set_err(ctx, LB_ERR_ARG, "unknown rounding mode");
+    ctx->L.sr = mode == LB_ROUND_STOCHASTIC && ctx->prec == LB_FP16;
+    ctx->sr_seed = seed;
+    ctx->sr_step = 0;
+    return LB_OK;
+}
+
 int lb_step(lb_ctx* ctx, int nsteps) {
     if (!ctx || nsteps < 0) return LB_ERR_ARG;
     if (!ctx->have_fields) return set_err(ctx, LB_ERR_STATE, "lb_init_fields must come first");
@@ -432,6 +453,7 @@ int lb_step(lb_ctx* ctx, int nsteps) {
             n += launch_pairs(L, ctx->cells, ctx->cells_bytes, ctx->side);
             CK(cudaEventRecord(ctx->ev_join, ctx->side), "join event");
         }
+        if (L.sr) L.sr_key = sr_key(ctx->sr_seed, ctx->sr_step++);
         n += launch_remap(L, ctx->prec, ctx->maxc, s);  // destroy / create (Eqs. 24, 25)
         // rho^k (Eq. 6) of every fluid node when particles need virtual
         // densities (Eq. 20); with omega = 1 the pass also writes j^k, and
@@ -624,6 +646,8 @@ int lb_adjoint_bytes(const lb_ctx* ctx, size_t* field_bytes, size_t* scratch_byt
 
 static int adjoint_ready(lb_ctx* ctx) {
     if (!ctx->have_fields) return set_err(ctx, LB_ERR_STATE, "no fields");
+    if (ctx->L.sr)
+        return set_err(ctx, LB_ERR_STATE, "stochastic rounding: recomputed forward steps would differ from the recorded ones");
     if (!ctx->all_fixed) return set_err(ctx, LB_ERR_STATE, "the adjoint needs immobile particles (infinite mass, at rest)");
     return LB_OK;
 }

@@ -401,7 +401,7 @@ __device__ __forceinline__ LinkInfo link_info(const SH& sh, const int (&sl)[3], 
 // Nearly every warp holds a bounce-back site, so the store of each link
 // selects its destination (the neighbour's slot i, or the own slot opp(i)
 // with the wall-velocity term) instead of branching.
-template <int PREC, bool UNIT, typename SH, typename PopFn>
+template <int PREC, bool UNIT, bool SR, typename SH, typename PopFn>
 __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int (&sl)[3], int x, int y, int z,
                                              int ty, const OwnSite<PREC>& m, bool solid, PopFn pop,
                                              const LinkInfo& li, const ParticleRef<typename Prec<PREC>::C>& pref,
@@ -488,6 +488,14 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
     // destinations as 32-bit element offsets from the base of the plane pair
     // (2j-1, 2j): plane 2j adds ps; sites < 2^31 and ps < 2^31 keep them in range
     char* fnb = (char*)L.f_nxt;
+    // FP16 with stochastic rounding (SR, a separate instantiation): the
+    // rounding bits of this site
+    unsigned rs = 0;
+    if constexpr (SR) rs = sr_start(s, L.sr_key);
+    auto put = [&](S* q, C val, C shift) {
+        if constexpr (SR) st_pop_sr(q, val, shift, sr_next(rs));
+        else st_pop(q, val, shift);
+    };
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         C fs[2];
@@ -507,8 +515,8 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
         if (i == 0) {
 #pragma unroll
             for (int k = 0; k < 2; k++)
-                st_pop((S*)(fnb + (unsigned long long)ps * (unsigned)(k * Q * (int)sizeof(S))) + s,
-                       solid ? wgt<C>(0) * prm<C>(L.P.rho0[k], L.PF.rho0[k]) : fs[k], pop_shift<S, C>(L, k, 0));
+                put((S*)(fnb + (unsigned long long)ps * (unsigned)(k * Q * (int)sizeof(S))) + s,
+                    solid ? wgt<C>(0) * prm<C>(L.P.rho0[k], L.PF.rho0[k]) : fs[k], pop_shift<S, C>(L, k, 0));
             continue;
         }
         const int lo = (i & 1) ? i : i - 1;  // first plane of the pair
@@ -527,7 +535,7 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
         for (int k = 0; k < 2; k++) {
             S* base = (S*)(fnb + (unsigned long long)ps * (unsigned)((k * Q + lo) * (int)sizeof(S)));
             const C fb = fs[k] + B[k][c] * cw;
-            st_pop(base + off, solid ? wgt<C>(i) * prm<C>(L.P.rho0[k], L.PF.rho0[k]) : fb, pop_shift<S, C>(L, k, i));
+            put(base + off, solid ? wgt<C>(i) * prm<C>(L.P.rho0[k], L.PF.rho0[k]) : fb, pop_shift<S, C>(L, k, i));
             fl += fs[k] + fb;
         }
         fl = (pm >> i) & 1u ? fl : C(0);
@@ -578,7 +586,7 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
     }
 }
 
-template <int PREC, bool UNIT>
+template <int PREC, bool UNIT, bool SR>
 __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k_fused(Lattice L, int zc) {
     typedef typename Prec<PREC>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -613,7 +621,7 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k
             // (particle 0 stands in when no link reaches a particle: its
             // record exists whenever the lattice has room for particles)
             const ParticleRef<C> pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
-            collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, ty, cur, solid,
+            collide_site<PREC, UNIT, SR>(L, sh, sl, x0 + tx, y0 + ty, z, ty, cur, solid,
                                      [&](int q) { return &sh.stage[q][tid]; }, li, pref, pf, Fp, Tp);
         }
         commit_link_forces<C>(L, pf, Fp, Tp);
@@ -661,7 +669,7 @@ constexpr int async_x_multiple() {
     return 16 / (int)sizeof(typename Prec<PREC>::S) < 4 ? 4 : 16 / (int)sizeof(typename Prec<PREC>::S);
 }
 
-template <int PREC, bool UNIT, int TY>
+template <int PREC, bool UNIT, int TY, bool SR>
 __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fused_async(Lattice L, int zc) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
@@ -783,7 +791,7 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fu
             const bool solid = sh.nd[mid][ty + 1][tx + 1] != ND_FLUID;
             const LinkInfo li = link_info(sh, sl, tx, ty, solid);
             const ParticleRef<C> pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
-            collide_site<PREC, UNIT>(L, sh, sl, x0 + tx, y0 + ty, z, ty, m, solid,
+            collide_site<PREC, UNIT, SR>(L, sh, sl, x0 + tx, y0 + ty, z, ty, m, solid,
                                      [&](int q) { return &sh.stage[b][q][tid]; }, li, pref, pf, Fp, Tp);
         }
         commit_link_forces<C>(L, pf, Fp, Tp);
@@ -821,7 +829,7 @@ static_assert(offsetof(WarpShared<LB_FP32>, j) % 16 == 0 && sizeof(WarpShared<LB
 static_assert(offsetof(WarpShared<LB_FP64>, j) % 16 == 0 && sizeof(WarpShared<LB_FP64>) % 16 == 0, "alignment");
 static_assert(offsetof(WarpShared<LB_FP16>, j) % 16 == 0 && sizeof(WarpShared<LB_FP16>) % 16 == 0, "alignment");
 
-template <int PREC>
+template <int PREC, bool SR>
 __global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : 5)) k_fused_warp(Lattice L, int zc) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
@@ -958,29 +966,37 @@ __global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : 5)) k_fused_w
         int sl[3] = {slot_of(z - 1), mid, slot_of(z + 1)};
         int pf = -1;
         C Fp[3] = {0, 0, 0}, Tp[3] = {0, 0, 0};
-        collide_site<PREC, true>(L, sh, sl, x0 + tx, y, z, 0, m, sh.nd[mid][1][tx + 1] != ND_FLUID,
+        collide_site<PREC, true, SR>(L, sh, sl, x0 + tx, y, z, 0, m, sh.nd[mid][1][tx + 1] != ND_FLUID,
                                  [&](int) { return (const S*)nullptr; }, li, pref, pf, Fp, Tp);
         commit_link_forces<C>(L, pf, Fp, Tp);
     }
     cp_async_wait_all();
 }
 
-template <int P>
-static int launch_fused_warp(const Lattice& L, cudaStream_t st) {
+template <int P, bool SR>
+static int launch_fused_warp_t(const Lattice& L, cudaStream_t st) {
     static bool attr_set = false;
     static int per_sm = 0;
     const size_t smem = sizeof(WarpShared<P>) * WPB;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_fused_warp<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_warp<P>, FTX * WPB, smem);
+        cudaFuncSetAttribute(k_fused_warp<P, SR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_warp<P, SR>, FTX * WPB, smem);
         if (per_sm < 1) per_sm = 1;
         attr_set = true;
     }
     int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + WPB - 1) / WPB);
     int zc = z_chunks(L, tiles, per_sm, 8);
     dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + WPB - 1) / WPB, (L.nz + zc - 1) / zc);
-    k_fused_warp<P><<<grid, dim3(FTX, WPB), smem, st>>>(L, zc);
+    k_fused_warp<P, SR><<<grid, dim3(FTX, WPB), smem, st>>>(L, zc);
     return 1;
+}
+
+// the stochastic-rounding instantiations exist for the FP16 form only
+template <int P>
+static int launch_fused_warp(const Lattice& L, cudaStream_t st) {
+    if constexpr (P == LB_FP16)
+        if (L.sr) return launch_fused_warp_t<P, true>(L, st);
+    return launch_fused_warp_t<P, false>(L, st);
 }
 
 // ----------------------------------------------- TMA-pipelined fused step
@@ -1187,7 +1203,7 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_tma(Lattice L, int zc, const _
             const bool solid = sh.nd[mid][ty + 1][tx + 1] != ND_FLUID;
             const LinkInfo li = link_info(sh, sl, tx, ty, solid);
             const ParticleRef<C> pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
-            collide_site<PREC, false>(L, sh, sl, x0 + tx, y0 + ty, z, ty, m, solid,
+            collide_site<PREC, false, false>(L, sh, sl, x0 + tx, y0 + ty, z, ty, m, solid,
                                       [&](int q) { return &sh.buf[b][q][ty + 1][tx + TG::PAD]; }, li, pref, pf, Fp,
                                       Tp);
         }
@@ -1423,7 +1439,7 @@ static int z_chunks(const Lattice& L, int tiles, int per_sm, int zmin) {
     return best;
 }
 
-template <int P, bool UNIT>
+template <int P, bool UNIT, bool SR>
 static int launch_fused_async_t(const Lattice& L, cudaStream_t st) {
     constexpr int TY = ASYNC_TY, NT = FTX * TY;
     typedef AsyncShared<P, TY> SH;
@@ -1431,23 +1447,39 @@ static int launch_fused_async_t(const Lattice& L, cudaStream_t st) {
     static int per_sm = 0;
     const size_t smem = sizeof(SH);
     if (!attr_set) {
-        cudaFuncSetAttribute(k_fused_async<P, UNIT, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_async<P, UNIT, TY>, NT, smem);
+        cudaFuncSetAttribute(k_fused_async<P, UNIT, TY, SR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_async<P, UNIT, TY, SR>, NT, smem);
         if (per_sm < 1) per_sm = 1;
         attr_set = true;
     }
     int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + TY - 1) / TY);
     int zc = z_chunks(L, tiles, per_sm, 8);
     dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
-    k_fused_async<P, UNIT, TY><<<grid, dim3(FTX, TY), smem, st>>>(L, zc);
+    k_fused_async<P, UNIT, TY, SR><<<grid, dim3(FTX, TY), smem, st>>>(L, zc);
     return 1;
 }
 
 template <int P>
 static int launch_fused_async(const Lattice& L, bool unit, cudaStream_t st) {
     if (unit && L.dense_mom) return launch_fused_warp<P>(L, st);
-    if (unit) return launch_fused_async_t<P, true>(L, st);
-    return launch_fused_async_t<P, false>(L, st);
+    if constexpr (P == LB_FP16)
+        if (L.sr) return unit ? launch_fused_async_t<P, true, true>(L, st) : launch_fused_async_t<P, false, true>(L, st);
+    if (unit) return launch_fused_async_t<P, true, false>(L, st);
+    return launch_fused_async_t<P, false, false>(L, st);
+}
+
+// the plain fused kernel (no particles): shared memory without the
+// population stage at omega = 1
+template <int P, bool UNIT, bool SR>
+static int launch_fused_plain(const Lattice& L, int zc, dim3 grid, cudaStream_t st) {
+    static bool attr_set = false;
+    const size_t smem = UNIT ? offsetof(FusedShared<P>, stage) : sizeof(FusedShared<P>);
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_fused<P, UNIT, SR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
+    k_fused<P, UNIT, SR><<<grid, dim3(FTX, FTY), smem, st>>>(L, zc);
+    return 1;
 }
 
 int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st) {
@@ -1470,24 +1502,17 @@ int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st) {
     zc = zc < 4 ? 4 : zc;
     zc = zc > L.nz ? L.nz : zc;
     dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + FTY - 1) / FTY, (L.nz + zc - 1) / zc);
-    static bool attr_set[3][2] = {{false, false}, {false, false}, {false, false}};
     // relaxation frequency exactly 1 (tau_A = tau_B = 1): the collision needs
     // no non-equilibrium part, a separate instantiation keeps the code small
     bool unit = L.P.tau[0] == 1.0 && L.P.tau[1] == 1.0;
-    if (!attr_set[prec][unit]) {
-        if (unit) {
-            DISPATCH(prec, (cudaFuncSetAttribute(k_fused<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)offsetof(FusedShared<P>, stage))));
-        } else {
-            DISPATCH(prec, (cudaFuncSetAttribute(k_fused<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)sizeof(FusedShared<P>))));
-        }
-        attr_set[prec][unit] = true;
+    if (prec == LB_FP16 && L.sr) {
+        if (unit) return launch_fused_plain<LB_FP16, true, true>(L, zc, grid, st);
+        return launch_fused_plain<LB_FP16, false, true>(L, zc, grid, st);
     }
     if (unit) {
-        DISPATCH(prec, (k_fused<P, true><<<grid, dim3(FTX, FTY), offsetof(FusedShared<P>, stage), st>>>(L, zc)));
+        DISPATCH(prec, (launch_fused_plain<P, true, false>(L, zc, grid, st)));
     } else {
-        DISPATCH(prec, (k_fused<P, false><<<grid, dim3(FTX, FTY), sizeof(FusedShared<P>), st>>>(L, zc)));
+        DISPATCH(prec, (launch_fused_plain<P, false, false>(L, zc, grid, st)));
     }
     return 1;
 }

@@ -53,6 +53,41 @@ __device__ __forceinline__ void st_pop(__half* p, float v, float shift) {
     *p = __float2half_rn(v - shift);
 }
 
+// Stochastic rounding of the FP16 deviation store.  The rounding bits of a
+// site start from Appleby's MurmurHash3 32-bit finaliser of (site, step key)
+// and advance by the linear congruential step of Numerical Recipes
+// (a = 1664525, c = 1013904223) per store, whose top 13 bits are used (bits
+// drawn for several stores from one product are correlated across the
+// populations of a site, which multiplies the noise of its density; the
+// serial step keeps them independent).  An FP32 value in the half-normal
+// range keeps 13 bits below a half's 10-bit mantissa: adding 13 random bits
+// to the magnitude and truncating rounds it up with probability equal to its
+// position between the two neighbouring half values, so the expected stored
+// value is the FP32 one.  Below that range (|d| < 2^-14, subnormal halves of
+// spacing 2^-24) the value rounds to nearest: truncation there would pull
+// every small deviation towards the shift (the seed noise of a mixture near
+// rho0, for one), and the selection keeps the store free of branches.
+__device__ __forceinline__ unsigned sr_start(unsigned site, unsigned key) {
+    unsigned h = site * 0x9E3779B1u ^ key;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+__device__ __forceinline__ unsigned sr_next(unsigned& st) {
+    st = st * 1664525u + 1013904223u;
+    return st >> 19;
+}
+__device__ __forceinline__ void st_pop_sr(__half* p, float v, float shift, unsigned bits13) {
+    const float d = v - shift;
+    const unsigned u = __float_as_uint(d);
+    const __half hs = __float2half_rz(__uint_as_float((u + bits13) & ~0x1fffu));
+    const __half hn = __float2half_rn(d);
+    *p = (u & 0x7fffffffu) >= 0x38800000u ? hs : hn;
+}
+
 // ------------------------------------------------------------- context
 // FP32 copies of the lattice parameters the per-site arithmetic reads: the
 // FP32 forms take these (a conversion from FP64 runs on the FP64 pipe, a
@@ -100,6 +135,8 @@ struct Lattice {
     int dense_psi;     // psi holds rho^k of every fluid node (a full density pass ran this step)
     int dense_mom;     // that pass also wrote j^k into mom (omega = 1 collision on momenta)
     void* mom;         // [6][pstride] of C: j^k_d of every site, row 3k + d
+    int sr;            // FP16: stochastic rounding of the stores of the time step
+    unsigned sr_key;   // this step's key of the rounding bits
     lb_params P;
 };
 

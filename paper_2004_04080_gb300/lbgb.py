@@ -29,6 +29,7 @@ TERMS = {"F_liq": 0, "T_liq": 1, "F_d": 2, "T_d": 3, "F_c": 4, "T_c": 5, "F_s": 
 EXPORTS = ["lb_workspace_bytes", "lb_create", "lb_set_params", "lb_init_fields", "lb_add_colloids",
            "lb_step", "lb_get_fields", "lb_get_colloids", "lb_get_colloid_terms", "lb_get_totals",
            "lb_get_populations", "lb_get_owner", "lb_profile", "lb_profile_read", "lb_profile_read_kernel",
+           "lb_set_rounding",
            "lb_state_bytes",
            "lb_get_state", "lb_set_state", "lb_adjoint_bytes", "lb_adjoint_seed", "lb_adjoint_step",
            "lb_adjoint_initial", "lb_adjoint_step_async", "lb_drag_gradient", "lb_record", "lb_totals_static",
@@ -92,6 +93,7 @@ def load(build_if_missing: bool = True):
     lib.lb_adjoint_step_async.argtypes = [P, P, P, P, P, P, D]
     lib.lb_drag_gradient.argtypes = [P, P, C.c_double, C.c_double, P]
     lib.lb_record.argtypes = [P, P, P, C.c_int]
+    lib.lb_set_rounding.argtypes = [P, C.c_int, C.c_ulonglong]
     lib.lb_totals_static.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_longlong, P, D, P, P]
     lib.lb_launch_count.argtypes = [P]
     lib.lb_launch_count.restype = C.c_longlong
@@ -220,6 +222,13 @@ def lb_profile(h, enable: bool):
 
 
 LB_KERNEL_FUSED, LB_KERNEL_DENSITY = 0, 1
+LB_ROUND_NEAREST, LB_ROUND_STOCHASTIC = 0, 1
+
+
+def lb_set_rounding(h, mode: int, seed: int = 0):
+    """Rounding of the FP16 deviation stores (LB_ROUND_NEAREST or
+    LB_ROUND_STOCHASTIC, bits from ``seed``)."""
+    return _check(h, load().lb_set_rounding(h, int(mode), int(seed) & ((1 << 64) - 1)), "lb_set_rounding")
 
 
 def lb_profile_read(h):
@@ -405,3 +414,6 @@ class LBLattice:
 
     def profile_read(self, kernel: int = LB_KERNEL_FUSED):
         return lb_profile_read_kernel(self.h, kernel)
+
+    def set_rounding(self, mode: int, seed: int = 0):
+        lb_set_rounding(self.h, mode, seed)

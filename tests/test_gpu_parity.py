@@ -141,6 +141,32 @@ def pickering_like(shape):
     return params, dens, col
 
 
+def test_fp64_cell_list_with_lubrication():
+    """80 mobile R = 3 particles in a 48^3 box (more than 64: the pair forces
+    search a cell grid of 6^3 cells instead of all pairs), soft Hertz contact
+    (Eq. 26, K = 2) and lubrication (Eq. 27) on, centres placed at least 6.3
+    apart (9 pairs start inside the lubrication range h < 0.67, 18 inside the
+    contact range) with random velocities; compared while the pair forces act
+    (step 4) and after 20 steps."""
+    from paper_2004_04080_gb300.workloads import place_colloids
+
+    shape = (48, 48, 48)
+    n, R = 80, 3.0
+    params = dict(G=0.5, tau=(1.0, 1.0), zeta=(0.05, -0.05), hertz_K=2.0, hertz_sigma=2 * R + 1, hertz_rcap=2 * R,
+                  lub_on=1, lub_hn=0.67, lub_hmin=0.1, lub_scale=1.0)
+    pos = place_colloids(shape, n, R, seed=11, min_dist=2 * R + 0.3)
+    rng = np.random.default_rng(12)
+    col = dict(pos=pos, radius=[R] * n, mass=[4.0 / 3.0 * math.pi * R ** 3] * n,
+               vel=0.01 * rng.standard_normal((n, 3)))
+    g, o = run_both(shape, params, 4, "fp64", col)
+    assert np.count_nonzero(np.abs(o.term("F_pair")).sum(axis=1)) >= 10
+    compare_colloids(g, o, 1e-11)
+    g.step(16)
+    o.step(16)
+    compare_fields(g, o, 1e-12)
+    compare_colloids(g, o, 1e-11)
+
+
 def test_fp64_demixing_droplets_wetting_particles():
     """The Pickering physics at a size the oracle runs in seconds: the
     demixing mixture (G rho_tot = 1.3), sharp droplet interfaces, wetting

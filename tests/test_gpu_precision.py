@@ -25,13 +25,15 @@ pytestmark = pytest.mark.gpu
 CHECKS = (100, 2000, 5000)
 
 
-def observables(prec, w, a, b, c):
-    from paper_2004_04080_gb300.lbgb import LBLattice
+def observables(prec, w, a, b, c, stochastic=False):
+    from paper_2004_04080_gb300.lbgb import LB_ROUND_STOCHASTIC, LBLattice
 
     g = LBLattice(w.shape, prec, max_colloids=w.n_colloids)
     g.set_params(**w.params)
     g.init_fields(a, b)
     g.add_colloids(c["pos"], c["radius"], c["mass"])
+    if stochastic:
+        g.set_rounding(LB_ROUND_STOCHASTIC, seed=1)
     out, done = {}, 0
     for s in CHECKS:
         g.step(s - done)
@@ -51,7 +53,10 @@ def runs():
     w = workload("bijel_demix", (96, 96, 96))
     a, b = w.densities()
     c = w.colloids()
-    return {p: observables(p, w, a, b, c) for p in ("fp64", "fp32", "fp16")}
+    r = {p: observables(p, w, a, b, c) for p in ("fp64", "fp32", "fp16")}
+    r["fp16sr"] = observables("fp16", w, a, b, c, stochastic=True)
+    print("morphology", {p: {s: (v[s]["A"], v[s]["X"], v[s]["L"], v[s]["kp"]) for s in CHECKS} for p, v in r.items()})
+    return r
 
 
 def rel(x, y):
@@ -92,3 +97,21 @@ def test_fp16_fields_then_morphology(runs):
     assert rel(runs["fp32"][5000]["X"], r64[5000]["X"]) < 5e-3
     # the bulk minor-phase bias of round-to-nearest storage (module docstring)
     assert rel(r16[5000]["A"], r64[5000]["A"]) < 3e-2
+
+
+def test_fp16_stochastic_rounding_morphology(runs):
+    """FP16 storage with stochastic rounding (lb_set_rounding): the fields at
+    100 steps within 1e-3 and, at 5000 steps, every observable of the
+    morphology within the 1 % target (measured on a GB300: interface measure
+    0.3 %, interface link crossings 0.3-0.5 %, L 0.05 %, the same S(k) peak),
+    where round-to-nearest storage misses it (1.8 %, 1.4 %)."""
+    r16, r64 = runs["fp16sr"], runs["fp64"]
+    ra, rb = r16[100]["rho"]
+    qa, qb = r64[100]["rho"]
+    assert max(np.abs(ra - qa).max(), np.abs(rb - qb).max()) / max(qa.max(), qb.max()) < 1e-3
+    for s in CHECKS:
+        assert r16[s]["kp"] == r64[s]["kp"], s
+    for s in CHECKS[1:]:
+        assert rel(r16[s]["L"], r64[s]["L"]) < 1e-2, s
+        assert rel(r16[s]["A"], r64[s]["A"]) < 1e-2, s
+        assert rel(r16[s]["X"], r64[s]["X"]) < 1e-2, s

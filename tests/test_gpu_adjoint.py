@@ -183,4 +183,8 @@ def test_async_reverse_sweep_matches_synchronous_steps():
     g = torch.empty((2, lat2.N), dtype=torch.float64, device="cuda")
     lbgb.lb_adjoint_initial(lat2.h, cur.data_ptr(), g.data_ptr())
     assert np.allclose(g_async, grads, rtol=1e-11, atol=1e-14), (g_async, grads)
-    assert np.allclose(r_async, g.cpu().numpy(), rtol=1e-11, atol=1e-14)
+    # the two forward runs sum the link forces (Eq. 22) with FP64 atomics in
+    # a different order, so dJ/dF differs in the last bits: the gradient
+    # field is compared on its own scale (run to run: 1.5e-14 of 0.086)
+    gg = g.cpu().numpy()
+    assert np.allclose(r_async, gg, rtol=1e-11, atol=1e-11 * np.abs(gg).max())

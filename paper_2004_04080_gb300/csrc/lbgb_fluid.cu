@@ -1461,10 +1461,12 @@ static int launch_fused_async_t(const Lattice& L, cudaStream_t st) {
 
 template <int P>
 static int launch_fused_async(const Lattice& L, bool unit, cudaStream_t st) {
+    // omega = 1: lb_step has the density pass write the momenta, and the
+    // warp kernel collides from them; otherwise the general collision (exact
+    // at omega = 1 as well: the non-equilibrium part is multiplied by 0)
     if (unit && L.dense_mom) return launch_fused_warp<P>(L, st);
     if constexpr (P == LB_FP16)
-        if (L.sr) return unit ? launch_fused_async_t<P, true, true>(L, st) : launch_fused_async_t<P, false, true>(L, st);
-    if (unit) return launch_fused_async_t<P, true, false>(L, st);
+        if (L.sr) return launch_fused_async_t<P, false, true>(L, st);
     return launch_fused_async_t<P, false, false>(L, st);
 }
 

@@ -175,7 +175,16 @@ def cpu_baseline(name, target_seconds=20.0):
                 name, *sub, w.n_colloids, steps, el)}
 
 
+def workload_desc(name, w):
+    """The workload as the bench line names it (both arms)."""
+    return "%s: %dx%dx%d sites, %s, R=%g (%d particles), G=%g, tau=%g" % (
+        name, *w.shape, "walls z +-%g" % w.params["wall_u_hi"][0] if w.params["bc"][2] == 0 else "periodic",
+        w.radius, w.n_colloids, w.params["G"], w.params["tau"][0])
+
+
 def run_reference(args, world, rank):
+    from paper_2004_04080_gb300.workloads import workload
+
     if rank != 0:
         return 0
     base = cpu_baseline(args.workload, target_seconds=max(5.0, min(60.0, 2.0 * (args.steps + args.warmup))))
@@ -183,7 +192,8 @@ def run_reference(args, world, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "prec": "fp64 oracle", "parallelism": "single host thread"},
+            "config": {"workload": workload_desc(args.workload, workload(args.workload, tuple(args.shape) if args.shape else None)),
+                       "prec": "fp64 oracle", "parallelism": "single host thread"},
             "cpu_baseline": base,
             "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -393,10 +403,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec],
             "data": "synthetic",
-            "config": {"workload": "%s: %dx%dx%d sites, %s, R=%g (%d particles), G=%g, tau=%g" % (
-                           args.workload, *w.shape,
-                           "walls z +-%g" % w.params["wall_u_hi"][0] if w.params["bc"][2] == 0 else "periodic",
-                           w.radius, n, w.params["G"], w.params["tau"][0]),
+            "config": {"workload": workload_desc(args.workload, w),
                        "prec": args.prec, "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (%.1f GB of populations)" % (
                            2 * 38 * N * {"fp64": 8, "fp32": 4, "fp16": 2}[args.prec] / 1e9)},

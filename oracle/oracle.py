@@ -1,8 +1,10 @@
 """ctypes binding of the plain C FP64 oracle (``lbgb_oracle.c``).
 
 Test infrastructure only.  The oracle shares no code with the CUDA library:
-it is compiled from its own C file with gcc (-O2 -ffp-contract=off) and only
-the seeded input generators of ``paper_2004_04080_gb300.workloads`` feed both.
+it is compiled from its own C file with gcc (-O2 -ffp-contract=off), it keeps
+its own table of parameter defaults (DEFAULTS below), and only the seeded
+input generators of ``paper_2004_04080_gb300.workloads`` (initial densities,
+particle placements, named parameter sets) feed both.
 """
 from __future__ import annotations
 
@@ -105,11 +107,27 @@ def _f64(a, shape=None):
     return a
 
 
-def make_params(**kw) -> OrcParams:
-    """Fill an OrcParams from keyword arguments (same names as lb_params)."""
-    from paper_2004_04080_gb300.workloads import default_params
+# Values of the parameters a caller leaves out: a plain two-component BGK
+# fluid at tau = 1 without coupling, wetting, walls, body force or particle
+# pair forces; reference density 1/2 per component (the 50/50 mixture of the
+# benchmark workloads); lubrication off, with the cut-off gap 0.67 and floor
+# 0.5 of App. D and the prefactor 0.1; rotation integrated (Eqs. 33-34).
+DEFAULTS = dict(
+    tau=(1.0, 1.0), G=0.0, zeta=(0.0, 0.0), rho0=(0.5, 0.5), bc=(1, 1, 1),
+    wall_u_lo=(0.0, 0.0, 0.0), wall_u_hi=(0.0, 0.0, 0.0), body_force=(0.0, 0.0, 0.0),
+    hertz_K=0.0, hertz_sigma=0.0, hertz_rcap=0.0,
+    lub_on=0, lub_hn=0.67, lub_hmin=0.5, lub_scale=0.1,
+    side_wall_k=0.0, side_wall_d=0.0, rotate=1,
+)
 
-    d = default_params()
+
+def make_params(**kw) -> OrcParams:
+    """Fill an OrcParams from keyword arguments (same names as lb_params),
+    the rest from DEFAULTS."""
+    unknown = set(kw) - set(DEFAULTS)
+    if unknown:
+        raise KeyError("unknown parameters: %s" % sorted(unknown))
+    d = dict(DEFAULTS)
     d.update(kw)
     p = OrcParams()
     for name, _t in OrcParams._fields_:

@@ -106,3 +106,48 @@ def test_hasimoto_drag_fixed_sphere_array():
         ratios.append(K / hasimoto_K(c))
     assert all(0.9 < q < 1.05 for q in ratios), ratios
     assert abs(1 - ratios[1]) <= abs(1 - ratios[0]) + 0.005  # converging with R
+
+
+@pytest.mark.slow
+def test_rotating_sphere_torque_and_decay():
+    """Eqs. 18 (reading c6: u_w = v_p + omega_p x (r_w - r_p)), 22-23 and 33:
+    a sphere spun about z in fluid at rest, its centre on a cell centre of a
+    periodic box so that the staircase is symmetric.
+      * Held at constant omega (very large mass, hence inertia), the steady
+        link torque opposes omega and matches Stokes' rotlet torque
+        T = -8 pi mu R^3 omega (mu = rho nu) within 10 % at R = 6 (measured
+        0.94 at tau = 1.5 in a 32^3 box: the halfway bounce-back surface and
+        the periodic images); the force and the other torque components
+        vanish by symmetry.
+      * Free (inertia I = 2/5 m R^2, density 1), omega decays monotonically
+        and the torque opposes it at every step.
+    A reversed rotation term in u_w makes the fluid push the sphere faster;
+    a transposed cross product in Eq. 23 reverses the torque."""
+    L, R, tau, w0 = 32, 6.0, 1.5, 1e-3
+    nu = (tau - 0.5) / 3.0
+    N = L ** 3
+    c = L / 2 - 0.5
+    o = Oracle(L, L, L, 1)
+    o.set_params(tau=(tau, tau))
+    o.init_fields(np.full(N, 0.5), np.full(N, 0.5))
+    o.add_colloids([[c, c, c]], R, 1e15, omega=[[0.0, 0.0, w0]])
+    o.step(400)
+    T, F = o.term("T_liq")[0], o.term("F_liq")[0]
+    ratio = T[2] / (-8.0 * math.pi * 1.0 * nu * R ** 3 * w0)
+    assert 0.9 < ratio < 1.1, ratio
+    assert np.abs(T[:2]).max() < 1e-12 and np.abs(F).max() < 1e-12
+    # free rotation: monotone decay, torque against omega
+    L2 = 24
+    o = Oracle(L2, L2, L2, 1)
+    o.set_params(tau=(1.0, 1.0))
+    o.init_fields(np.full(L2 ** 3, 0.5), np.full(L2 ** 3, 0.5))
+    c2 = L2 / 2 - 0.5
+    o.add_colloids([[c2, c2, c2]], R, 4.0 / 3.0 * math.pi * R ** 3, omega=[[0.0, 0.0, w0]])
+    prev = w0
+    for _ in range(60):
+        o.step(1)
+        wz = o.get_colloids()["omega"][0, 2]
+        assert 0.0 < wz < prev
+        assert o.term("T_liq")[0, 2] * wz < 0.0
+        prev = wz
+    assert prev < 0.1 * w0

@@ -412,6 +412,109 @@ def test_hertz_force_is_potential_gradient():
     assert np.allclose(pair_force(10.0 * d, 5.5, 5.5, **pr), pair_force(11.0 * d, 5.5, 5.5, **pr))
 
 
+def test_moving_particle_mass_budget_exact():
+    """Eqs. 17, 24, 25 with reading c10: while two rotating particles move
+    through a demixing-capable mixture, destroying and creating nodes, the
+    fluid mass of each component changes per step by exactly
+        - sum over destroyed nodes of rho^k (their fluid is removed, Eq. 24)
+        + sum over created nodes of rhobar^k (Eq. 25: f = f^eq(rhobar, u_w),
+          rhobar the w_i-weighted mean over neighbours fluid before and
+          after the remap, rho0^k if there is none)
+        - sum over bounce-back links (x, i) of 6 w_i rho^k(x) c_i . u_w (Eq. 17),
+    u_w = v_p + omega_p x (x + c_i/2 - r_p) the rigid-body velocity of Eq. 18
+    (reading c6) at v(t-1/2), omega(t-1/2); streaming and the collision
+    (Eqs. 3, 13-16) conserve it.  The right-hand side is formed here from the
+    observable state alone (fields, node maps and particle state before and
+    after each step), so a slip in the refill weights, the destroy set, the
+    wall-velocity term or its rotation sign breaks the identity."""
+    shape = (20, 18, 16)
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    rng = np.random.default_rng(5)
+    a = 0.5 * (1 + 0.05 * rng.uniform(-1, 1, N))
+    b = 0.5 * (1 - 0.05 * rng.uniform(-1, 1, N))
+    params = dict(G=0.5, zeta=(0.1, -0.1), hertz_K=20, hertz_sigma=9.0, hertz_rcap=8.0, rho0=(0.5, 0.5))
+    o = make(shape, 2, **params)
+    o.init_fields(a, b)
+    o.add_colloids([[6.3, 7.7, 5.2], [14.6, 11.1, 10.4]], [3.6, 3.2], [400.0, 300.0],
+                   vel=[[0.08, -0.05, 0.03], [-0.06, 0.04, 0.05]],
+                   omega=[[0.01, 0.02, -0.015], [-0.02, 0.0, 0.03]])
+    c, w, _ = lattice()
+    s = np.arange(N)
+    X, Y, Z = s % nx, (s // nx) % ny, s // (nx * ny)
+    NB = [((X + c[i, 0]) % nx) + nx * (((Y + c[i, 1]) % ny) + ny * ((Z + c[i, 2]) % nz)) for i in range(19)]
+    xyz = np.stack([X, Y, Z], 1).astype(float)
+    box = np.array(shape, float)
+    events = 0
+    for _ in range(40):
+        ra, rb, _ = o.get_fields()
+        own0, col, m0 = o.owner(), o.get_colloids(), o.totals()[:2]
+        o.step(1)
+        own1, m1 = o.owner(), o.totals()[:2]
+        destroyed = (own0 == -1) & (own1 >= 0)
+        created = (own0 >= 0) & (own1 == -1)
+        events += int(destroyed.sum() + created.sum())
+        expect = np.zeros(2)
+        rho_b = []
+        for k, rho in enumerate((ra, rb)):
+            num, den = np.zeros(N), np.zeros(N)
+            for i in range(1, 19):
+                ok = (own0[NB[i]] == -1) & (own1[NB[i]] == -1)
+                num += np.where(ok, w[i] * rho[NB[i]], 0.0)
+                den += np.where(ok, w[i], 0.0)
+            bar = np.where(den > 0, num / np.where(den > 0, den, 1.0), params["rho0"][k])
+            expect[k] = bar[created].sum() - rho[destroyed].sum()
+            rho_b.append(np.where(created, bar, rho))
+        fluid = own1 == -1
+        for i in range(1, 19):
+            p = own1[NB[i]]
+            m = fluid & (p >= 0)
+            if not m.any():
+                continue
+            rw = xyz[m] + 0.5 * c[i] - col["pos"][p[m]]
+            rw -= box * np.round(rw / box)
+            cu = (col["vel"][p[m]] + np.cross(col["omega"][p[m]], rw)) @ c[i]
+            for k in range(2):
+                expect[k] -= (6.0 * w[i] * rho_b[k][m] * cu).sum()
+        assert np.all(np.abs((m1 - m0) - expect) < 1e-13 * m0), ((m1 - m0), expect)
+    assert events > 10
+
+
+def test_lubrication_magnitude_leading_order():
+    """Eq. 27 (reading c13) against the leading-order lubrication force
+    between two spheres approaching along their line of centres (Reynolds
+    lubrication of the gap; e.g. Jeffrey and Onishi 1984, Kim and Karrila
+    1991): F h -> 6 pi mu (a_i a_j / (a_i + a_j))^2 v as h -> 0, mu = rho nu
+    with rho = 1 and the mixture's nu = cs^2 (tau - 1/2) averaged over the two
+    components; the prefactor s scales it, the cut-off 1/h_n subtracts a
+    constant, the floor h_min clamps it, and a relative velocity
+    perpendicular to the line of centres gives no squeeze force."""
+    tau = (1.3, 0.9)
+    nu = 0.5 * ((tau[0] - 0.5) + (tau[1] - 0.5)) / 3.0
+    for Ri, Rj, s in ((5.5, 5.5, 1.0), (4.0, 6.0, 0.3)):
+        astar = Ri * Rj / (Ri + Rj)
+        pr = dict(lub_on=1, lub_hn=50.0, lub_hmin=1e-6, lub_scale=s, tau=tau)
+        d = np.array([0.48, -0.6, 0.64])
+        vn = 0.013
+        for h in (1e-3, 1e-4):
+            F = pair_force((Ri + Rj + h) * d, Ri, Rj, vi=vn * d, vj=(0, 0, 0), **pr)
+            leading = 6.0 * math.pi * nu * s * astar ** 2 * vn
+            assert abs((-F @ d) * h / leading - 1.0) < 1e-4 + h / 50.0
+            assert np.allclose(F, (F @ d) * d, atol=1e-12 * abs(F @ d))
+        # below the floor the force stays at its value at h_min
+        pr_floor = dict(pr, lub_hmin=0.05)
+        F1 = pair_force((Ri + Rj + 0.01) * d, Ri, Rj, vi=vn * d, **pr_floor)
+        F2 = pair_force((Ri + Rj + 0.05) * d, Ri, Rj, vi=vn * d, **pr_floor)
+        assert np.allclose(F1, F2, rtol=1e-14)
+        # sliding past each other: no squeeze force (to the rounding of
+        # v . r_hat, relative to the squeeze force at the same gap and speed)
+        t = np.cross(d, [0.0, 0.0, 1.0])
+        t /= np.linalg.norm(t)
+        Ft = pair_force((Ri + Rj + 0.01) * d, Ri, Rj, vi=vn * t, **pr)
+        Fn = pair_force((Ri + Rj + 0.01) * d, Ri, Rj, vi=vn * d, **pr)
+        assert np.abs(Ft).max() < 1e-12 * np.abs(Fn).max()
+
+
 def test_lubrication_opposes_approach():
     """Eq. 27: inside h_n the lubrication force on i opposes the relative
     approach velocity along the line of centres and diverges like 1/h."""

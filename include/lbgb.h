@@ -51,7 +51,7 @@ enum {
     LB_ERR_NOMEM = -4,     /* workspace too small                             */
     LB_ERR_NONFINITE = -5, /* a density became non-finite or negative         */
     LB_ERR_OVERLAP = -6,   /* two particles claimed the same lattice node     */
-    LB_ERR_TIMEOUT = -7    /* a bounded device wait (TMA copy) gave up        */
+    LB_ERR_TIMEOUT = -7    /* reserved: no call returns it (no kernel spin-waits) */
 };
 
 /* Storage precision of the populations.  LB_FP64 and LB_FP32 compute in the
@@ -89,10 +89,7 @@ int lb_workspace_bytes(int nx, int ny, int nz, int prec, int max_colloids, size_
  * d_workspace: device pointer, 256-byte aligned, >= lb_workspace_bytes bytes,
  * owned by the caller.  cuda_stream: a cudaStream_t or NULL.
  * Lattice sides must be >= 4; nx must be a multiple of 4; nx*ny*nz below
- * 2^31 - 4096 (LB_ERR_ARG otherwise: sites are indexed in 32 bits).  With
- * LBGB_FUSED_TMA=1 in the environment at lb_create, LB_FP32 (and LB_FP16 with
- * nx a multiple of 8) use a fused lattice kernel that stages its tiles with
- * tensor-memory-accelerator copies instead of the default plain loads. */
+ * 2^31 - 4096 (LB_ERR_ARG otherwise: sites are indexed in 32 bits). */
 int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void *d_workspace,
               size_t bytes, void *cuda_stream, lb_ctx **out);
 
@@ -150,7 +147,8 @@ int lb_get_owner(lb_ctx *ctx, int *out);
 /* Kernel timing.  While enabled, lb_step records a CUDA event pair on the
  * context stream around every launch of the fused lattice kernel (the
  * collide + Shan-Chen + bounce-back + stream kernel, the dominant one) and
- * around every full density pass (launched when particles are present).
+ * around the full density pass that precedes it when particles are present
+ * (see lb_fused_kernel).
  * lb_profile(ctx, 1) enables and clears the records, lb_profile(ctx, 0)
  * disables them; lb_profile_read_kernel waits for the recorded events of one
  * kernel (LB_KERNEL_FUSED or LB_KERNEL_DENSITY; LB_ERR_ARG otherwise) and
@@ -168,8 +166,7 @@ enum { LB_KERNEL_FUSED = 0, LB_KERNEL_DENSITY = 1 };
  * the same way every step.  The sequence of bits is fixed by `seed` and the
  * number of steps since this call.  No effect on LB_FP32 / LB_FP64 contexts.
  * The adjoint functions return LB_ERR_STATE while stochastic rounding is on
- * (their forward recomputation would not reproduce the recorded steps).  The
- * opt-in TMA kernel (LBGB_FUSED_TMA) rounds to nearest.
+ * (their forward recomputation would not reproduce the recorded steps).
  * LB_ERR_ARG for another mode. */
 enum { LB_ROUND_NEAREST = 0, LB_ROUND_STOCHASTIC = 1 };
 int lb_set_rounding(lb_ctx *ctx, int mode, unsigned long long seed);
@@ -263,6 +260,22 @@ int lb_totals_static(const void *d_pops, int prec, int nx, int ny, int nz, long 
 
 /* Number of kernel launches issued by this context since creation. */
 long long lb_launch_count(const lb_ctx *ctx);
+
+/* Which fused lattice kernel lb_step launches in the context's present state
+ * (the sequence of Sec. 3.1 is the same for all; they differ in how the
+ * moments and the Shan-Chen halo densities of Eq. 11 reach the collision):
+ *  LB_FUSED_MOMENTUM  particles present, tau_A = tau_B = 1: a density pass
+ *      writes rho^k and j^k of every node (Eqs. 6-7); the fused kernel
+ *      collides from them (Eq. 16 at omega = 1), staging the halo of rho^k
+ *      and of the node map in shared memory with asynchronous copies;
+ *  LB_FUSED_TWO_PASS  particles, other tau: a density pass writes rho^k, the
+ *      fused kernel re-reads the populations;
+ *  LB_FUSED_PLAIN     no particles: one pass, halo densities formed from the
+ *      neighbours' populations.
+ * Returns the code, or LB_ERR_ARG for a NULL context. */
+enum { LB_FUSED_MOMENTUM = 1, LB_FUSED_TWO_PASS = 2, LB_FUSED_PLAIN = 3 };
+int lb_fused_kernel(const lb_ctx *ctx);
+
 
 /* Release the context (not the caller's workspace). */
 int lb_destroy(lb_ctx *ctx);

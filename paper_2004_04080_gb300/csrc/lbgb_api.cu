@@ -7,7 +7,6 @@
 #include <string.h>
 
 #include <cuda.h>
-#include <cudaTypedefs.h>
 #include <stdlib.h>
 
 #include <new>
@@ -17,8 +16,6 @@
 using namespace lbgb;
 
 struct lb_ctx {
-    CUtensorMap tmaps[2];       // population buffers 0 and 1 for the TMA fused kernel
-    int tma_ok;                 // tensor maps encoded and enabled
     Lattice L;
     int prec;
     int maxc;
@@ -130,44 +127,6 @@ int launched(lb_ctx* ctx, int n, const char* what) {
 
 double* stage_ptr(lb_ctx* ctx) { return (double*)ctx->L.f_nxt; }
 
-// Tensor maps of the two population buffers for the TMA-pipelined fused
-// kernel (FP32 / FP16): a 4-D view {x, y, z, population} with the box of one
-// tile plus its ring.  That kernel is selected with LBGB_FUSED_TMA=1 in the
-// environment (and needs 16-byte row strides: nx a multiple of 4 for FP32, of
-// 8 for FP16).  It is not the default: a plane box of 38 populations
-// (60.8 KB in FP32) three planes deep leaves room for one 8-warp block per
-// SM, too few warps to hide the collision's instruction latency, and it
-// measured slower than the plain fused kernel (two 8-warp blocks per SM).
-void encode_tensor_maps(lb_ctx* ctx, const Layout& l) {
-    const Lattice& L = ctx->L;
-    if (ctx->prec == LB_FP64) return;
-    size_t sb = storage_bytes(ctx->prec);
-    if (((size_t)L.nx * sb) % 16 != 0) return;
-    const char* env = getenv("LBGB_FUSED_TMA");
-    if (!env || env[0] != '1') return;
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn) {
-        cudaGetLastError();
-        return;
-    }
-    PFN_cuTensorMapEncodeTiled_v12000 encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    cuuint64_t dims[4] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny, (cuuint64_t)L.nz, (cuuint64_t)(2 * Q)};
-    cuuint64_t strides[3] = {(cuuint64_t)L.nx * sb, (cuuint64_t)L.nx * L.ny * sb, (cuuint64_t)L.pstride * sb};
-    cuuint32_t box[4] = {(cuuint32_t)fused_tma_box_x(ctx->prec), 10u, 1u, (cuuint32_t)(2 * Q)};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUtensorMapDataType dt = ctx->prec == LB_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    void* bases[2] = {ctx->ws + l.f0, ctx->ws + l.f1};
-    for (int b = 0; b < 2; b++) {
-        CUresult r = encode(&ctx->tmaps[b], dt, 4, bases[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return;
-    }
-    ctx->tma_ok = 1;
-}
-
 }  // namespace
 
 extern "C" {
@@ -258,13 +217,14 @@ int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_worksp
     ctx->cells = ctx->ws + l.cells;
     ctx->cells_bytes = l.cells_bytes;
     L.nc = 0;
-    ctx->tma_ok = 0;
-    encode_tensor_maps(ctx, l);
     // empty node map, no particles, no error flags
     cudaError_t e = cudaMemsetAsync(ctx->ws + l.mask, 0, (size_t)L.N, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.owner, 0xff, (size_t)L.N * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.evt, 0, (size_t)L.N * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.flags, 0, 64, ctx->stream);
+    // psi: kernels read it on particle nodes that no virtual density has
+    // reached yet (deep nodes), where any finite value serves
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.psi, 0, (size_t)2 * L.N * compute_bytes(prec), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.col, 0, (size_t)mc * DOUBLES_PER_PARTICLE * 8, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.prev, 0, (size_t)mc * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -457,12 +417,12 @@ int lb_step(lb_ctx* ctx, int nsteps) {
         n += launch_remap(L, ctx->prec, ctx->maxc, s);  // destroy / create (Eqs. 24, 25)
         // rho^k (Eq. 6) of every fluid node when particles need virtual
         // densities (Eq. 20); with omega = 1 the pass also writes j^k, and
-        // the fused kernel collides from the momenta instead of re-reading the
+        // the fused kernel collides from the moments instead of re-reading the
         // populations.  Without particles only the planes next to the walls
         // (the fused kernel then forms its halo densities itself).
         const bool unit = L.P.tau[0] == 1.0 && L.P.tau[1] == 1.0;
         L.dense_psi = L.nc > 0;
-        L.dense_mom = L.dense_psi && unit && !ctx->tma_ok;
+        L.dense_mom = L.dense_psi && unit;
         if (L.dense_psi) {
             const bool timed_d = ctx->prof_on && ctx->prof_nd < PROF_MAX;
             if (timed_d) CK(cudaEventRecord(ctx->prof_evd[2 * ctx->prof_nd], s), "profile event");
@@ -479,10 +439,7 @@ int lb_step(lb_ctx* ctx, int nsteps) {
         bool timed = ctx->prof_on && ctx->prof_n < PROF_MAX;
         if (timed) CK(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], s), "profile event");
         // Eqs. 11, 14, 16, 3, 9, 17; the link forces of Eqs. 19, 22, 23
-        if (ctx->tma_ok)
-            n += launch_fluid_step_tma(L, ctx->prec, &ctx->tmaps[L.f_cur == (void*)ctx->ws ? 0 : 1], s);
-        else
-            n += launch_fluid_step(L, ctx->prec, s);
+        n += launch_fluid_step(L, ctx->prec, s);
         if (timed) {
             CK(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], s), "profile event");
             ctx->prof_n++;
@@ -507,7 +464,6 @@ int lb_step(lb_ctx* ctx, int nsteps) {
     int flags = 0;
     CK(cudaMemcpyAsync(&flags, L.flags, 4, cudaMemcpyDeviceToHost, s), "read flags");
     CK(cudaStreamSynchronize(s), "step sync");
-    if (flags & FLAG_TIMEOUT) return set_err(ctx, LB_ERR_TIMEOUT, "a bounded device wait gave up");
     if (flags & FLAG_OVERLAP) return set_err(ctx, LB_ERR_OVERLAP, "two particles claimed one node");
     if (flags & FLAG_NONFINITE) return set_err(ctx, LB_ERR_NONFINITE, "non-finite or negative density");
     return LB_OK;
@@ -604,6 +560,14 @@ int lb_get_colloid_terms(lb_ctx* ctx, int which, double* out) {
 }
 
 long long lb_launch_count(const lb_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int lb_fused_kernel(const lb_ctx* ctx) {
+    if (!ctx) return LB_ERR_ARG;
+    const bool unit = ctx->L.P.tau[0] == 1.0 && ctx->L.P.tau[1] == 1.0;
+    if (ctx->L.nc > 0) return unit ? LB_FUSED_MOMENTUM : LB_FUSED_TWO_PASS;
+    return LB_FUSED_PLAIN;
+}
+
 
 // ------------------------------------------------------------- adjoint
 

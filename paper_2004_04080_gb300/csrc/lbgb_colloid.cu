@@ -940,12 +940,7 @@ int launch_virtual(const Lattice& L, int prec, int store_terms, cudaStream_t st)
     if (L.nc <= 0) return 0;
     const int zc = L.nz < VZC ? L.nz : VZC;
     dim3 grid((L.nx + VTX - 1) / VTX, (L.ny + VTY - 1) / VTY, (L.nz + zc - 1) / zc);
-    static bool attr_set[3] = {false, false, false};
-    if (!attr_set[prec]) {
-        DISPATCHC(prec, (cudaFuncSetAttribute(k_virtual<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)virtual_smem<P>())));
-        attr_set[prec] = true;
-    }
+    DISPATCHC(prec, (kernel_setup<k_virtual<P>>(VTX * VTY, virtual_smem<P>())));
     DISPATCHC(prec, (k_virtual<P><<<grid, dim3(VTX, VTY), virtual_smem<P>(), st>>>(L, store_terms, zc)));
     return 1;
 }

@@ -114,65 +114,6 @@ __global__ void k_wall_psi(Lattice L) {
     pw[(side * 2 + 1) * nxy + w] = den > C(0) ? num1 / den : C(0);
 }
 
-// U0 = v_p + omega_p x (x - r_p) for a site x next to particle p.  For the
-// link along c_i the wall velocity of Eq. 18 is u_w = v_p + omega_p x (r_w -
-// r_p) with r_w = x + c_i/2, and c_i . u_w = c_i . U0 because c_i . (omega x
-// c_i) = 0: one U0 per site serves every link of that site into p.  The
-// offset x - r_p is formed from the integer part of r_p and its fractional
-// part, exact in FP64 and accurate to FP32 rounding of a number below 1 in the
-// FP32 forms (which read the FP32 particle snapshot).  The loads
-// (particle_load) and the arithmetic (particle_u0_of) are split so that a
-// caller can issue the loads early.
-template <typename C>
-struct ParticleRef {
-    int ip[3];
-    C fr[3], v[3], w[3];
-};
-
-template <typename C>
-__device__ __forceinline__ ParticleRef<C> particle_load(const Lattice& L, int p) {
-    ParticleRef<C> r;
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        if (sizeof(C) == 8) {
-            double q = __ldg(L.pos + 3 * p + d);
-            r.ip[d] = (int)floor(q);
-            r.fr[d] = C(q - (double)r.ip[d]);
-            r.v[d] = C(__ldg(L.vel + 3 * p + d));
-            r.w[d] = C(__ldg(L.omg + 3 * p + d));
-        } else {
-            r.ip[d] = __ldg(L.ipos + 3 * p + d);
-            r.fr[d] = C(__ldg(L.fsnap + 9 * p + d));
-            r.v[d] = C(__ldg(L.fsnap + 9 * p + 3 + d));
-            r.w[d] = C(__ldg(L.fsnap + 9 * p + 6 + d));
-        }
-    }
-    return r;
-}
-
-template <typename C>
-__device__ __forceinline__ void particle_u0_of(const Lattice& L, const ParticleRef<C>& r, int x, int y, int z,
-                                               C (&U0)[3], C (&rel)[3]) {
-    int xs[3] = {x, y, z}, Ls[3] = {L.nx, L.ny, L.nz};
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        int dd = xs[d] - r.ip[d];
-        if (L.per[d]) {
-            if (2 * dd > Ls[d]) dd -= Ls[d];
-            else if (2 * dd < -Ls[d]) dd += Ls[d];
-        }
-        rel[d] = C(dd) - r.fr[d];
-    }
-    U0[0] = r.v[0] + (r.w[1] * rel[2] - r.w[2] * rel[1]);
-    U0[1] = r.v[1] + (r.w[2] * rel[0] - r.w[0] * rel[2]);
-    U0[2] = r.v[2] + (r.w[0] * rel[1] - r.w[1] * rel[0]);
-}
-
-template <typename C>
-__device__ __forceinline__ void particle_u0(const Lattice& L, int p, int x, int y, int z, C (&U0)[3], C (&rel)[3]) {
-    particle_u0_of<C>(L, particle_load<C>(L, p), x, y, z, U0, rel);
-}
-
 // Add the link force and torque of one site (Eqs. 22, 23) to F_liq, T_liq of
 // its particle with FP64 atomics (p < 0: no link of the site reaches a
 // particle).  One warp instruction per component; the L2 serves them
@@ -975,15 +916,8 @@ __global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : 5)) k_fused_w
 
 template <int P, bool SR>
 static int launch_fused_warp_t(const Lattice& L, cudaStream_t st) {
-    static bool attr_set = false;
-    static int per_sm = 0;
     const size_t smem = sizeof(WarpShared<P>) * WPB;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_fused_warp<P, SR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_warp<P, SR>, FTX * WPB, smem);
-        if (per_sm < 1) per_sm = 1;
-        attr_set = true;
-    }
+    const int per_sm = kernel_setup<k_fused_warp<P, SR>>(FTX * WPB, smem);
     int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + WPB - 1) / WPB);
     int zc = z_chunks(L, tiles, per_sm, 8);
     dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + WPB - 1) / WPB, (L.nz + zc - 1) / zc);
@@ -997,227 +931,6 @@ static int launch_fused_warp(const Lattice& L, cudaStream_t st) {
     if constexpr (P == LB_FP16)
         if (L.sr) return launch_fused_warp_t<P, true>(L, st);
     return launch_fused_warp_t<P, false>(L, st);
-}
-
-// ----------------------------------------------- TMA-pipelined fused step
-// The same per-plane work as k_fused for the FP32 / FP16 forms, with the
-// populations of the tile and its one-site ring brought into shared memory by
-// the tensor-memory accelerator: one cp.async.bulk.tensor per plane copies a
-// box of (32 + 2 PAD) x 10 sites x 38 populations (PAD = 16 bytes of
-// elements, so that the box starts on a 16-byte boundary), three planes are
-// in flight on mbarriers, and the threads only read shared memory.  Waits are
-// bounded: on a timeout the block records LB_ERR_TIMEOUT, waits (bounded)
-// for its outstanding copies and returns.  Ring sites outside the box's
-// domain (periodic images at the lattice edges, which the copy fills with
-// zeros) are read from global memory.
-constexpr int TNB = 3;         // planes in flight
-constexpr int TBY = FTY + 2;   // box rows
-constexpr long TMA_SPIN = 1L << 22;
-
-template <int PREC>
-struct TmaGeom {
-    typedef typename Prec<PREC>::S S;
-    static constexpr int PAD = 16 / (int)sizeof(S);
-    static constexpr int BXT = FTX + 2 * PAD;
-    static constexpr unsigned BYTES = (unsigned)(BXT * TBY * 2 * Q * sizeof(S));
-};
-
-template <int PREC>
-struct TmaShared {
-    typedef typename Prec<PREC>::S S;
-    typedef typename Prec<PREC>::C C;
-    S buf[TNB][2 * Q][TBY][TmaGeom<PREC>::BXT];
-    C psi[3][2][RH][RW];
-    int nd[3][RH][RW];
-    unsigned long long mbar[TNB];
-    int abort;
-};
-
-__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
-    for (long it = 0; it < TMA_SPIN; it++)
-        if (mbar_try(bar, parity)) return true;
-    return false;
-}
-
-template <int PREC>
-__global__ void __launch_bounds__(FNT, 1) k_fused_tma(Lattice L, int zc, const __grid_constant__ CUtensorMap tm) {
-    typedef typename Prec<PREC>::S S;
-    typedef typename Prec<PREC>::C C;
-    typedef TmaGeom<PREC> TG;
-    extern __shared__ unsigned char smem_raw[];
-    TmaShared<PREC>& sh =
-        *reinterpret_cast<TmaShared<PREC>*>((((uintptr_t)smem_raw) + 127) & ~(uintptr_t)127);
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
-    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
-    const int W = min(FTX, L.nx - x0), H = min(FTY, L.ny - y0);
-    const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, L.nz);
-    const bool act = tx < W && ty < H;
-    const S* fg = (const S*)L.f_cur;
-    const C* psig = (const C*)L.psi;
-    if (tid == 0) {
-        for (int b = 0; b < TNB; b++)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sh.mbar[b])), "r"(1) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        sh.abort = 0;
-    }
-    __syncthreads();
-    unsigned phase = 0;    // parity bit per buffer
-    unsigned pending = 0;  // buffers with a copy issued and not yet waited for
-    auto wall_plane = [&](int p) { return !L.per[2] && (p < 0 || p >= L.nz); };
-    auto buf_of = [&](int p) { return (p - z0 + 1) % TNB; };
-    auto issue = [&](int p) {
-        if (p > z1 || wall_plane(p)) return;
-        int b = buf_of(p);
-        pending |= 1u << b;
-        if (tid != 0) return;
-        int Z = p < 0 ? p + L.nz : (p >= L.nz ? p - L.nz : p);
-        unsigned bar = smem_u32(&sh.mbar[b]);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(TG::BYTES) : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-            "%5}], [%6];" ::"r"(smem_u32(&sh.buf[b][0][0][0])),
-            "l"(reinterpret_cast<unsigned long long>(&tm)), "r"(x0 - TG::PAD), "r"(y0 - 1), "r"(Z), "r"(0), "r"(bar)
-            : "memory");
-    };
-    auto wait = [&](int p) -> bool {
-        if (wall_plane(p)) return true;
-        int b = buf_of(p);
-        bool ok = mbar_wait_bounded(smem_u32(&sh.mbar[b]), (phase >> b) & 1u);
-        phase ^= 1u << b;
-        pending &= ~(1u << b);
-        if (!ok) sh.abort = 1;
-        return ok;
-    };
-    // psi^k and node flags of plane p (tile + ring) into ring slot `slot`
-    auto fill = [&](int p, int slot) {
-        if (wall_plane(p)) {
-            const C* pw = (const C*)L.psi_wall;
-            int side = p < 0 ? 0 : 1;
-            long long nxy = (long long)L.nx * L.ny;
-            for (int q = tid; q < (W + 2) * (H + 2); q += FNT) {
-                int lx = q % (W + 2) - 1, ly = q / (W + 2) - 1;
-                int X = x0 + lx, Y = y0 + ly;
-                X = X < 0 ? X + L.nx : (X >= L.nx ? X - L.nx : X);
-                Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
-                long long w = (long long)X + (long long)L.nx * Y;
-                sh.psi[slot][0][ly + 1][lx + 1] = pw[(side * 2 + 0) * nxy + w];
-                sh.psi[slot][1][ly + 1][lx + 1] = pw[(side * 2 + 1) * nxy + w];
-                sh.nd[slot][ly + 1][lx + 1] = ND_WALL;
-            }
-            return;
-        }
-        int b = buf_of(p);
-        int Z = p < 0 ? p + L.nz : (p >= L.nz ? p - L.nz : p);
-        long long zoff = (long long)L.nx * L.ny * Z;
-        int npos = (W + 2) * (H + 2);
-        for (int q = tid; q < npos; q += FNT) {
-            // own sites first (q < W*H), then the ring
-            int lx, ly;
-            if (q < W * H) {
-                lx = q % W;
-                ly = q / W;
-            } else {
-                int r = q - W * H;
-                if (r < W + 2) { lx = r - 1; ly = -1; }
-                else if (r < 2 * (W + 2)) { lx = r - (W + 2) - 1; ly = H; }
-                else if (r < 2 * (W + 2) + H) { lx = -1; ly = r - 2 * (W + 2); }
-                else { lx = W; ly = r - 2 * (W + 2) - H; }
-            }
-            int X = x0 + lx, Y = y0 + ly;
-            bool inside = X >= 0 && X < L.nx && Y >= 0 && Y < L.ny;
-            X = X < 0 ? X + L.nx : (X >= L.nx ? X - L.nx : X);
-            Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
-            long long s = (long long)X + (long long)L.nx * Y + zoff;
-            C r0 = 0, r1 = 0;
-            int nd = ND_FLUID;
-            if (L.mask[s]) {
-                r0 = psig[s];
-                r1 = psig[L.N + s];
-                nd = L.owner[s];
-            } else if (inside) {
-#pragma unroll
-                for (int i = 0; i < Q; i++) {
-                    r0 += ld_pop(&sh.buf[b][i][ly + 1][lx + TG::PAD], pop_shift<S, C>(L, 0, i));
-                    r1 += ld_pop(&sh.buf[b][Q + i][ly + 1][lx + TG::PAD], pop_shift<S, C>(L, 1, i));
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < Q; i++) {
-                    r0 += ld_pop(fg + ((long long)i) * L.pstride + s, pop_shift<S, C>(L, 0, i));
-                    r1 += ld_pop(fg + ((long long)(Q + i)) * L.pstride + s, pop_shift<S, C>(L, 1, i));
-                }
-            }
-            sh.psi[slot][0][ly + 1][lx + 1] = r0;
-            sh.psi[slot][1][ly + 1][lx + 1] = r1;
-            sh.nd[slot][ly + 1][lx + 1] = nd;
-        }
-    };
-
-    issue(z0 - 1);
-    issue(z0);
-    issue(z0 + 1);
-    wait(z0 - 1);
-    fill(z0 - 1, 0);
-    __syncthreads();
-    if (!sh.abort) issue(z0 + 2);
-    wait(z0);
-    fill(z0, 1);
-    int lo = 0, mid = 1, hi = 2;
-    for (int z = z0; z < z1; z++) {
-        wait(z + 1);
-        fill(z + 1, hi);
-        __syncthreads();
-        if (sh.abort) break;
-        int pf = -1;
-        C Fp[3] = {0, 0, 0}, Tp[3] = {0, 0, 0};
-        if (act) {
-            int sl[3] = {lo, mid, hi};
-            int b = buf_of(z);
-            // own populations, moments from the shared copy
-            OwnSite<PREC> m;
-#pragma unroll
-            for (int k = 0; k < 2; k++) {
-                C r = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-                for (int i = 0; i < Q; i++) {
-                    C v = ld_pop(&sh.buf[b][k * Q + i][ty + 1][tx + TG::PAD], pop_shift<S, C>(L, k, i));
-                    r += v;
-                    if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
-                    if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
-                    if (cz(i) > 0) jz += v; else if (cz(i) < 0) jz -= v;
-                }
-                m.rho[k] = r;
-                m.j[k][0] = jx; m.j[k][1] = jy; m.j[k][2] = jz;
-            }
-            const bool solid = sh.nd[mid][ty + 1][tx + 1] != ND_FLUID;
-            const LinkInfo li = link_info(sh, sl, tx, ty, solid);
-            const ParticleRef<C> pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
-            collide_site<PREC, false, false>(L, sh, sl, x0 + tx, y0 + ty, z, ty, m, solid,
-                                      [&](int q) { return &sh.buf[b][q][ty + 1][tx + TG::PAD]; }, li, pref, pf, Fp,
-                                      Tp);
-        }
-        commit_link_forces<C>(L, pf, Fp, Tp);
-        __syncthreads();
-        issue(z + 3);
-        int t = lo; lo = mid; mid = hi; hi = t;
-    }
-    if (sh.abort) {
-        // record the timeout, then wait (bounded) for the copies still in flight
-        if (tid == 0) atomicOr(L.flags, FLAG_TIMEOUT);
-        for (int b = 0; b < TNB; b++)
-            if ((pending >> b) & 1u) mbar_wait_bounded(smem_u32(&sh.mbar[b]), (phase >> b) & 1u);
-    }
 }
 
 // rho^k of the fluid nodes in the planes next to the walls, written to psi
@@ -1374,55 +1087,11 @@ int launch_wall_psi(const Lattice& L, int prec, cudaStream_t st) {
     return 1;
 }
 
-size_t fused_tma_smem(int prec) {
-    if (prec == LB_FP32) return sizeof(TmaShared<LB_FP32>) + 128;
-    if (prec == LB_FP16) return sizeof(TmaShared<LB_FP16>) + 128;
-    return 0;
-}
-
-int fused_tma_box_x(int prec) {
-    return prec == LB_FP32 ? TmaGeom<LB_FP32>::BXT : (prec == LB_FP16 ? TmaGeom<LB_FP16>::BXT : 0);
-}
-
-int launch_fluid_step_tma(const Lattice& L, int prec, const void* tmap, cudaStream_t st) {
-    int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + FTY - 1) / FTY);
-    // one block per SM: z chunks so that the grid is several waves deep
-    int zc = (int)((long long)L.nz * tiles / (152 * 6));
-    zc = zc < 4 ? 4 : zc;
-    zc = zc > L.nz ? L.nz : zc;
-    dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + FTY - 1) / FTY, (L.nz + zc - 1) / zc);
-    const CUtensorMap& tm = *(const CUtensorMap*)tmap;
-    static bool attr_set[3] = {false, false, false};
-    if (prec == LB_FP32) {
-        if (!attr_set[prec]) {
-            cudaFuncSetAttribute(k_fused_tma<LB_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fused_tma_smem(prec));
-            attr_set[prec] = true;
-        }
-        k_fused_tma<LB_FP32><<<grid, dim3(FTX, FTY), fused_tma_smem(prec), st>>>(L, zc, tm);
-    } else {
-        if (!attr_set[prec]) {
-            cudaFuncSetAttribute(k_fused_tma<LB_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fused_tma_smem(prec));
-            attr_set[prec] = true;
-        }
-        k_fused_tma<LB_FP16><<<grid, dim3(FTX, FTY), fused_tma_smem(prec), st>>>(L, zc, tm);
-    }
-    return 1;
-}
-
 // Number of z chunks for a kernel with `per_sm` resident blocks per SM: the
 // grid (tiles x chunks) is close to a whole number of full waves, with
 // chunks of at least `zmin` planes.
 static int z_chunks(const Lattice& L, int tiles, int per_sm, int zmin) {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    long long R = (long long)sms * per_sm;
+    long long R = (long long)device_sms() * per_sm;
     int best = 1;
     double best_eff = 0;
     for (int zc = L.nz; zc >= zmin || zc == L.nz; zc--) {
@@ -1443,15 +1112,8 @@ template <int P, bool UNIT, bool SR>
 static int launch_fused_async_t(const Lattice& L, cudaStream_t st) {
     constexpr int TY = ASYNC_TY, NT = FTX * TY;
     typedef AsyncShared<P, TY> SH;
-    static bool attr_set = false;
-    static int per_sm = 0;
     const size_t smem = sizeof(SH);
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_fused_async<P, UNIT, TY, SR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_async<P, UNIT, TY, SR>, NT, smem);
-        if (per_sm < 1) per_sm = 1;
-        attr_set = true;
-    }
+    const int per_sm = kernel_setup<k_fused_async<P, UNIT, TY, SR>>(NT, smem);
     int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + TY - 1) / TY);
     int zc = z_chunks(L, tiles, per_sm, 8);
     dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
@@ -1474,12 +1136,8 @@ static int launch_fused_async(const Lattice& L, bool unit, cudaStream_t st) {
 // population stage at omega = 1
 template <int P, bool UNIT, bool SR>
 static int launch_fused_plain(const Lattice& L, int zc, dim3 grid, cudaStream_t st) {
-    static bool attr_set = false;
     const size_t smem = UNIT ? offsetof(FusedShared<P>, stage) : sizeof(FusedShared<P>);
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_fused<P, UNIT, SR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = true;
-    }
+    kernel_setup<k_fused<P, UNIT, SR>>(FTX * FTY, smem);
     k_fused<P, UNIT, SR><<<grid, dim3(FTX, FTY), smem, st>>>(L, zc);
     return 1;
 }

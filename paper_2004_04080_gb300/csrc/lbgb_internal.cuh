@@ -3,6 +3,7 @@
 // conversions, the context layout and the kernel entry points.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -140,7 +141,7 @@ struct Lattice {
     lb_params P;
 };
 
-enum { FLAG_NONFINITE = 1, FLAG_OVERLAP = 2, FLAG_TIMEOUT = 4 };
+enum { FLAG_NONFINITE = 1, FLAG_OVERLAP = 2 };
 
 // node codes of the shared-memory planes of the streaming kernels: a fluid
 // node, a node beyond a wall, or the index (>= 0) of the particle that owns a
@@ -299,6 +300,65 @@ __device__ __forceinline__ void mixture(const Lattice& L, const C (&rho)[2], con
     om = q / (C(3) + C(0.5) * q);                                     // 1/(3 nubar + 1/2)
 }
 
+// U0 = v_p + omega_p x (x - r_p) for a site x next to particle p.  For the
+// link along c_i the wall velocity of Eq. 18 is u_w = v_p + omega_p x (r_w -
+// r_p) with r_w = x + c_i/2, and c_i . u_w = c_i . U0 because c_i . (omega x
+// c_i) = 0: one U0 per site serves every link of that site into p.  The
+// offset x - r_p is formed from the integer part of r_p and its fractional
+// part, exact in FP64 and accurate to FP32 rounding of a number below 1 in the
+// FP32 forms (which read the FP32 particle snapshot).  The loads
+// (particle_load) and the arithmetic (particle_u0_of) are split so that a
+// caller can issue the loads early.
+template <typename C>
+struct ParticleRef {
+    int ip[3];
+    C fr[3], v[3], w[3];
+};
+
+template <typename C>
+__device__ __forceinline__ ParticleRef<C> particle_load(const Lattice& L, int p) {
+    ParticleRef<C> r;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (sizeof(C) == 8) {
+            double q = __ldg(L.pos + 3 * p + d);
+            r.ip[d] = (int)floor(q);
+            r.fr[d] = C(q - (double)r.ip[d]);
+            r.v[d] = C(__ldg(L.vel + 3 * p + d));
+            r.w[d] = C(__ldg(L.omg + 3 * p + d));
+        } else {
+            r.ip[d] = __ldg(L.ipos + 3 * p + d);
+            r.fr[d] = C(__ldg(L.fsnap + 9 * p + d));
+            r.v[d] = C(__ldg(L.fsnap + 9 * p + 3 + d));
+            r.w[d] = C(__ldg(L.fsnap + 9 * p + 6 + d));
+        }
+    }
+    return r;
+}
+
+template <typename C>
+__device__ __forceinline__ void particle_u0_of(const Lattice& L, const ParticleRef<C>& r, int x, int y, int z,
+                                               C (&U0)[3], C (&rel)[3]) {
+    int xs[3] = {x, y, z}, Ls[3] = {L.nx, L.ny, L.nz};
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        int dd = xs[d] - r.ip[d];
+        if (L.per[d]) {
+            if (2 * dd > Ls[d]) dd -= Ls[d];
+            else if (2 * dd < -Ls[d]) dd += Ls[d];
+        }
+        rel[d] = C(dd) - r.fr[d];
+    }
+    U0[0] = r.v[0] + (r.w[1] * rel[2] - r.w[2] * rel[1]);
+    U0[1] = r.v[1] + (r.w[2] * rel[0] - r.w[0] * rel[2]);
+    U0[2] = r.v[2] + (r.w[0] * rel[1] - r.w[1] * rel[0]);
+}
+
+template <typename C>
+__device__ __forceinline__ void particle_u0(const Lattice& L, int p, int x, int y, int z, C (&U0)[3], C (&rel)[3]) {
+    particle_u0_of<C>(L, particle_load<C>(L, p), x, y, z, U0, rel);
+}
+
 // Neumaier sum in the compute type (per-thread partials before the FP64 merge)
 template <typename C>
 struct CSum {
@@ -325,12 +385,48 @@ __device__ __forceinline__ void cp_async_8(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// ------------------------------------------------ per-device launch state
+// The > 48 KB dynamic shared-memory attribute is a property of a function on
+// one device, and the resident-block and SM counts that size the grids can
+// differ between devices: each is looked up once per (device, kernel), on
+// the device current at the launch.
+constexpr int MAX_DEV = 64;
+
+inline int current_device() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return dev >= 0 && dev < MAX_DEV ? dev : 0;
+}
+
+inline int device_sms() {
+    static int sms[MAX_DEV] = {0};
+    const int dev = current_device();
+    if (!sms[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        sms[dev] = n > 0 ? n : 1;
+    }
+    return sms[dev];
+}
+
+// Allow `smem` bytes of dynamic shared memory for kernel FN on the current
+// device (once) and return its resident blocks per SM at `threads` threads.
+template <auto FN>
+inline int kernel_setup(int threads, size_t smem) {
+    static int per_sm[MAX_DEV] = {0};
+    const int dev = current_device();
+    if (!per_sm[dev]) {
+        if (smem > 48 * 1024) cudaFuncSetAttribute(FN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, FN, threads, smem);
+        per_sm[dev] = n > 0 ? n : 1;
+    }
+    return per_sm[dev];
+}
+
 // kernel launchers (each returns the number of kernels it launched)
 int launch_init_fields(const Lattice& L, int prec, const double* stage, cudaStream_t st);
 int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st);
-size_t fused_tma_smem(int prec);
-int fused_tma_box_x(int prec);
-int launch_fluid_step_tma(const Lattice& L, int prec, const void* tmap, cudaStream_t st);
 int launch_shell_density(const Lattice& L, int prec, cudaStream_t st);
 int launch_density(const Lattice& L, int prec, cudaStream_t st);
 int launch_wall_psi(const Lattice& L, int prec, cudaStream_t st);

@@ -33,7 +33,7 @@ EXPORTS = ["lb_workspace_bytes", "lb_create", "lb_set_params", "lb_init_fields",
            "lb_state_bytes",
            "lb_get_state", "lb_set_state", "lb_adjoint_bytes", "lb_adjoint_seed", "lb_adjoint_step",
            "lb_adjoint_initial", "lb_adjoint_step_async", "lb_drag_gradient", "lb_record", "lb_totals_static",
-           "lb_launch_count", "lb_destroy", "lb_last_error"]
+           "lb_launch_count", "lb_fused_kernel", "lb_destroy", "lb_last_error"]
 
 
 class LbParams(C.Structure):
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
     lib.lb_totals_static.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_longlong, P, D, P, P]
     lib.lb_launch_count.argtypes = [P]
     lib.lb_launch_count.restype = C.c_longlong
+    lib.lb_fused_kernel.argtypes = [P]
     lib.lb_destroy.argtypes = [P]
     lib.lb_last_error.argtypes = [P]
     lib.lb_last_error.restype = C.c_char_p
@@ -320,6 +321,16 @@ def lb_launch_count(h) -> int:
     return int(load().lb_launch_count(h))
 
 
+LB_FUSED_MOMENTUM, LB_FUSED_TWO_PASS, LB_FUSED_PLAIN = 1, 2, 3
+FUSED_KERNEL_NAMES = {LB_FUSED_MOMENTUM: "k_fused_warp", LB_FUSED_TWO_PASS: "k_fused_async",
+                      LB_FUSED_PLAIN: "k_fused"}
+
+
+def lb_fused_kernel(h) -> int:
+    """Which fused lattice kernel lb_step launches now (LB_FUSED_*)."""
+    return _check(h, load().lb_fused_kernel(h), "lb_fused_kernel")
+
+
 def lb_destroy(h):
     return load().lb_destroy(h)
 
@@ -417,3 +428,7 @@ class LBLattice:
 
     def set_rounding(self, mode: int, seed: int = 0):
         lb_set_rounding(self.h, mode, seed)
+
+    def fused_kernel(self) -> str:
+        """Name of the fused lattice kernel lb_step launches now."""
+        return FUSED_KERNEL_NAMES[lb_fused_kernel(self.h)]

@@ -230,24 +230,23 @@ def test_reduced_precision_small_workload(prec, tol):
 
 
 @pytest.mark.parametrize("prec,tol,tol_u", [("fp64", 1e-12, 1e-12), ("fp32", 1e-5, 1e-5), ("fp16", 1e-3, 2e-3)])
-@pytest.mark.parametrize("tma", ["1", "0"])
-def test_sheared_walls_with_particles(prec, tol, tol_u, tma, monkeypatch):
+@pytest.mark.parametrize("nx", [32, 36])
+def test_sheared_walls_with_particles(prec, tol, tol_u, nx):
     """Walls at z = -1/2, nz - 1/2 moving at -/+0.05 (the confined shear
     workload's boundary), four particles, 100 steps: velocities are O(0.05)
-    here and are compared relative to themselves.  Both fused-kernel variants
-    (plain loads by default, TMA-staged tiles with LBGB_FUSED_TMA=1) are checked.
-    FP16 deviation storage
-    rounds each population to 11 significant bits of f_i - w_i rho0; next to
-    the sheared walls (|u| = 0.05) this leaves a velocity error of about 1.1e-3
-    of max |u| after 100 steps (5e-5 of the lattice speed), so the FP16
-    velocity bound here is 2e-3 relative to max |u|."""
-    monkeypatch.setenv("LBGB_FUSED_TMA", tma)
-    shape = (32, 21, 23)
+    here and are compared relative to themselves.  At tau = 1 the momentum
+    kernel runs; nx = 36 leaves a ragged last tile of 4 columns.  FP16
+    deviation storage rounds each population to 11 significant bits of
+    f_i - w_i rho0; next to the sheared walls (|u| = 0.05) this leaves a
+    velocity error of about 1.1e-3 of max |u| after 100 steps (5e-5 of the
+    lattice speed), so the FP16 velocity bound here is 2e-3 relative to max |u|."""
+    shape = (nx, 21, 23)
     w = workload("shear512")
     params = dict(w.params, side_wall_d=6.5)
     col = dict(pos=[[8.2, 5.3, 7.7], [22.6, 14.1, 11.4], [9.9, 16.2, 15.8], [25.1, 4.4, 16.0]],
                radius=5.5, mass=700.0)
     g, o = run_both(shape, params, 100, prec, col)
+    assert g.fused_kernel() == "k_fused_warp"
     ga, gb, gu = g.get_fields()
     ra, rb, ru = o.get_fields()
     assert np.abs(ru).max() > 0.02
@@ -255,6 +254,23 @@ def test_sheared_walls_with_particles(prec, tol, tol_u, tma, monkeypatch):
     assert rel(ga, ra) < tol and rel(gb, rb) < tol
     assert rel(gu, ru) < tol_u, rel(gu, ru)
     compare_colloids(g, o, tol)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_momentum_kernel_runs_the_particle_workloads(prec):
+    """The tau = 1 particle workloads (bijel, Pickering, confined shear) take
+    the momentum kernel after the full density pass; other tau the two-pass one."""
+    w = workload("small_fp64")
+    g = _lattice(w.shape, prec, w.n_colloids)
+    g.set_params(**w.params)
+    a, b = w.densities()
+    g.init_fields(a, b)
+    assert g.fused_kernel() == "k_fused"
+    c = w.colloids()
+    g.add_colloids(c["pos"], c["radius"], c["mass"])
+    assert g.fused_kernel() == "k_fused_warp"
+    g.set_params(**dict(w.params, tau=(0.8, 1.2)))
+    assert g.fused_kernel() == "k_fused_async"
 
 
 def test_mass_conservation_gpu_fp64():

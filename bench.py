@@ -15,10 +15,12 @@ plain FP64 CPU oracle on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -154,15 +156,30 @@ def dist_setup(args):
     return world, rank, local
 
 
-def cpu_baseline(name, target_seconds=20.0):
-    """The FP64 oracle (as it stands, one host thread) on a bounded sample of
-    the workload: a 128x128x64 sub-box with the same physics and particle
-    volume fraction, stepped until about target_seconds have passed."""
-    from oracle import Oracle
-    from paper_2004_04080_gb300.workloads import workload
+def cpu_model():
+    """The host CPU as the OS names it."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
 
-    sub = (128, 128, 64)
-    w = workload(name, scale=sub)
+
+def oracle_mlups(w, target_seconds, max_steps=50):
+    """Steps the FP64 oracle on workload ``w`` for about target_seconds after
+    one untimed step; returns (MLUPS, steps, seconds)."""
+    from oracle import Oracle
+
     a, b = w.densities()
     c = w.colloids()
     o = Oracle(*w.shape, max(w.n_colloids, 1))
@@ -170,17 +187,63 @@ def cpu_baseline(name, target_seconds=20.0):
     o.init_fields(a, b)
     if c is not None:
         o.add_colloids(c["pos"], c["radius"], c["mass"])
+    o.step(1)
     steps, t0 = 0, time.perf_counter()
     while True:
         o.step(1)
         steps += 1
         el = time.perf_counter() - t0
-        if el > target_seconds or steps >= 50:
+        if el > target_seconds or steps >= max_steps:
             break
-    mlups = w.n_sites * steps / el / 1e6
-    return {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%s sub-box %dx%dx%d, %d particles, %d steps, %.1f s" % (
-                name, *sub, w.n_colloids, steps, el)}
+    return w.n_sites * steps / el / 1e6, steps, el
+
+
+# The paper's two-component Shan-Chen throughput per core without particles
+# (1024^3, G = 0.65, 128 cores of 2x Xeon Gold 6148 nodes; Sec. 5.1 table of
+# the two-component runs, case 0).
+PAPER_MLUPS_PER_CORE_2COMP = 1.41
+
+
+def cpu_baseline(name, target_seconds=20.0, extras=True):
+    """The FP64 oracle (as it stands) on the host cores, on a bounded sample
+    of the workload: a 128x128x64 sub-box with the same physics and particle
+    volume fraction.  ``value`` uses every core (OpenMP over the site loops;
+    the particle-link sums stay single-threaded).  With ``extras``: the same
+    sample on one thread, and the 128^3 two-component mixture without
+    particles (G = 0.65) on all cores and on one, per core beside the
+    paper's figure for that case."""
+    from oracle import set_threads
+    from paper_2004_04080_gb300.workloads import workload
+
+    sub = (128, 128, 64)
+    w = workload(name, scale=sub)
+    cores = set_threads(0)
+    mlups, steps, el = oracle_mlups(w, target_seconds)
+    out = {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+           "sample": "%s sub-box %dx%dx%d, %d particles, %d steps, %.1f s, FP64, %d OpenMP threads" % (
+               name, *sub, w.n_colloids, steps, el, cores),
+           "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+    if extras:
+        try:
+            set_threads(1)
+            m1, s1, e1 = oracle_mlups(w, target_seconds / 3)
+            out["one_thread"] = {"value": round(m1, 3), "steps": s1, "seconds": round(e1, 1)}
+            # the paper's two-component case: G = 0.65 with density 1 per component
+            w0 = dataclasses.replace(workload("bijel_demix"), n_colloids=0)
+            two = {}
+            for th in (0, 1):
+                n = set_threads(th)
+                m, s_, e_ = oracle_mlups(w0, target_seconds / 4, max_steps=20)
+                two["all_cores" if th == 0 else "one_thread"] = {
+                    "threads": n, "mlups": round(m, 3), "mlups_per_core": round(m / n, 3),
+                    "steps": s_, "seconds": round(e_, 1)}
+            two["case"] = "128^3 two-component Shan-Chen, G = 0.65, rho = 1 + 1, tau = 1, no particles, FP64"
+            two["paper_mlups_per_core"] = PAPER_MLUPS_PER_CORE_2COMP
+            two["paper_case"] = "1024^3 case 0, 128 cores (2x Xeon Gold 6148 per node), FP64 Fortran"
+            out["two_component_no_particles"] = two
+        finally:
+            set_threads(0)
+    return out
 
 
 def workload_desc(name, w):
@@ -195,13 +258,14 @@ def run_reference(args, world, rank):
 
     if rank != 0:
         return 0
-    base = cpu_baseline(args.workload, target_seconds=max(5.0, min(60.0, 2.0 * (args.steps + args.warmup))))
+    base = cpu_baseline(args.workload, target_seconds=max(5.0, min(60.0, 2.0 * (args.steps + args.warmup))),
+                        extras=False)
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "MLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_desc(args.workload, workload(args.workload, tuple(args.shape) if args.shape else None)),
-                       "prec": "fp64 oracle", "parallelism": "single host thread"},
+                       "prec": "fp64 oracle", "parallelism": "%d host threads (OpenMP)" % base["cores"]},
             "cpu_baseline": base,
             "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -408,6 +472,8 @@ def main():
                            "kernel": L2.fused_kernel(),
                            "kernel_frac": round(alg_bytes(prec) * N / (kk / 1e3) / 1e9 / peak, 4),
                            "stated_rel_error_vs_fp64_oracle": STATED_ERROR[prec]}
+            if prec == "fp16":
+                forms[prec]["rounding"] = "stochastic (cvt.rs.f16x2.f32, the FP16 default)"
             del L2
             torch.cuda.empty_cache()
         forms[args.prec] = {"mlups": round(value, 1), "stated_rel_error_vs_fp64_oracle": STATED_ERROR[args.prec]}

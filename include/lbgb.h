@@ -157,16 +157,20 @@ int lb_get_owner(lb_ctx *ctx, int *out);
 enum { LB_KERNEL_FUSED = 0, LB_KERNEL_DENSITY = 1 };
 
 /* Rounding of the FP16 deviation storage (the precision forms; the paper
- * stores FP64).  LB_ROUND_NEAREST (the default) stores half(f_i - w_i rho0^k)
- * rounded to nearest.  LB_ROUND_STOCHASTIC rounds every population stored by
- * the time step up or down with probability given by the value's position
- * between the two neighbouring half values (bits from a counter-based hash of
- * site, step and `seed`), so that the expected stored value is the FP32 one:
- * a population that stays the same from step to step is then not rounded
- * the same way every step.  The sequence of bits is fixed by `seed` and the
- * number of steps since this call.  No effect on LB_FP32 / LB_FP64 contexts.
- * The adjoint functions return LB_ERR_STATE while stochastic rounding is on
- * (their forward recomputation would not reproduce the recorded steps).
+ * stores FP64).  LB_ROUND_STOCHASTIC (the default of an LB_FP16 context)
+ * rounds every population stored by the time step up or down with
+ * probability given by the value's position between the two neighbouring half
+ * values (the hardware's stochastic-rounding conversion, with bits from a
+ * counter-based hash of site, step and `seed`), so that the expected stored
+ * value is the FP32 one: a population that stays the same from step to step
+ * is then not rounded the same way every step (rounding to nearest makes the
+ * error of such a population a bias that grows with the number of steps).
+ * LB_ROUND_NEAREST stores half(f_i - w_i rho0^k) rounded to nearest.  The
+ * sequence of bits is fixed by `seed` and the number of steps since this call
+ * or since lb_init_fields (the default seed is a fixed constant).  No effect
+ * on LB_FP32 / LB_FP64 contexts.  The adjoint functions return LB_ERR_STATE
+ * while stochastic rounding is on (their forward recomputation would not
+ * reproduce the recorded steps): an FP16 adjoint needs LB_ROUND_NEAREST.
  * LB_ERR_ARG for another mode. */
 enum { LB_ROUND_NEAREST = 0, LB_ROUND_STOCHASTIC = 1 };
 int lb_set_rounding(lb_ctx *ctx, int mode, unsigned long long seed);
@@ -250,8 +254,10 @@ int lb_adjoint_initial(lb_ctx *ctx, const void *d_adj, double *d_grad);
  *   d_out:  device array of 5 doubles: mass of A and B, sum_k j^k (x, y, z).
  * The scratch is a static device array of per-plane partials (320 KiB on each
  * device that loads the library, kept until exit): nz must be <= 4096,
- * otherwise LB_ERR_ARG.  The first call on a device looks up that array's
- * address and should come before any stream capture.  Calls share the array,
+ * otherwise LB_ERR_ARG.  The first call in each CUDA context looks up that
+ * array's address and should come before any stream capture; a device reset
+ * replaces the context, and the next call then looks it up again.  Calls share
+ * the array,
  * so calls that overlap on the GPU race; calls ordered on one stream do not.
  * Runs asynchronously on cuda_stream; returns LB_ERR_ARG / LB_ERR_CUDA on bad
  * arguments or a failed launch. */

@@ -24,7 +24,11 @@
  *   8. streaming (Eq. 3)
  * Every loop is a plain loop over lattice sites or particles; nothing is
  * fused, blocked or reordered beyond what the equations state.  Build with
- * -O2 -ffp-contract=off so that no multiply-add is contracted.
+ * -O2 -ffp-contract=off so that no multiply-add is contracted.  Loops whose
+ * iterations each write only their own site's values are shared out over
+ * threads with OpenMP (-fopenmp); a site's arithmetic does not depend on the
+ * thread count, so every thread count gives the same bits.  Sums into
+ * per-particle totals stay single-threaded, in site order.
  *
  * Readings taken where the paper is silent or garbled (each is also used by
  * the CUDA library, which is written independently):
@@ -73,6 +77,9 @@
  *    QUAD_FORCEINT concern, Sec. 3.1).
  */
 #define _DEFAULT_SOURCE
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -358,7 +365,8 @@ int orc_init_fields(orc_t *o, const double *rhoA, const double *rhoB, const doub
 static void moments(orc_t *o)
 {
     long s, N = o->N;
-    int k, i;
+    int k, i, bad = 0;
+#pragma omp parallel for private(k, i) reduction(| : bad) schedule(static)
     for (s = 0; s < N; s++) {
         for (k = 0; k < 2; k++) {
             double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
@@ -371,7 +379,7 @@ static void moments(orc_t *o)
                     jz += fi * CZ[i];
                 }
                 if (!isfinite(r) || r < 0.0 || !isfinite(jx) || !isfinite(jy) || !isfinite(jz))
-                    o->err = ORC_ERR_NONFINITE;
+                    bad = 1;
             }
             o->rho[k][s] = r;
             o->jm[k][s] = jx;
@@ -379,6 +387,8 @@ static void moments(orc_t *o)
             o->jm[k][2 * N + s] = jz;
         }
     }
+    if (bad)
+        o->err = ORC_ERR_NONFINITE;
 }
 
 /* Eq. 14: u = sum_k omega^k j^k / sum_k omega^k rho^k, omega^k = 1/tau_k */
@@ -625,6 +635,7 @@ static void lb_forces(orc_t *o, int store_particle_terms)
     int k, i, d, x, y, z;
     nsum *acc = (nsum *)zalloc(sizeof(nsum) * 6 * (size_t)(o->nc ? o->nc : 1));
     /* Eq. 20 on every solid node that has a fluid neighbour */
+#pragma omp parallel for private(k, i, x, y, z) schedule(static)
     for (s = 0; s < N; s++) {
         o->psi[0][s] = 0.0;
         o->psi[1][s] = 0.0;
@@ -671,6 +682,7 @@ static void lb_forces(orc_t *o, int store_particle_terms)
                 }
     }
     /* Eq. 11 on fluid nodes (plus the body force rho^k g) */
+#pragma omp parallel for private(k, i, d, x, y, z) schedule(static)
     for (s = 0; s < N; s++) {
         for (k = 0; k < 2; k++)
             for (d = 0; d < 3; d++)
@@ -740,6 +752,7 @@ static void collide(orc_t *o)
     long s, N = o->N;
     int k, i;
     double nu0 = CS2 * (o->P.tau[0] - 0.5), nu1 = CS2 * (o->P.tau[1] - 0.5);
+#pragma omp parallel for private(k, i) schedule(static)
     for (s = 0; s < N; s++) {
         double u[3], rt, inv_nu, nubar, om;
         if (o->owner[s] >= 0)
@@ -773,6 +786,9 @@ static void bounce_and_stream(orc_t *o)
     long s, N = o->N;
     int k, i, d, x, y, z, p;
     nsum *acc = (nsum *)zalloc(sizeof(nsum) * 6 * (size_t)(o->nc ? o->nc : 1));
+    /* every (link, target) is written by one source site; the particle-link
+     * sums run in site order, so with particles the loop is single-threaded */
+#pragma omp parallel for private(k, i, d, x, y, z, p) schedule(static) if (o->nc == 0)
     for (s = 0; s < N; s++) {
         if (o->owner[s] >= 0)
             continue;
@@ -1111,6 +1127,16 @@ int orc_set_populations(orc_t *o, int k, const double *in)
     return ORC_OK;
 }
 
+/* psi^k of the last force evaluation, [N]: the virtual density (Eq. 20) on
+ * particle frontier nodes, 0 elsewhere */
+int orc_get_psi(orc_t *o, int k, double *out)
+{
+    if (!o || !out || k < 0 || k > 1)
+        return ORC_ERR_ARG;
+    memcpy(out, o->psi[k], sizeof(double) * o->N);
+    return ORC_OK;
+}
+
 /* node map: -1 fluid, else the owning particle */
 int orc_get_owner(orc_t *o, int *out)
 {
@@ -1135,4 +1161,19 @@ int orc_set_colloid_state(orc_t *o, int p, const double *pos, const double *vel,
         for (d = 0; d < 4; d++)
             o->quat[4 * p + d] = quat[d];
     return ORC_OK;
+}
+
+/* OpenMP threads used by the site loops (n <= 0: all available); returns the
+ * count now in effect, 1 in a build without OpenMP. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n <= 0)
+        n = omp_get_num_procs();
+    omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

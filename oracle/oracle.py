@@ -1,7 +1,8 @@
 """ctypes binding of the plain C FP64 oracle (``lbgb_oracle.c``).
 
 Test infrastructure only.  The oracle shares no code with the CUDA library:
-it is compiled from its own C file with gcc (-O2 -ffp-contract=off), it keeps
+it is compiled from its own C file with gcc (-O2 -ffp-contract=off -fopenmp;
+every thread count gives the same bits), it keeps
 its own table of parameter defaults (DEFAULTS below), and only the seeded
 input generators of ``paper_2004_04080_gb300.workloads`` (initial densities,
 particle placements, named parameter sets) feed both.
@@ -53,7 +54,7 @@ def build_oracle(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-fPIC", "-shared",
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-fopenmp", "-fPIC", "-shared",
                "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
@@ -83,11 +84,14 @@ def _load():
         lib.orc_get_populations.argtypes = [P, C.c_int, D]
         lib.orc_set_populations.argtypes = [P, C.c_int, D]
         lib.orc_get_owner.argtypes = [P, I]
+        lib.orc_get_psi.argtypes = [P, C.c_int, D]
         lib.orc_set_colloid_state.argtypes = [P, C.c_int, D, D, D, D]
         lib.orc_feq.argtypes = [C.c_double, D, D]
         lib.orc_lattice.argtypes = [I, I, I, D, I]
         lib.orc_pair_force.argtypes = [C.POINTER(OrcParams), D, C.c_double, C.c_double, D, D, D]
         lib.orc_integrate_one.argtypes = [D, D, D, D, C.c_double, C.c_double, D, D, C.c_int, I]
+        lib.orc_set_threads.argtypes = [C.c_int]
+        lib.orc_set_threads.restype = C.c_int
         _lib = lib
         return lib
 
@@ -233,6 +237,13 @@ class Oracle:
         f = _f64(f).reshape(19, self.N)
         self._chk(self.lib.orc_set_populations(self.h, k, _dp(f)), "orc_set_populations")
 
+    def psi(self, k: int):
+        """psi^k of the last force evaluation: virtual densities (Eq. 20)
+        on particle frontier nodes, 0 elsewhere."""
+        out = np.empty(self.N)
+        self._chk(self.lib.orc_get_psi(self.h, k, _dp(out)), "orc_get_psi")
+        return out
+
     def owner(self):
         out = np.empty(self.N, dtype=np.int32)
         self._chk(self.lib.orc_get_owner(self.h, out.ctypes.data_as(C.POINTER(C.c_int))), "orc_get_owner")
@@ -241,6 +252,11 @@ class Oracle:
     def set_colloid_state(self, p, pos=None, vel=None, omega=None, quat=None):
         args = [None if a is None else _f64(a) for a in (pos, vel, omega, quat)]
         self._chk(self.lib.orc_set_colloid_state(self.h, p, *[_dp(a) for a in args]), "orc_set_colloid_state")
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's site loops (0: all cores); returns the count."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def lattice():

@@ -44,6 +44,7 @@ class AdjointRunner:
         self.scratch = torch.empty(sb, dtype=torch.uint8, device=dev)
         self.stack = torch.empty((self.K, self.state_bytes), dtype=torch.uint8, device=dev)
         self.checkpoints = {}
+        self.generation = 0  # number of forward runs so far
 
     def _state(self):
         t = self.torch.empty(self.state_bytes, dtype=self.torch.uint8, device=self.lat.device)
@@ -54,6 +55,7 @@ class AdjointRunner:
         """Run T steps; returns (J_drag, A).  ``colloids``: pos, radius (the
         particles are added immobile)."""
         lat, torch = self.lat, self.torch
+        self.generation += 1
         lat.set_params(**params)
         lat.init_fields(rhoA0, rhoB0)
         self.n = 0
@@ -125,14 +127,22 @@ def _objective_function():
             t = [float(v) for v in theta.detach().cpu().tolist()]
             params = dict(base_params, tau=(t[0], t[1]), G=t[2], zeta=(t[3], t[4]))
             J, A = runner.forward(params, rhoA0.detach().cpu().numpy(), rhoB0.detach().cpu().numpy(), colloids)
-            ctx.runner = runner
-            return torch.tensor([J, A], dtype=torch.float64)
+            # the runner holds one forward's checkpoints: remember which one
+            ctx.runner, ctx.generation = runner, runner.generation
+            ctx.like = [(x.device, x.dtype) for x in (theta, rhoA0, rhoB0)]
+            return torch.tensor([J, A], dtype=torch.float64, device=theta.device)
 
         @staticmethod
         def backward(ctx, grad_out):
-            grads, grho = ctx.runner.backward(float(grad_out[0]), float(grad_out[1]))
-            return (torch.from_numpy(grads), torch.from_numpy(grho[0].copy()),
-                    torch.from_numpy(grho[1].copy()), None, None, None)
+            if ctx.runner.generation != ctx.generation:
+                raise RuntimeError("LBObjective: the AdjointRunner ran another forward since this graph was "
+                                   "built, so its checkpoints belong to other inputs; use one runner per "
+                                   "graph or call backward before the next forward")
+            g = grad_out.detach().cpu()
+            grads, grho = ctx.runner.backward(float(g[0]), float(g[1]))
+            out = [torch.from_numpy(np.ascontiguousarray(x)) for x in (grads, grho[0], grho[1])]
+            out = [x.to(device=d, dtype=t) for x, (d, t) in zip(out, ctx.like)]
+            return (*out, None, None, None)
 
     return LBObjective
 

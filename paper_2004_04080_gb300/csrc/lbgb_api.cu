@@ -9,11 +9,39 @@
 #include <cuda.h>
 #include <stdlib.h>
 
+#include <mutex>
 #include <new>
 
 #include "lbgb_internal.cuh"
 
 using namespace lbgb;
+
+// The driver's context queries, found through the runtime so that the library
+// links against the runtime only.
+unsigned long long lbgb::current_context_id() {
+    typedef CUresult (*GetCurrent)(CUcontext*);
+    typedef CUresult (*GetId)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (GetCurrent)p;
+        p = nullptr;
+        q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (GetId)p;
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c) return 0;
+    if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 struct lb_ctx {
     Lattice L;
@@ -58,6 +86,9 @@ size_t compute_bytes(int prec) { return prec == LB_FP64 ? 8 : 4; }
 size_t state_bytes(const lb_ctx* ctx) { return (size_t)2 * Q * ctx->L.pstride * storage_bytes(ctx->prec); }
 
 const int DOUBLES_PER_PARTICLE = 57;  // pos..Ttot, see carve()
+// seed of the default stochastic rounding of FP16 contexts (any constant: the
+// sequence of rounding bits is fixed by it and the steps since lb_init_fields)
+const unsigned long long SR_DEFAULT_SEED = 0x2545F4914F6CDD1Dull;
 const int RED_BLOCKS = 1024;
 const int PROF_MAX = 16384;
 
@@ -217,6 +248,10 @@ int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_worksp
     ctx->cells = ctx->ws + l.cells;
     ctx->cells_bytes = l.cells_bytes;
     L.nc = 0;
+    // FP16 storage rounds stochastically by default (lb_set_rounding)
+    L.sr = prec == LB_FP16;
+    ctx->sr_seed = SR_DEFAULT_SEED;
+    ctx->sr_step = 0;
     // empty node map, no particles, no error flags
     cudaError_t e = cudaMemsetAsync(ctx->ws + l.mask, 0, (size_t)L.N, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.owner, 0xff, (size_t)L.N * 4, ctx->stream);
@@ -290,6 +325,7 @@ int lb_init_fields(lb_ctx* ctx, const double* rhoA, const double* rhoB, const do
     else CK(cudaMemsetAsync(st + 2 * L.N, 0, 3 * nb, ctx->stream), "zero u");
     L.nc = 0;
     ctx->all_fixed = 1;
+    ctx->sr_step = 0;  // a new state starts the rounding sequence afresh
     int n = launch_clear_map(L, ctx->stream);
     n += launch_init_fields(L, ctx->prec, st, ctx->stream);
     int rc = launched(ctx, n, "init kernels");

@@ -591,14 +591,7 @@ __global__ void __launch_bounds__(VTX* VTY) k_virtual(Lattice L, int store_terms
         if (!(den > C(0))) continue;
         const int z = z0 + q - 1;
         const long long s = nxy * z + (x0 + cx0) + (long long)L.nx * (y0 + cy0);
-        const C pa = zA * num[0] / den;
-        const C pb = zB * num[1] / den;
-        psi[s] = pa;
-        psi[L.N + s] = pb;
-        if (!store_terms) continue;
         C fs[3], d[3], tq[3];
-#pragma unroll
-        for (int c = 0; c < 3; c++) fs[c] = -G * pa * sB[c] + -G * pb * sA[c];
         // x_s - r_p (minimum image) from the integer cell and offset of r_p
         const int xs[3] = {x0 + cx0, y0 + cy0, z}, Ls[3] = {L.nx, L.ny, L.nz};
 #pragma unroll

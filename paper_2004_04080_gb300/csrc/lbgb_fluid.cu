@@ -430,12 +430,17 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
     // (2j-1, 2j): plane 2j adds ps; sites < 2^31 and ps < 2^31 keep them in range
     char* fnb = (char*)L.f_nxt;
     // FP16 with stochastic rounding (SR, a separate instantiation): the
-    // rounding bits of this site
+    // rounding bits of this site; both components of a link are stored by
+    // one call
     unsigned rs = 0;
     if constexpr (SR) rs = sr_start(s, L.sr_key);
-    auto put = [&](S* q, C val, C shift) {
-        if constexpr (SR) st_pop_sr(q, val, shift, sr_next(rs));
-        else st_pop(q, val, shift);
+    auto put2 = [&](S* qa, S* qb, C va, C vb, C sa, C sb) {
+        if constexpr (SR) {
+            st_pop2_sr(qa, qb, va, vb, sa, sb, sr_next2(rs));
+        } else {
+            st_pop(qa, va, sa);
+            st_pop(qb, vb, sb);
+        }
     };
 #pragma unroll
     for (int i = 0; i < Q; i++) {
@@ -454,10 +459,10 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
             }
         }
         if (i == 0) {
-#pragma unroll
-            for (int k = 0; k < 2; k++)
-                put((S*)(fnb + (unsigned long long)ps * (unsigned)(k * Q * (int)sizeof(S))) + s,
-                    solid ? wgt<C>(0) * prm<C>(L.P.rho0[k], L.PF.rho0[k]) : fs[k], pop_shift<S, C>(L, k, 0));
+            put2((S*)fnb + s, (S*)(fnb + (unsigned long long)ps * (unsigned)(Q * (int)sizeof(S))) + s,
+                 solid ? wgt<C>(0) * prm<C>(L.P.rho0[0], L.PF.rho0[0]) : fs[0],
+                 solid ? wgt<C>(0) * prm<C>(L.P.rho0[1], L.PF.rho0[1]) : fs[1], pop_shift<S, C>(L, 0, 0),
+                 pop_shift<S, C>(L, 1, 0));
             continue;
         }
         const int lo = (i & 1) ? i : i - 1;  // first plane of the pair
@@ -471,14 +476,15 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
         C cw = C(cx(i)) * V[zs][0] + C(cy(i)) * V[zs][1] + C(cz(i)) * V[zs][2];
         cw = b ? C(-2) * cw : C(0);  // f_ibar = f*_i - 6 w_i rho c_i.u_w (Eq. 17)
         const int c = i <= 6 ? 1 : 2;
-        C fl = 0;
+        C fb[2];
 #pragma unroll
-        for (int k = 0; k < 2; k++) {
-            S* base = (S*)(fnb + (unsigned long long)ps * (unsigned)((k * Q + lo) * (int)sizeof(S)));
-            const C fb = fs[k] + B[k][c] * cw;
-            put(base + off, solid ? wgt<C>(i) * prm<C>(L.P.rho0[k], L.PF.rho0[k]) : fb, pop_shift<S, C>(L, k, i));
-            fl += fs[k] + fb;
-        }
+        for (int k = 0; k < 2; k++) fb[k] = fs[k] + B[k][c] * cw;
+        put2((S*)(fnb + (unsigned long long)ps * (unsigned)(lo * (int)sizeof(S))) + off,
+             (S*)(fnb + (unsigned long long)ps * (unsigned)((Q + lo) * (int)sizeof(S))) + off,
+             solid ? wgt<C>(i) * prm<C>(L.P.rho0[0], L.PF.rho0[0]) : fb[0],
+             solid ? wgt<C>(i) * prm<C>(L.P.rho0[1], L.PF.rho0[1]) : fb[1], pop_shift<S, C>(L, 0, i),
+             pop_shift<S, C>(L, 1, i));
+        C fl = fs[0] + fb[0] + fs[1] + fb[1];
         fl = (pm >> i) & 1u ? fl : C(0);
         if (cx(i)) Fl[0] += C(cx(i)) * fl;
         if (cy(i)) Fl[1] += C(cy(i)) * fl;
@@ -501,20 +507,20 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
             C U[3], r2[3];
             particle_u0<C>(L, nd, x, y, z, U, r2);
             C cw = C(cx(i)) * U[0] + C(cy(i)) * U[1] + C(cz(i)) * U[2];
-            C fl = 0;
+            C fsv[2], fbv[2];
             for (int k = 0; k < 2; k++) {
-                C fs;
                 if (UNIT)
-                    fs = feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
+                    fsv[k] = feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
                 else
-                    fs = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
-                                     feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
-                         feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
-                S* dst = (S*)(fnb + (unsigned long long)ps * (unsigned)((k * Q + opp(i)) * (int)sizeof(S))) + s;
-                const C fb = fs - C(6) * wgt<C>(i) * m.rho[k] * cw;
-                st_pop(dst, fb, pop_shift<S, C>(L, k, i));
-                fl += fs + fb;
+                    fsv[k] = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
+                                         feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
+                             feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
+                fbv[k] = fsv[k] - C(6) * wgt<C>(i) * m.rho[k] * cw;
             }
+            put2((S*)(fnb + (unsigned long long)ps * (unsigned)(opp(i) * (int)sizeof(S))) + s,
+                 (S*)(fnb + (unsigned long long)ps * (unsigned)((Q + opp(i)) * (int)sizeof(S))) + s, fbv[0], fbv[1],
+                 pop_shift<S, C>(L, 0, i), pop_shift<S, C>(L, 1, i));
+            const C fl = fsv[0] + fbv[0] + fsv[1] + fbv[1];
             // the link force into the second particle, added directly
             const C F2[3] = {C(cx(i)) * fl, C(cy(i)) * fl, C(cz(i)) * fl};
             const C T2[3] = {r2[1] * F2[2] - r2[2] * F2[1], r2[2] * F2[0] - r2[0] * F2[2],

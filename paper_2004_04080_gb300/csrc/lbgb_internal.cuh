@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/lbgb.h"
 
 namespace lbgb {
@@ -54,20 +56,18 @@ __device__ __forceinline__ void st_pop(__half* p, float v, float shift) {
     *p = __float2half_rn(v - shift);
 }
 
-// Stochastic rounding of the FP16 deviation store.  The rounding bits of a
-// site start from Appleby's MurmurHash3 32-bit finaliser of (site, step key)
-// and advance by the linear congruential step of Numerical Recipes
-// (a = 1664525, c = 1013904223) per store, whose top 13 bits are used (bits
-// drawn for several stores from one product are correlated across the
-// populations of a site, which multiplies the noise of its density; the
-// serial step keeps them independent).  An FP32 value in the half-normal
-// range keeps 13 bits below a half's 10-bit mantissa: adding 13 random bits
-// to the magnitude and truncating rounds it up with probability equal to its
-// position between the two neighbouring half values, so the expected stored
-// value is the FP32 one.  Below that range (|d| < 2^-14, subnormal halves of
-// spacing 2^-24) the value rounds to nearest: truncation there would pull
-// every small deviation towards the shift (the seed noise of a mixture near
-// rho0, for one), and the selection keeps the store free of branches.
+// Stochastic rounding of the FP16 deviation stores.  The two components of
+// a link are converted together by the hardware's stochastic-rounding
+// conversion to a pair of halves (cvt.rs.f16x2.f32: component A in the upper
+// half, rounded with random bits 31..16, component B in the lower half with
+// bits 15..0; each value rounds up with probability equal to its position
+// between the two neighbouring half values, so the expected stored value is
+// the FP32 one; subnormal halves included).  The random bits of a site start
+// from Appleby's MurmurHash3 32-bit finaliser of (site, step key) and advance
+// by the linear congruential step of Numerical Recipes (a = 1664525,
+// c = 1013904223); each component takes the upper 16 bits of its own step
+// (the low bits of such a generator are weak, and bits for several stores
+// sliced from one product are correlated across a site's populations).
 __device__ __forceinline__ unsigned sr_start(unsigned site, unsigned key) {
     unsigned h = site * 0x9E3779B1u ^ key;
     h ^= h >> 16;
@@ -77,16 +77,19 @@ __device__ __forceinline__ unsigned sr_start(unsigned site, unsigned key) {
     h ^= h >> 16;
     return h;
 }
-__device__ __forceinline__ unsigned sr_next(unsigned& st) {
+// 32 random bits for one pair of stores: the upper halves of two steps
+__device__ __forceinline__ unsigned sr_next2(unsigned& st) {
     st = st * 1664525u + 1013904223u;
-    return st >> 19;
+    const unsigned hi = st & 0xffff0000u;
+    st = st * 1664525u + 1013904223u;
+    return hi | (st >> 16);
 }
-__device__ __forceinline__ void st_pop_sr(__half* p, float v, float shift, unsigned bits13) {
-    const float d = v - shift;
-    const unsigned u = __float_as_uint(d);
-    const __half hs = __float2half_rz(__uint_as_float((u + bits13) & ~0x1fffu));
-    const __half hn = __float2half_rn(d);
-    *p = (u & 0x7fffffffu) >= 0x38800000u ? hs : hn;
+__device__ __forceinline__ void st_pop2_sr(__half* pa, __half* pb, float va, float vb, float sa, float sb,
+                                           unsigned bits) {
+    unsigned d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(va - sa), "f"(vb - sb), "r"(bits));
+    *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(d >> 16);
+    *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(d & 0xffffu);
 }
 
 // ------------------------------------------------------------- context
@@ -386,10 +389,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // ------------------------------------------------ per-device launch state
-// The > 48 KB dynamic shared-memory attribute is a property of a function on
-// one device, and the resident-block and SM counts that size the grids can
-// differ between devices: each is looked up once per (device, kernel), on
-// the device current at the launch.
+// The > 48 KB dynamic shared-memory attribute is a property of a function in
+// one CUDA context, and the resident-block and SM counts that size the grids
+// can differ between devices: each is looked up once per (context, kernel),
+// in the context current at the launch.  A context that replaces another on
+// the same device (after a device reset) has a new id, so nothing set up in
+// the old one is reused.
 constexpr int MAX_DEV = 64;
 
 inline int current_device() {
@@ -398,30 +403,38 @@ inline int current_device() {
     return dev >= 0 && dev < MAX_DEV ? dev : 0;
 }
 
+// Unique id of the calling thread's current CUDA context; 0 when no context
+// is current or the driver cannot say (callers then redo their set-up).
+unsigned long long current_context_id();
+
 inline int device_sms() {
-    static int sms[MAX_DEV] = {0};
+    static std::atomic<int> sms[MAX_DEV];
     const int dev = current_device();
-    if (!sms[dev]) {
-        int n = 0;
+    int n = sms[dev].load(std::memory_order_relaxed);
+    if (!n) {
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        sms[dev] = n > 0 ? n : 1;
+        n = n > 0 ? n : 1;
+        sms[dev].store(n, std::memory_order_relaxed);
     }
-    return sms[dev];
+    return n;
 }
 
-// Allow `smem` bytes of dynamic shared memory for kernel FN on the current
-// device (once) and return its resident blocks per SM at `threads` threads.
+// Allow `smem` bytes of dynamic shared memory for kernel FN in the current
+// context (once) and return its resident blocks per SM at `threads` threads.
 template <auto FN>
 inline int kernel_setup(int threads, size_t smem) {
-    static int per_sm[MAX_DEV] = {0};
+    static std::atomic<unsigned long long> ctx[MAX_DEV];
+    static std::atomic<int> per_sm[MAX_DEV];
     const int dev = current_device();
-    if (!per_sm[dev]) {
-        if (smem > 48 * 1024) cudaFuncSetAttribute(FN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, FN, threads, smem);
-        per_sm[dev] = n > 0 ? n : 1;
-    }
-    return per_sm[dev];
+    const unsigned long long id = current_context_id();
+    if (id && ctx[dev].load(std::memory_order_acquire) == id) return per_sm[dev].load(std::memory_order_relaxed);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(FN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, FN, threads, smem);
+    n = n > 0 ? n : 1;
+    per_sm[dev].store(n, std::memory_order_relaxed);
+    ctx[dev].store(id, std::memory_order_release);
+    return n;
 }
 
 // kernel launchers (each returns the number of kernels it launched)

@@ -12,9 +12,10 @@
 //
 // The scratch is g_plane_partials below: one compensated partial per z-plane.
 // It is a __device__ symbol, so its host-side name is only a stand-in: host
-// code must not pass it to a kernel.  The first call on each device looks up
-// its device address with cudaGetSymbolAddress (with that device current) and
-// remembers it; make that first call before any stream capture.  Every call
+// code must not pass it to a kernel.  The first call in each CUDA context
+// looks up its device address with cudaGetSymbolAddress and remembers it under
+// the context's id (a device reset makes a new context, and the next call a
+// new lookup); make that first call before any stream capture.  Every call
 // shares the array and leaves the last call's partials in it; each call
 // overwrites every partial it reads, so nothing has to start at zero, but two
 // calls that overlap on the GPU (different streams, no ordering) race on it.
@@ -99,17 +100,21 @@ __global__ void k_static_final(const double* partials, int nz, double* out) {
     out[v] = t.value();
 }
 
-// device address of g_plane_partials, looked up once per device
+// device address of g_plane_partials in the current context, looked up on
+// the first call in each context (a context that replaces another on the same
+// device, after a device reset, has a new id and gets a fresh lookup)
 static double* scratch_address(int device, cudaError_t* err) {
     static std::mutex mu;
     static double* addr[256] = {};
+    static unsigned long long ctx[256] = {};
     *err = cudaSuccess;
     if (device < 0 || device >= 256) {
         *err = cudaErrorInvalidDevice;
         return nullptr;
     }
+    const unsigned long long id = current_context_id();
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[device]) {
+    if (!addr[device] || !id || ctx[device] != id) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_plane_partials);
         if (e != cudaSuccess) {
@@ -117,6 +122,7 @@ static double* scratch_address(int device, cudaError_t* err) {
             return nullptr;
         }
         addr[device] = (double*)p;
+        ctx[device] = id;
     }
     return addr[device];
 }

@@ -6,13 +6,12 @@ component) and the wetting parameter Delta(77 deg) (zeta_A = +Delta,
 zeta_B = -Delta, Eq. 20) were measured with the FP64 oracle
 (tests/golden/calibrate_pickering.py -> pickering_calibration.json).
 
-The FP16 deviation storage and the FP32 form against the FP64 path on the
-same inputs: the fields after 100 steps (FP32 within 1e-5, FP16 within 1e-3
-of the largest density), and after 5000 steps the interface (its link
-crossing count and the structure-factor peak within 1 %).  The smooth
-interface measure A = sum (1 - phi^2), whose value is dominated by the bulk
-phases, is compared with a looser bound (its FP16 bias is discussed in the
-long-run bijel test)."""
+The FP16 deviation storage (stochastic rounding, its default) and the FP32
+form against the FP64 path on the same inputs: the fields after 100 steps
+(FP32 within 1e-5, FP16 within 1e-3 of the largest density on every node),
+and after 5000 steps the interface (its link crossing count, the smooth
+measure A = sum (1 - phi^2) and the structure-factor peak within 1 %).  FP16
+with rounding to nearest is run beside it and its errors recorded."""
 import json
 import os
 
@@ -35,14 +34,17 @@ def calibration():
 
 
 def run_fixed(prec, w, a, b, c, steps=100):
-    """The fields after ``steps`` with the particles held immobile."""
+    """The fields after ``steps`` with the particles held immobile
+    (``fp16rn``: FP16 storage rounded to nearest)."""
     import torch
 
-    from paper_2004_04080_gb300.lbgb import LBLattice
+    from paper_2004_04080_gb300.lbgb import LB_ROUND_NEAREST, LBLattice
 
-    g = LBLattice(w.shape, prec, max_colloids=w.n_colloids)
+    g = LBLattice(w.shape, "fp16" if prec == "fp16rn" else prec, max_colloids=w.n_colloids)
     g.set_params(**w.params)
     g.init_fields(a, b)
+    if prec == "fp16rn":
+        g.set_rounding(LB_ROUND_NEAREST)
     g.add_colloids(c["pos"], c["radius"], np.full(w.n_colloids, np.inf))
     g.step(steps)
     ra, rb, _ = g.get_fields()
@@ -94,7 +96,7 @@ def runs():
     for p, v in r.items():  # a record of the observables (pytest -s)
         print(p, {s: {k: x for k, x in o.items() if k not in ("rho", "own", "pos")} for s, o in v.items()})
     print("initial", init)
-    fixed = {p: run_fixed(p, w, a, b, c) for p in ("fp64", "fp32", "fp16")}
+    fixed = {p: run_fixed(p, w, a, b, c) for p in ("fp64", "fp32", "fp16", "fp16rn")}
     return init, r, fixed
 
 
@@ -143,25 +145,28 @@ def test_fields_after_100_steps_immobile_particles(runs):
     """The fields at 100 steps on the same inputs with the particles held in
     place (the node map is then the same in every form, so the comparison
     measures the storage forms).  FP32: within 1e-5 on every node (measured
-    3.0e-6).  FP16: the bound of this workload, 1e-3, holds in the L2 norm
-    (measured 6.3e-4) but not on every node (measured 2.4e-3 at the worst
-    node): at the coexistence densities 1.80 / 0.24 of this mixture every
-    population deviates by about 0.8 w_i from the shift w_i rho0 (rho0 = 1),
-    so each store rounds at 2^-11 of that, and the largest of 16.8 M
-    accumulated site errors reaches a few times their spread."""
+    3.0e-6).  FP16 with stochastic rounding: within 1e-3 on every node
+    (measured 8.4e-4 at the worst node, 1.6e-4 in the L2 norm).  Recorded
+    beside it: FP16 rounded to nearest misses the bound on single nodes
+    (measured 2.4e-3, L2 6.3e-4): at the coexistence densities 1.80 / 0.24 of
+    this mixture every population deviates by about 0.8 w_i from the shift
+    w_i rho0 (rho0 = 1), and rounding a value that changes little from step to
+    step the same way every step makes its error a bias that grows with the
+    steps; stochastic rounding makes it a random walk."""
     _, _, fx = runs
     qa, qb, q_own = fx["fp64"]
     top = max(qa.max(), qb.max())
     res = {}
-    for prec in ("fp32", "fp16"):
+    for prec in ("fp32", "fp16", "fp16rn"):
         ra, rb, own = fx[prec]
         assert np.array_equal(own, q_own)
         e = np.maximum(np.abs(ra - qa), np.abs(rb - qb)) / top
         l2 = np.sqrt((np.sum((ra - qa) ** 2) + np.sum((rb - qb) ** 2)) / (np.sum(qa ** 2) + np.sum(qb ** 2)))
         res[prec] = dict(max=float(e.max()), l2=float(l2))
     print("immobile particles, field errors vs FP64 at 100 steps", res)
-    assert res["fp16"]["l2"] < 1e-3 and res["fp16"]["max"] < 5e-3, res
+    assert res["fp16"]["max"] < 1e-3 and res["fp16"]["l2"] < 1e-3, res
     assert res["fp32"]["max"] < 1e-5, res
+    assert res["fp16rn"]["l2"] < 1e-3 and res["fp16rn"]["max"] < 5e-3, res
 
 
 def test_fields_after_100_steps_mobile_particles(runs):
@@ -192,4 +197,4 @@ def test_interface_after_5000_steps(runs, prec):
     assert rel(a["X"], q["X"]) < 1e-2, (a["X"], q["X"])
     assert a["kp"] == q["kp"]
     assert rel(a["Sp"], q["Sp"]) < 1e-2, (a["Sp"], q["Sp"])
-    assert rel(a["A"], q["A"]) < (1e-3 if prec == "fp32" else 3e-2), (a["A"], q["A"])
+    assert rel(a["A"], q["A"]) < (1e-3 if prec == "fp32" else 1e-2), (a["A"], q["A"])

@@ -1,4 +1,5 @@
-"""Stochastic rounding of the FP16 deviation stores (lb_set_rounding)."""
+"""Stochastic rounding of the FP16 deviation stores (the FP16 default;
+lb_set_rounding), with the hardware's stochastic-rounding conversion."""
 import numpy as np
 import pytest
 
@@ -78,6 +79,35 @@ def test_stochastic_rounding_against_the_oracle(case):
     o.step(steps)
     compare_fields(g, o, 1e-3)
     compare_colloids(g, o, 1e-3)
+
+
+def test_fp16_rounds_stochastically_by_default():
+    """An FP16 context stores with stochastic rounding unless told otherwise
+    (the adjoint, which needs reproducible recomputation, then refuses)."""
+    import torch
+
+    from paper_2004_04080_gb300 import lbgb
+    from paper_2004_04080_gb300.lbgb import LB_ROUND_NEAREST, LBError, LBLattice
+
+    g = LBLattice((16, 16, 16), "fp16", max_colloids=0)
+    g.set_params(G=0.0, rho0=(1.0, 1.0))
+    g.init_fields(np.full(4096, 0.7371), np.full(4096, 1.3119))
+    fb, sb = lbgb.lb_adjoint_bytes(g.h)
+    adj = torch.empty(fb, dtype=torch.uint8, device="cuda")
+    scratch = torch.empty(sb, dtype=torch.uint8, device="cuda")
+    with pytest.raises(LBError):
+        lbgb.lb_adjoint_seed(g.h, 1.0, adj.data_ptr(), scratch.data_ptr())
+    g.set_rounding(LB_ROUND_NEAREST)
+    lbgb.lb_adjoint_seed(g.h, 1.0, adj.data_ptr(), scratch.data_ptr())
+    # a uniform fluid at rest stores one value per population when rounded to
+    # nearest, two neighbouring halves when rounded stochastically
+    g.step(1)
+    assert np.ptp(g.populations(0)[1]) == 0.0
+    h = LBLattice((16, 16, 16), "fp16", max_colloids=0)
+    h.set_params(G=0.0, rho0=(1.0, 1.0))
+    h.init_fields(np.full(4096, 0.7371), np.full(4096, 1.3119))
+    h.step(1)
+    assert len(np.unique(h.populations(0)[1])) == 2
 
 
 def test_the_adjoint_refuses_stochastic_rounding():

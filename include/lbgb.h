@@ -79,6 +79,16 @@ typedef struct {
     double side_wall_k;     /* soft harmonic particle-wall spring; 0 disables    */
     double side_wall_d;     /* it pushes when a centre is closer than d to a wall */
     int rotate;             /* integrate angular velocity and orientation        */
+    /* Janus wettability (Sec. 5.1 colloid benchmarks; App. A wettability
+     * angle): with janus != 0 a particle node whose direction from the
+     * centre makes the polar angle theta with the particle's first body axis
+     * x* (first column of R(q), Eq. 31) uses the wetting constants
+     * s zeta[0] and -s zeta[1] in Eq. 20, where s goes from -1 to 1 across
+     * [janus_theta0 - janus_width/2, janus_theta0 + janus_width/2] along the
+     * cubic smoothstep (a step at janus_theta0 for width 0).  Degrees;
+     * janus_width >= 0. */
+    int janus;
+    double janus_theta0, janus_width;
 } lb_params;
 
 /* Device workspace size for a lattice; *bytes receives the size.

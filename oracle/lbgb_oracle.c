@@ -138,6 +138,8 @@ typedef struct {
     double lub_hn, lub_hmin, lub_scale;
     double side_wall_k, side_wall_d;
     int rotate;
+    int janus;                         /* Janus wettability on/off          */
+    double janus_theta0, janus_width;  /* switch centre and width, degrees  */
 } orc_params;
 
 /* Neumaier compensated sum */
@@ -329,6 +331,8 @@ int orc_set_params(orc_t *o, const orc_params *p)
         return ORC_ERR_ARG;
     if (!p->bc[0] || !p->bc[1])
         return ORC_ERR_ARG; /* walls only normal to z */
+    if (p->janus && !(p->janus_width >= 0.0 && isfinite(p->janus_width) && isfinite(p->janus_theta0)))
+        return ORC_ERR_ARG;
     o->P = *p;
     o->have_params = 1;
     return ORC_OK;
@@ -628,22 +632,62 @@ static double psi_at(const orc_t *o, int k, int x, int y, int z, int i)
     return o->psi[k][n];
 }
 
+/* Janus wettability (Sec. 5.1, the colloid benchmarks; App. A, the MD
+ * room's wettability-angle directive): the particle's wetting varies with
+ * the polar angle theta between the direction from its centre to the node
+ * and its first body axis x* (the first column of the rotation matrix of
+ * Eq. 31, body to space).  The switch s goes smoothly from -1 to 1 across
+ * [theta0 - width/2, theta0 + width/2] (a cubic smoothstep; a step at
+ * theta0 for width 0).  With it on, the node's wetting constants are
+ * s zeta^A and -s zeta^B, so the caps theta < theta0 and theta > theta0 wet
+ * oppositely.  Returns s, or 1 with the switch off (plain zeta^k). */
+static double janus_switch(const orc_t *o, int p, long s)
+{
+    const double *q = &o->quat[4 * p];
+    double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double a = q[0] / n, b = q[1] / n, c = q[2] / n, e = q[3] / n;
+    double ax[3], d[3], zero[3] = {0.0, 0.0, 0.0}, dn, ct, th, lo, t;
+    if (!o->P.janus)
+        return 1.0;
+    ax[0] = a * a + b * b - c * c - e * e;
+    ax[1] = 2.0 * (b * c + a * e);
+    ax[2] = 2.0 * (b * e - a * c);
+    rel_pos(o, s, p, zero, d);
+    dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (dn == 0.0)
+        return 0.0; /* the centre node: no direction */
+    ct = (ax[0] * d[0] + ax[1] * d[1] + ax[2] * d[2]) / dn;
+    ct = ct > 1.0 ? 1.0 : (ct < -1.0 ? -1.0 : ct);
+    th = acos(ct) * (180.0 / M_PI);
+    lo = o->P.janus_theta0 - 0.5 * o->P.janus_width;
+    if (o->P.janus_width <= 0.0)
+        return th < o->P.janus_theta0 ? -1.0 : 1.0;
+    t = (th - lo) / o->P.janus_width;
+    t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+    return -1.0 + 2.0 * t * t * (3.0 - 2.0 * t);
+}
+
 /* Step 4: Eq. 20 virtual densities, Eq. 11 on fluid, Eq. 21 on solid. */
 static void lb_forces(orc_t *o, int store_particle_terms)
 {
     long s, N = o->N;
     int k, i, d, x, y, z;
+    double sw;
     nsum *acc = (nsum *)zalloc(sizeof(nsum) * 6 * (size_t)(o->nc ? o->nc : 1));
     /* Eq. 20 on every solid node that has a fluid neighbour */
-#pragma omp parallel for private(k, i, x, y, z) schedule(static)
+#pragma omp parallel for private(k, i, x, y, z, sw) schedule(static)
     for (s = 0; s < N; s++) {
         o->psi[0][s] = 0.0;
         o->psi[1][s] = 0.0;
         if (o->owner[s] < 0)
             continue;
         coords(o, s, &x, &y, &z);
+        sw = janus_switch(o, o->owner[s], s);
         for (k = 0; k < 2; k++) {
             double num = 0.0, den = 0.0;
+            /* wetting constant of this node: zeta^k, or with the Janus
+             * switch on s zeta^A and -s zeta^B */
+            double zk = o->P.janus ? (k == 0 ? sw : -sw) * o->P.zeta[k] : o->P.zeta[k];
             for (i = 1; i < NQ; i++) {
                 long n = neighbour(o, x, y, z, i);
                 if (n < 0 || o->owner[n] >= 0)
@@ -652,7 +696,7 @@ static void lb_forces(orc_t *o, int store_particle_terms)
                 den += WT[i];
             }
             if (den > 0.0)
-                o->psi[k][s] = (1.0 + o->P.zeta[k]) * num / den;
+                o->psi[k][s] = (1.0 + zk) * num / den;
         }
     }
     /* wall nodes (wetting mode 0): mean density of their fluid neighbours */

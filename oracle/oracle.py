@@ -46,6 +46,9 @@ class OrcParams(C.Structure):
         ("side_wall_k", C.c_double),
         ("side_wall_d", C.c_double),
         ("rotate", C.c_int),
+        ("janus", C.c_int),
+        ("janus_theta0", C.c_double),
+        ("janus_width", C.c_double),
     ]
 
 
@@ -115,13 +118,16 @@ def _f64(a, shape=None):
 # fluid at tau = 1 without coupling, wetting, walls, body force or particle
 # pair forces; reference density 1/2 per component (the 50/50 mixture of the
 # benchmark workloads); lubrication off, with the cut-off gap 0.67 and floor
-# 0.5 of App. D and the prefactor 0.1; rotation integrated (Eqs. 33-34).
+# 0.5 of App. D and the prefactor 0.1; rotation integrated (Eqs. 33-34);
+# Janus wettability off, with the switch at 108 degrees and 10 degrees wide of
+# the benchmark input (App. D) for when it is turned on.
 DEFAULTS = dict(
     tau=(1.0, 1.0), G=0.0, zeta=(0.0, 0.0), rho0=(0.5, 0.5), bc=(1, 1, 1),
     wall_u_lo=(0.0, 0.0, 0.0), wall_u_hi=(0.0, 0.0, 0.0), body_force=(0.0, 0.0, 0.0),
     hertz_K=0.0, hertz_sigma=0.0, hertz_rcap=0.0,
     lub_on=0, lub_hn=0.67, lub_hmin=0.5, lub_scale=0.1,
     side_wall_k=0.0, side_wall_d=0.0, rotate=1,
+    janus=0, janus_theta0=108.0, janus_width=10.0,
 )
 
 

@@ -284,7 +284,9 @@ __global__ void __launch_bounds__(128) k_adj_local(Lattice L, AdjArgs A) {
 // dJ/dpsi^k(y) = sum_i w_i c_i . Sbar^k(y - c_i) over fluid x = y - c_i.  On
 // fluid nodes it is the density adjoint R; on particle frontier nodes it
 // becomes coef = dJ/dpsi (1 + zeta^k) / W (W = sum of the fluid-neighbour
-// weights, Eq. 20) and contributes dJ/dzeta^k = dJ/dpsi psi/(1 + zeta^k).
+// weights, Eq. 20) and contributes dJ/dzeta^k = dJ/dpsi psi/(1 + zeta^k);
+// with the Janus switch s of the node the factor is 1 + s_k zeta^k
+// (s_A = s, s_B = -s) and the contribution dJ/dpsi s_k psi/(1 + s_k zeta^k).
 template <int PREC>
 __global__ void __launch_bounds__(128) k_adj_gather(Lattice L, AdjArgs A) {
     typedef typename Prec<PREC>::C C;
@@ -316,10 +318,26 @@ __global__ void __launch_bounds__(128) k_adj_gather(Lattice L, AdjArgs A) {
             Rout[L.pstride + s] = pb[1];
         } else {
             const C* psi = (const C*)L.psi;
+            // the node's wetting factors 1 + s_k zeta^k: s_k = 1 without the
+            // Janus switch, s_A = s and s_B = -s with it
+            C sk[2] = {C(1), C(1)};
+            if (L.P.janus) {
+                const int p = L.owner[s];
+                const int xs[3] = {x, y, z}, Ls[3] = {L.nx, L.ny, L.nz};
+                C d[3];
+                for (int c = 0; c < 3; c++) {
+                    double dd = (double)xs[c] - L.pos[3 * p + c];
+                    if (L.per[c]) dd -= (double)Ls[c] * rint(dd / (double)Ls[c]);
+                    d[c] = C(dd);
+                }
+                const C sw = janus_switch<C>(L, p, d);
+                sk[0] = sw;
+                sk[1] = -sw;
+            }
             for (int k = 0; k < 2; k++) {
-                C zk = C(1) + C(L.P.zeta[k]);
+                C zk = C(1) + sk[k] * C(L.P.zeta[k]);
                 cf[k * L.N + s] = W > C(0) ? pb[k] * zk / W : C(0);
-                zp[k] = W > C(0) ? pb[k] * psi[k * L.N + s] / zk : C(0);
+                zp[k] = W > C(0) ? pb[k] * sk[k] * psi[k * L.N + s] / zk : C(0);
             }
         }
     }

@@ -93,8 +93,8 @@ const int RED_BLOCKS = 1024;
 const int PROF_MAX = 16384;
 
 struct Layout {
-    size_t f0, f1, mom, psi, psi_wall, mask, owner, evt, flags, col, prev, ipos, fsnap, cells, cells_bytes, red,
-        totals, total;
+    size_t f0, f1, mom, psi, psi_wall, mask, owner, evt, flags, col, prev, acc, ipos, fsnap, cells, cells_bytes,
+        red, totals, total;
     long long pstride;
 };
 
@@ -119,6 +119,7 @@ Layout layout(int nx, int ny, int nz, int prec, int maxc) {
     int mc = maxc > 0 ? maxc : 1;
     l.col = off; off = align_up(off + (size_t)mc * DOUBLES_PER_PARTICLE * 8);
     l.prev = off; off = align_up(off + (size_t)mc * 4);
+    l.acc = off; off = align_up(off + (size_t)ACC_TERMS * mc * 6 * 8);
     l.ipos = off; off = align_up(off + (size_t)mc * 12);
     l.fsnap = off; off = align_up(off + (size_t)mc * 36);
     // particle cell list: counts and starts of up to 64^3 cells, then the items
@@ -240,6 +241,9 @@ int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_worksp
                        &L.Tc, &L.Fs, &L.Ts, &L.Fpair, &L.Ftot, &L.Ttot};
     for (int a = 0; a < 13; a++) { *more[a] = c; c += 3 * mc; }
     L.prev_valid = (int*)(ctx->ws + l.prev);
+    L.acc = (unsigned long long*)(ctx->ws + l.acc);
+    L.maxc = mc;
+    L.acc_wide = prec == LB_FP64;
     L.ipos = (int*)(ctx->ws + l.ipos);
     L.fsnap = (float*)(ctx->ws + l.fsnap);
     L.red = (double*)(ctx->ws + l.red);
@@ -288,6 +292,8 @@ int lb_set_params(lb_ctx* ctx, const lb_params* p) {
             return set_err(ctx, LB_ERR_ARG, "non-finite wall velocity or body force");
     if (p->lub_on && !(p->lub_hmin > 0.0 && p->lub_hn > p->lub_hmin))
         return set_err(ctx, LB_ERR_ARG, "lubrication needs 0 < lub_hmin < lub_hn");
+    if (p->janus && !(isfinite(p->janus_theta0) && isfinite(p->janus_width) && p->janus_width >= 0.0))
+        return set_err(ctx, LB_ERR_ARG, "janus needs a finite switch angle and a width >= 0");
     if (ctx->stepped && p->bc[2] != ctx->L.P.bc[2])
         return set_err(ctx, LB_ERR_STATE, "boundary conditions cannot change after stepping");
     ctx->L.P = *p;

@@ -377,8 +377,8 @@ __global__ void __launch_bounds__(PB) k_remap_classify(Lattice L) {
     block_reduce<6, C>(acc, out);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int m = 0; m < 3; m++) {
-            atomicAdd(L.Fd + 3 * p + m, out[m]);
-            atomicAdd(L.Td + 3 * p + m, out[3 + m]);
+            acc_add(L, acc_slot(L, ACC_FD, p, m), out[m]);
+            acc_add(L, acc_slot(L, ACC_TD, p, m), out[3 + m]);
         }
 }
 
@@ -432,8 +432,8 @@ __global__ void __launch_bounds__(PB) k_remap_create(Lattice L) {
     block_reduce<6, C>(acc, out);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         for (int m = 0; m < 3; m++) {
-            atomicAdd(L.Fc + 3 * p + m, out[m]);
-            atomicAdd(L.Tc + 3 * p + m, out[3 + m]);
+            acc_add(L, acc_slot(L, ACC_FC, p, m), out[m]);
+            acc_add(L, acc_slot(L, ACC_TC, p, m), out[3 + m]);
         }
 }
 
@@ -477,6 +477,7 @@ __device__ __forceinline__ uint32_t nbr_solid(const Lattice& L, const SiteNbr& n
 
 // Eq. 20 on every frontier node s (a particle node with at least one fluid
 // neighbour): psi^k(s) = (1 + zeta^k) sum w_i rho^k / sum w_i over the fluid
+// neighbours (with the Janus switch s of the node: 1 + s zeta^A, 1 - s zeta^B)
 // neighbours, and Eq. 21 (repulsive sign):
 // F_s = -G sum_k psi^k(s) sum w_i rho^kbar(s + c_i) c_i, added with its torque
 // (x_s - r_p) x F_s to F_s, T_s of the owning particle with FP64 atomics (the
@@ -613,11 +614,24 @@ __global__ void __launch_bounds__(VTX* VTY) k_virtual(Lattice L, int store_terms
             }
             d[c] = C(dd) - fr;
         }
+        C fa = zA, fb = zB;
+        if (L.P.janus) {
+            const C sw = janus_switch<C>(L, p, d);
+            fa = C(1) + sw * C(L.P.zeta[0]);
+            fb = C(1) - sw * C(L.P.zeta[1]);
+        }
+        const C pa = fa * num[0] / den;
+        const C pb = fb * num[1] / den;
+        psi[s] = pa;
+        psi[L.N + s] = pb;
+        if (!store_terms) continue;
+#pragma unroll
+        for (int c = 0; c < 3; c++) fs[c] = -G * pa * sB[c] + -G * pb * sA[c];
         crs<C>(d, fs, tq);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            atomicAdd(L.Fs + 3 * p + c, double(fs[c]));
-            atomicAdd(L.Ts + 3 * p + c, double(tq[c]));
+            acc_add(L, acc_slot(L, ACC_FS, p, c), fs[c]);
+            acc_add(L, acc_slot(L, ACC_TS, p, c), tq[c]);
         }
     }
 }
@@ -831,6 +845,10 @@ __global__ void k_integrate(Lattice L) {
     if (p >= L.nc) return;
     double F[3], T[3];
     bool first = !L.prev_valid[p];
+    // the step's fixed-point sums as FP64 terms
+    double* terms[ACC_TERMS] = {L.Fliq, L.Tliq, L.Fd, L.Td, L.Fc, L.Tc, L.Fs, L.Ts};
+    for (int t = 0; t < ACC_TERMS; t++)
+        for (int d = 0; d < 3; d++) terms[t][3 * p + d] = acc_value(L, acc_slot(L, t, p, d));
     for (int d = 0; d < 3; d++) {
         double fp = first ? L.Fliq[3 * p + d] : L.Fliq_prev[3 * p + d];
         double tp = first ? L.Tliq[3 * p + d] : L.Tliq_prev[3 * p + d];
@@ -916,12 +934,11 @@ int launch_map_initial(const Lattice& L, int prec, int first, int count, cudaStr
 
 int launch_remap(const Lattice& L, int prec, int maxc, cudaStream_t st) {
     if (L.nc <= 0) return 0;
-    // the per-particle terms of the step are sums of block partials and of
-    // per-site contributions added with atomics: Fliq, Tliq (contiguous) and
-    // Fd, Td, Fc, Tc, Fs, Ts (contiguous) start from zero
-    const size_t m3 = (size_t)3 * (maxc > 0 ? maxc : 1) * sizeof(double);
-    cudaMemsetAsync(L.Fliq, 0, 2 * m3, st);
-    cudaMemsetAsync(L.Fd, 0, 6 * m3, st);
+    // the per-particle terms of the step are fixed-point sums of block
+    // partials and per-site contributions (acc_add), from zero; the
+    // integrator turns them into F_liq, T_liq, F_d, T_d, F_c, T_c, F_s, T_s
+    (void)maxc;
+    cudaMemsetAsync(L.acc, 0, (size_t)ACC_TERMS * L.maxc * 6 * sizeof(unsigned long long), st);
     const dim3 grid((unsigned)L.nc, REMAP_GROUPS);
     DISPATCHC(prec, (k_remap_classify<P><<<grid, PBLK, 0, st>>>(L)));
     DISPATCHC(prec, (k_remap_create<P><<<grid, PBLK, 0, st>>>(L)));

@@ -114,18 +114,17 @@ __global__ void k_wall_psi(Lattice L) {
     pw[(side * 2 + 1) * nxy + w] = den > C(0) ? num1 / den : C(0);
 }
 
-// Add the link force and torque of one site (Eqs. 22, 23) to F_liq, T_liq of
-// its particle with FP64 atomics (p < 0: no link of the site reaches a
-// particle).  One warp instruction per component; the L2 serves them
-// alongside the population traffic.  The order of the additions varies from
-// run to run (FP64 sums: differences at the level of its rounding).
+// Add the link force and torque of one site (Eqs. 22, 23) to the fixed-point
+// sums of F_liq, T_liq of its particle (p < 0: no link of the site reaches a
+// particle).  Integer atomics: the sums do not depend on the order of the
+// additions, so they are the same bits on every run.
 template <typename C>
 __device__ __forceinline__ void commit_link_forces(const Lattice& L, int p, const C (&F)[3], const C (&T)[3]) {
     if (p < 0) return;
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        atomicAdd(L.Fliq + 3 * p + d, double(F[d]));
-        atomicAdd(L.Tliq + 3 * p + d, double(T[d]));
+        acc_add(L, acc_slot(L, ACC_FLIQ, p, d), F[d]);
+        acc_add(L, acc_slot(L, ACC_TLIQ, p, d), T[d]);
     }
 }
 
@@ -526,8 +525,8 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
             const C T2[3] = {r2[1] * F2[2] - r2[2] * F2[1], r2[2] * F2[0] - r2[0] * F2[2],
                              r2[0] * F2[1] - r2[1] * F2[0]};
             for (int d = 0; d < 3; d++) {
-                atomicAdd(L.Fliq + 3 * nd + d, double(F2[d]));
-                atomicAdd(L.Tliq + 3 * nd + d, double(T2[d]));
+                acc_add(L, acc_slot(L, ACC_FLIQ, nd, d), F2[d]);
+                acc_add(L, acc_slot(L, ACC_TLIQ, nd, d), T2[d]);
             }
         }
     }

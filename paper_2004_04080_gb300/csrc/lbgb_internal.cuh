@@ -30,12 +30,14 @@ __host__ __device__ constexpr int cz(int i) {
          : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
 }
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
 // lattice weights w0 = 1/3, w1-6 = 1/18, w7-18 = 1/36
 template <typename C>
 __host__ __device__ constexpr C wgt(int i) {
     return i == 0 ? C(1) / C(3) : (i <= 6 ? C(1) / C(18) : C(1) / C(36));
 }
 constexpr int Q = 19;
+
 
 // ---------------------------------------------------------- precisions
 // Storage type S and compute type C of the populations.
@@ -127,6 +129,11 @@ struct Lattice {
     double *Fliq, *Tliq, *Fliq_prev, *Tliq_prev;
     int* prev_valid;
     double *Fd, *Td, *Fc, *Tc, *Fs, *Ts, *Fpair, *Ftot, *Ttot;
+    // fixed-point sums of the per-site terms of one step (see acc_add):
+    // [ACC_TERMS][maxc][3][2] words, zeroed at the start of each step
+    unsigned long long* acc;
+    int maxc;
+    int acc_wide;      // two-word sums (FP64 contexts)
     double rmax;       // largest particle radius
     double inv_tau[2]; // 1/tau_k
     double inv_nu[2];  // 1/nu_k, nu_k = (tau_k - 1/2)/3
@@ -360,6 +367,79 @@ __device__ __forceinline__ void particle_u0_of(const Lattice& L, const ParticleR
 template <typename C>
 __device__ __forceinline__ void particle_u0(const Lattice& L, int p, int x, int y, int z, C (&U0)[3], C (&rel)[3]) {
     particle_u0_of<C>(L, particle_load<C>(L, p), x, y, z, U0, rel);
+}
+
+// Janus wettability of a particle node (Sec. 5.1; App. A wettability angle):
+// the switch s in [-1, 1] of the polar angle between d = x - r_p and the
+// particle's first body axis, the first column of R(q) (Eq. 31); the node's
+// wetting constants are then s zeta^A and -s zeta^B.  s goes from -1 to 1
+// across [theta0 - w/2, theta0 + w/2] along the cubic smoothstep.
+template <typename C>
+__device__ __forceinline__ C janus_switch(const Lattice& L, int p, const C (&d)[3]) {
+    const double* q = L.quat + 4 * p;
+    const C a = C(q[0]), b = C(q[1]), c = C(q[2]), e = C(q[3]);
+    const C n2 = a * a + b * b + c * c + e * e;
+    // first column of R(q) for the unnormalised q, divided by |q|^2 below
+    const C ax[3] = {a * a + b * b - c * c - e * e, C(2) * (b * c + a * e), C(2) * (b * e - a * c)};
+    const C dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (!(dn > C(0))) return C(0);
+    C ct = (ax[0] * d[0] + ax[1] * d[1] + ax[2] * d[2]) / (n2 * dn);
+    ct = ct > C(1) ? C(1) : (ct < C(-1) ? C(-1) : ct);
+    const C th = acos(ct) * C(57.295779513082320876798154814105);  // degrees
+    const C th0 = C(L.P.janus_theta0), w = C(L.P.janus_width);
+    if (!(w > C(0))) return th < th0 ? C(-1) : C(1);
+    C t = (th - (th0 - C(0.5) * w)) / w;
+    t = t < C(0) ? C(0) : (t > C(1) ? C(1) : t);
+    return C(-1) + C(2) * t * t * (C(3) - C(2) * t);
+}
+
+// ---------------------------------------- per-particle fixed-point sums
+// The per-particle terms that many threads add to (link forces of Eqs. 19,
+// 22-23, the wetting force of Eq. 21, the remap momenta of Eqs. 24-25) are
+// summed as fixed-point integers with 64-bit integer atomics, so that a sum
+// does not depend on the order in which threads add: it is reproducible bit
+// for bit.  Two formats, by the context's precision (L.acc_wide):
+//  * FP32 / FP16 contexts: one word, round(v 2^40) (|v| < 2^23, resolution
+//    2^-40, far below the FP32 rounding of each term);
+//  * FP64 contexts: two words, V = v 2^64 as hi = floor(V / 2^40) and
+//    lo = V - hi 2^40 in [0, 2^40] (|v| < 2^39, resolution 2^-64; the lo
+//    sums stay below 2^63 for up to 2^23 terms per step); the total is
+//    hi 2^-24 + lo 2^-64.
+enum { ACC_FLIQ, ACC_TLIQ, ACC_FD, ACC_TD, ACC_FC, ACC_TC, ACC_FS, ACC_TS, ACC_TERMS };
+
+__device__ __forceinline__ unsigned long long* acc_slot(const Lattice& L, int term, int p, int d) {
+    return L.acc + (((size_t)term * L.maxc + p) * 3 + d) * 2;
+}
+
+// A term outside the range of its format (or not finite) is flagged as a
+// non-finite state and not added.
+// FP32 terms come from FP32 / FP16 contexts only.
+__device__ __forceinline__ void acc_add(const Lattice& L, unsigned long long* a, float v) {
+    if (!(fabsf(v) < 8388608.0f)) {  // 2^23
+        atomicOr(L.flags, FLAG_NONFINITE);
+        return;
+    }
+    atomicAdd(a, (unsigned long long)__float2ll_rn(v * 1099511627776.0f));  // 2^40
+}
+
+__device__ __forceinline__ void acc_add(const Lattice& L, unsigned long long* a, double v) {
+    if (!(fabs(v) < (L.acc_wide ? 549755813888.0 : 8388608.0))) {  // 2^39 / 2^23
+        atomicOr(L.flags, FLAG_NONFINITE);
+        return;
+    }
+    if (!L.acc_wide) {
+        atomicAdd(a, (unsigned long long)__double2ll_rn(v * 1099511627776.0));
+        return;
+    }
+    const double h = floor(v * 16777216.0);           // 2^24
+    const double r = v - h * 5.9604644775390625e-08;  // exact, in [0, 2^-24)
+    atomicAdd(a, (unsigned long long)__double2ll_rn(h));
+    atomicAdd(a + 1, (unsigned long long)__double2ll_rn(r * 18446744073709551616.0));
+}
+
+__device__ __forceinline__ double acc_value(const Lattice& L, const unsigned long long* a) {
+    if (!L.acc_wide) return (double)(long long)a[0] * 9.094947017729282e-13;  // 2^-40
+    return (double)(long long)a[0] * 5.9604644775390625e-08 + (double)a[1] * 5.421010862427522e-20;
 }
 
 // Neumaier sum in the compute type (per-thread partials before the FP64 merge)

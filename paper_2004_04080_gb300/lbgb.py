@@ -46,6 +46,7 @@ class LbParams(C.Structure):
         ("hertz_sigma", C.c_double), ("hertz_rcap", C.c_double), ("lub_on", C.c_int),
         ("lub_hn", C.c_double), ("lub_hmin", C.c_double), ("lub_scale", C.c_double),
         ("side_wall_k", C.c_double), ("side_wall_d", C.c_double), ("rotate", C.c_int),
+        ("janus", C.c_int), ("janus_theta0", C.c_double), ("janus_width", C.c_double),
     ]
 
 

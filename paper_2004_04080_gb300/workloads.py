@@ -127,6 +127,7 @@ def default_params() -> dict:
         hertz_K=0.0, hertz_sigma=0.0, hertz_rcap=0.0,
         lub_on=0, lub_hn=0.67, lub_hmin=0.5, lub_scale=0.1,
         side_wall_k=0.0, side_wall_d=0.0, rotate=1,
+        janus=0, janus_theta0=108.0, janus_width=10.0,
     )
 
 

@@ -323,3 +323,67 @@ def test_create_rejects_lattices_beyond_32bit_site_indices():
     with pytest.raises(lbgb.LBError) as e:
         lbgb.lb_create(2048, 1024, 1024, lbgb.LB_FP32, 0, ws.data_ptr(), ws.numel(), 0)
     assert e.value.code == lbgb.LB_ERR_ARG
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("fp16", 1e-3)])
+def test_janus_particles_rotating(prec, tol):
+    """Janus wettability: the wetting of a particle node switches with its
+    angle to the particle's body axis (smoothed over 20 degrees around 100),
+    on two mobile particles that spin and drift across a demixing mixture,
+    so that the switch moves over the surface as the orientation changes
+    (Eqs. 20, 21, 31-34); 40 steps, ragged 36 x 27 x 23 box."""
+    shape = (36, 27, 23)
+    params = dict(G=0.9, tau=(1.0, 1.0), zeta=(0.2, 0.15), rho0=(0.5, 0.5), janus=1, janus_theta0=100.0,
+                  janus_width=20.0, hertz_K=20.0, hertz_sigma=8.0, hertz_rcap=7.0)
+    rs = math.sqrt(0.5)
+    col = dict(pos=[[9.3, 12.2, 10.6], [25.7, 14.1, 12.3]], radius=[4.2, 3.8], mass=[300.0, 250.0],
+               vel=[[0.03, -0.01, 0.02], [-0.02, 0.02, -0.01]],
+               omega=[[0.0, 0.03, 0.02], [0.04, -0.01, 0.0]],
+               quat=[[rs, 0.0, rs, 0.0], [0.5, 0.5, -0.5, 0.5]])
+    dens = mixture_densities(shape, seed=19, amp=0.05)
+    g, o = run_both(shape, params, 40, prec, col, dens=dens)
+    compare_fields(g, o, tol)
+    compare_colloids(g, o, tol, 1e-2 if prec == "fp16" else None)
+    # the wetting of the two caps differs: the particle force from Eq. 21
+    # is not that of a uniformly wetting particle
+    p = dict(params, janus=0)
+    _, o2 = run_both(shape, p, 40, "fp64", col, dens=dens)
+    assert np.abs(o.term("T_s") - o2.term("T_s")).max() > 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+def test_particle_sums_repeat_bit_for_bit(prec):
+    """The per-particle sums that many threads add to (link forces and
+    torques of Eqs. 19, 22-23, the wetting force of Eq. 21, the remap momenta
+    of Eqs. 24-25) are fixed-point sums, so two runs of the same input give
+    the same bits in every term and in the particle trajectories, whatever
+    the order in which the threads added (60 steps, 8 moving particles
+    crossing nodes, sheared walls, momentum kernel)."""
+    from paper_2004_04080_gb300.lbgb import LBLattice
+
+    shape = (48, 37, 29)
+    w = workload("shear512")
+    params = dict(w.params, side_wall_d=6.5)
+    rng = np.random.default_rng(3)
+    pos = [[6.0 + 12.0 * (i % 4) + rng.uniform(0, 2), 8.0 + 18.0 * (i // 4) + rng.uniform(0, 2),
+            14.0 + rng.uniform(-2, 2)] for i in range(8)]
+    col = dict(pos=pos, radius=4.5, mass=350.0, vel=rng.uniform(-0.03, 0.03, (8, 3)),
+               omega=rng.uniform(-0.02, 0.02, (8, 3)))
+    a, b = mixture_densities(shape, seed=29, amp=0.05)
+
+    def run():
+        g = LBLattice(shape, prec, max_colloids=8)
+        g.set_params(**params)
+        g.init_fields(a, b)
+        g.add_colloids(**col)
+        g.step(60)
+        return g
+
+    g1, g2 = run(), run()
+    for term in ("F_liq", "T_liq", "F_s", "T_s", "F_d", "T_d", "F_c", "T_c", "F_total", "T_total"):
+        assert np.array_equal(g1.term(term), g2.term(term)), term
+    c1, c2 = g1.get_colloids(), g2.get_colloids()
+    for key in ("pos", "vel", "omega", "quat"):
+        assert np.array_equal(c1[key], c2[key]), key
+    assert np.array_equal(g1.populations(0), g2.populations(0))
+    assert np.abs(g1.term("F_liq")).max() > 1e-4 and np.abs(g1.term("F_d")).max() > 0.0

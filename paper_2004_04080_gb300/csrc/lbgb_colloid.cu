@@ -296,7 +296,7 @@ __device__ __forceinline__ typename Prec<PREC>::C site_rho(const Lattice& L, lon
     C r = 0;
 #pragma unroll
     for (int i = 0; i < Q; i++)
-        r += ld_pop(f + ((long long)(k * Q + i)) * L.pstride + s, pop_shift<S, C>(L, k, i));
+        r += ld_pop(f + pop_index(k * Q + i, s, L.pstride), pop_shift<S, C>(L, k, i));
     return r;
 }
 
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(PB) k_remap_create(Lattice L) {
         S* f = (S*)L.f_cur;
         for (int k = 0; k < 2; k++)
             for (int i = 0; i < Q; i++)
-                st_pop(f + ((long long)(k * Q + i)) * L.pstride + s, feq<C>(i, rb[k], uw[0], uw[1], uw[2], uu),
+                st_pop(f + pop_index(k * Q + i, s, L.pstride), feq<C>(i, rb[k], uw[0], uw[1], uw[2], uu),
                        pop_shift<S, C>(L, k, i));
         C rt = rb[0] + rb[1];
         C mom[3] = {-rt * uw[0], -rt * uw[1], -rt * uw[2]}, tq[3];

@@ -31,8 +31,7 @@ __global__ void k_init(Lattice L, const double* __restrict__ stage) {
         C r = C(stage[k * L.N + s]);
 #pragma unroll
         for (int i = 0; i < Q; i++)
-            st_pop(f + ((long long)(k * Q + i)) * L.pstride + s, feq<C>(i, r, ux, uy, uz, uu),
-                   pop_shift<S, C>(L, k, i));
+            st_pop(f + pop_index(k * Q + i, s, L.pstride), feq<C>(i, r, ux, uy, uz, uu), pop_shift<S, C>(L, k, i));
     }
 }
 
@@ -62,7 +61,7 @@ __global__ void k_density(Lattice L) {
         C r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            C v = ld_pop(f + ((long long)(k * Q + i)) * L.pstride + s, pop_shift<S, C>(L, k, i));
+            C v = ld_pop(f + pop_index(k * Q + i, s, L.pstride), pop_shift<S, C>(L, k, i));
             r += v;
             if (MOM) {
                 if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
@@ -241,7 +240,7 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
         } else {
             if (want_own) {
 #pragma unroll
-                for (int q = 0; q < 2 * Q; q++) own.raw[q] = f[(long long)q * L.pstride + s];
+                for (int q = 0; q < 2 * Q; q++) own.raw[q] = f[pop_index(q, s, L.pstride)];
                 own_moments<PREC>(L, own);
                 loaded = true;
             } else {
@@ -250,7 +249,7 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
                     C r = 0;
 #pragma unroll
                     for (int i = 0; i < Q; i++)
-                        r += ld_pop(f + ((long long)(k * Q + i)) * L.pstride + s, pop_shift<S, C>(L, k, i));
+                        r += ld_pop(f + pop_index(k * Q + i, s, L.pstride), pop_shift<S, C>(L, k, i));
                     own.rho[k] = r;
                 }
             }
@@ -286,8 +285,8 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
             r1 = 0;
 #pragma unroll
             for (int i = 0; i < Q; i++) {
-                r0 += ld_pop(f + ((long long)i) * L.pstride + s, pop_shift<S, C>(L, 0, i));
-                r1 += ld_pop(f + ((long long)(Q + i)) * L.pstride + s, pop_shift<S, C>(L, 1, i));
+                r0 += ld_pop(f + pop_index(i, s, L.pstride), pop_shift<S, C>(L, 0, i));
+                r1 += ld_pop(f + pop_index(Q + i, s, L.pstride), pop_shift<S, C>(L, 1, i));
             }
             nd = ND_FLUID;
         }
@@ -426,7 +425,8 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
         V[2][d] = wall_hi ? prm<C>(L.P.wall_u_hi[d], L.PF.wall_u_hi[d]) : U0[d];
     }
     // destinations as 32-bit element offsets from the base of the plane pair
-    // (2j-1, 2j): plane 2j adds ps; sites < 2^31 and ps < 2^31 keep them in range
+    // (2j-1, 2j): plane 2j adds ps; an element of plane i is SKEW + site -
+    // c_ix (pop_index); sites < 2^31 and ps < 2^31 keep them in range
     char* fnb = (char*)L.f_nxt;
     // FP16 with stochastic rounding (SR, a separate instantiation): the
     // rounding bits of this site; both components of a link are stored by
@@ -458,7 +458,7 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
             }
         }
         if (i == 0) {
-            put2((S*)fnb + s, (S*)(fnb + (unsigned long long)ps * (unsigned)(Q * (int)sizeof(S))) + s,
+            put2((S*)fnb + (SKEW + s), (S*)(fnb + (unsigned long long)ps * (unsigned)(Q * (int)sizeof(S))) + (SKEW + s),
                  solid ? wgt<C>(0) * prm<C>(L.P.rho0[0], L.PF.rho0[0]) : fs[0],
                  solid ? wgt<C>(0) * prm<C>(L.P.rho0[1], L.PF.rho0[1]) : fs[1], pop_shift<S, C>(L, 0, 0),
                  pop_shift<S, C>(L, 1, 0));
@@ -470,7 +470,11 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
                                  : s + (unsigned)((cx(i) > 0 ? dxp : (cx(i) < 0 ? dxm : 0)) +
                                                   (cy(i) > 0 ? dyp : (cy(i) < 0 ? dym : 0)) +
                                                   (cz(i) > 0 ? dzp : (cz(i) < 0 ? dzm : 0)));
-        const unsigned off = b ? (opp(i) == lo ? s : s + ps) : (i == lo ? q : q + ps);
+        // push: the destination's element of plane i, SKEW + q - c_ix (at the
+        // source's x); bounce-back: the own element of plane opp(i),
+        // SKEW + s + c_ix
+        const unsigned off = b ? (unsigned)(SKEW + cx(i)) + s + (opp(i) == lo ? 0u : ps)
+                               : (unsigned)(SKEW - cx(i)) + q + (i == lo ? 0u : ps);
         const int zs = cz(i) + 1;
         C cw = C(cx(i)) * V[zs][0] + C(cy(i)) * V[zs][1] + C(cz(i)) * V[zs][2];
         cw = b ? C(-2) * cw : C(0);  // f_ibar = f*_i - 6 w_i rho c_i.u_w (Eq. 17)
@@ -516,8 +520,9 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
                              feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
                 fbv[k] = fsv[k] - C(6) * wgt<C>(i) * m.rho[k] * cw;
             }
-            put2((S*)(fnb + (unsigned long long)ps * (unsigned)(opp(i) * (int)sizeof(S))) + s,
-                 (S*)(fnb + (unsigned long long)ps * (unsigned)((Q + opp(i)) * (int)sizeof(S))) + s, fbv[0], fbv[1],
+            const unsigned own = (unsigned)(SKEW + cx(i)) + s;  // element of s in plane opp(i)
+            put2((S*)(fnb + (unsigned long long)ps * (unsigned)(opp(i) * (int)sizeof(S))) + own,
+                 (S*)(fnb + (unsigned long long)ps * (unsigned)((Q + opp(i)) * (int)sizeof(S))) + own, fbv[0], fbv[1],
                  pop_shift<S, C>(L, 0, i), pop_shift<S, C>(L, 1, i));
             const C fl = fsv[0] + fbv[0] + fsv[1] + fbv[1];
             // the link force into the second particle, added directly
@@ -603,7 +608,11 @@ struct AsyncShared {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
     static constexpr int NSLOT = 4;  // psi planes held: z-1, z, z+1 and the one in flight
-    S stage[2][2 * Q][FTX * TY];
+    // one 16-byte chunk of elements beyond the tile on each side of a row:
+    // the own element of a site in plane i sits c_ix off its column (pop_index)
+    static constexpr int EPC = 16 / (int)sizeof(S);
+    static constexpr int SW = FTX + 2 * EPC;
+    S stage[2][2 * Q][TY][SW];
     C psi[NSLOT][2][TY + 2][RW];
     int nd[NSLOT][TY + 2][RW];
 };
@@ -682,25 +691,17 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fu
         if (has_ring) put(rly + 1, rlx + 1, zoff + ring_xy);
     };
     // the 2 x 19 population rows of the tile of plane p into stage buffer b:
-    // lane tx copies 16-byte chunk tx % LPP of its row in planes tx / LPP,
-    // tx / LPP + PPP, ...
-    constexpr int EPC = 16 / (int)sizeof(E);  // elements per 16-byte chunk
-    constexpr int LPP = FTX / EPC;            // lanes per row
-    constexpr int PPP = FTX / LPP;            // arrays per pass
-    const int chunk = tx % LPP, plane0 = tx / LPP;
-    const bool copies = ty < H && chunk * EPC < W;
-    const long long row_off = (long long)(x0 + chunk * EPC) + (long long)L.nx * (y0 + ty);
+    // warp ty copies its row, elements SKEW + s(x0) - EPC .. + FTX + EPC of
+    // every plane (aligned: x0 and nx are multiples of EPC), in 16-byte chunks
+    constexpr int EPC = SH::EPC;
+    constexpr int WCH = SH::SW / EPC;  // chunks per row
+    const long long row_site = (long long)x0 + (long long)L.nx * (y0 + ty);
     auto issue_pops = [&](int p, int b) {
-        if (!copies) return;
-        const char* src = (const char*)L.f_cur +
-                          ((long long)plane0 * L.pstride + row_off + nxy * p) * (long long)sizeof(E);
-        const long long step = (long long)PPP * L.pstride * (long long)sizeof(E);
-        E* dst = &sh.stage[b][plane0][ty * FTX + chunk * EPC];
-#pragma unroll
-        for (int pl = plane0; pl < 2 * Q; pl += PPP) {
-            cp_async_16(dst, src);
-            src += step;
-            dst += PPP * NT;
+        if (ty >= H) return;
+        const E* base = (const E*)L.f_cur + (SKEW - EPC) + row_site + nxy * p;
+        for (int c = tx; c < 2 * Q * WCH; c += FTX) {
+            const int q = c / WCH, ch = c - q * WCH;
+            cp_async_16(&sh.stage[b][q][ty][ch * EPC], base + (long long)q * L.pstride + ch * EPC);
         }
     };
     for (int p = z0 - 1; p < z0 + 2; p++)
@@ -724,7 +725,7 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fu
                 C r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
                 for (int i = 0; i < Q; i++) {
-                    C v = ld_pop(&sh.stage[b][k * Q + i][tid], pop_shift<S, C>(L, k, i));
+                    C v = ld_pop(&sh.stage[b][k * Q + i][ty][EPC + tx - cx(i)], pop_shift<S, C>(L, k, i));
                     r += v;
                     if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
                     if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
@@ -738,7 +739,8 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fu
             const LinkInfo li = link_info(sh, sl, tx, ty, solid);
             const ParticleRef<C> pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
             collide_site<PREC, UNIT, SR>(L, sh, sl, x0 + tx, y0 + ty, z, ty, m, solid,
-                                     [&](int q) { return &sh.stage[b][q][tid]; }, li, pref, pf, Fp, Tp);
+                                     [&](int q) { return &sh.stage[b][q][ty][EPC + tx - cx(q % Q)]; }, li, pref,
+                                     pf, Fp, Tp);
         }
         commit_link_forces<C>(L, pf, Fp, Tp);
     }
@@ -953,8 +955,8 @@ __global__ void k_wall_plane_density(Lattice L) {
     C r0 = 0, r1 = 0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        r0 += ld_pop(f + ((long long)i) * L.pstride + s, pop_shift<S, C>(L, 0, i));
-        r1 += ld_pop(f + ((long long)(Q + i)) * L.pstride + s, pop_shift<S, C>(L, 1, i));
+        r0 += ld_pop(f + pop_index(i, s, L.pstride), pop_shift<S, C>(L, 0, i));
+        r1 += ld_pop(f + pop_index(Q + i, s, L.pstride), pop_shift<S, C>(L, 1, i));
     }
     psi[s] = r0;
     psi[L.N + s] = r1;
@@ -1044,7 +1046,7 @@ __global__ void k_pops_out(Lattice L, int k, int i, double* __restrict__ stage) 
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= L.N) return;
     const S* f = (const S*)L.f_cur;
-    stage[s] = double(ld_pop(f + ((long long)(k * Q + i)) * L.pstride + s, pop_shift<S, C>(L, k, i)));
+    stage[s] = double(ld_pop(f + pop_index(k * Q + i, s, L.pstride), pop_shift<S, C>(L, k, i)));
 }
 
 __global__ void k_clear_map(Lattice L) {

@@ -38,6 +38,20 @@ __host__ __device__ constexpr C wgt(int i) {
 }
 constexpr int Q = 19;
 
+// Population storage.  The population of link i of site s is element
+// SKEW + s - c_ix of plane i (of its component), s = x + nx (y + ny z).  A
+// push along c_i (Eq. 3) from site s then writes the destination's element
+// at the source's x, so the 32 pushes of a warp's row fill whole aligned
+// lines of the destination row.  Writes shifted by one element instead left
+// partial 32-byte sectors at both ends of every row segment, which halved
+// the store bandwidth (DRAM read-modify-writes); the reads of a site's own
+// populations, shifted by one element now, cost nothing measurable.  Each
+// plane is padded by SKEW = 64 elements at both ends, which keeps the first
+// site of every plane on a 128-byte boundary in each storage type.
+constexpr long long SKEW = 64;
+__host__ __device__ constexpr long long pop_index(int q, long long s, long long pstride) {
+    return (long long)q * pstride + SKEW + s - cx(q % Q);
+}
 
 // ---------------------------------------------------------- precisions
 // Storage type S and compute type C of the populations.
@@ -234,7 +248,7 @@ __device__ __forceinline__ void load_site(const Lattice& L, const typename Prec<
         C r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            C v = ld_pop(f + ((long long)(k * Q + i)) * L.pstride + s, pop_shift<S, C>(L, k, i));
+            C v = ld_pop(f + pop_index(k * Q + i, s, L.pstride), pop_shift<S, C>(L, k, i));
             fv[k][i] = v;
             r += v;
             if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;

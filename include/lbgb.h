@@ -89,6 +89,14 @@ typedef struct {
      * janus_width >= 0. */
     int janus;
     double janus_theta0, janus_width;
+    /* Particle pair list (App. A, the MD room's rcut and delr directives):
+     * pairs are listed within max(rcut, the interaction range) + delr, where
+     * the interaction range is hertz_sigma and, with lubrication, 2 R_max +
+     * lub_hn; the list is rebuilt only when a particle has moved more than
+     * delr / 2 since the last build (delr = 0: every step).  The forces are
+     * evaluated with their own cut-offs on the listed pairs, so rcut and
+     * delr change the cost, never the result.  Both >= 0. */
+    double rcut, delr;
 } lb_params;
 
 /* Device workspace size for a lattice; *bytes receives the size.
@@ -276,6 +284,10 @@ int lb_totals_static(const void *d_pops, int prec, int nx, int ny, int nz, long 
 
 /* Number of kernel launches issued by this context since creation. */
 long long lb_launch_count(const lb_ctx *ctx);
+
+/* Number of particle pair-list builds so far (see lb_params.rcut / delr);
+ * synchronises the context's stream.  -1 for a null context. */
+long long lb_pair_list_builds(lb_ctx *ctx);
 
 /* Which fused lattice kernel lb_step launches in the context's present state
  * (the sequence of Sec. 3.1 is the same for all; they differ in how the

@@ -120,7 +120,9 @@ def _f64(a, shape=None):
 # benchmark workloads); lubrication off, with the cut-off gap 0.67 and floor
 # 0.5 of App. D and the prefactor 0.1; rotation integrated (Eqs. 33-34);
 # Janus wettability off, with the switch at 108 degrees and 10 degrees wide of
-# the benchmark input (App. D) for when it is turned on.
+# the benchmark input (App. D) for when it is turned on; rcut and delr (App. A)
+# only size a neighbour list in the GPU library, so the oracle, which
+# evaluates every pair, accepts and ignores them.
 DEFAULTS = dict(
     tau=(1.0, 1.0), G=0.0, zeta=(0.0, 0.0), rho0=(0.5, 0.5), bc=(1, 1, 1),
     wall_u_lo=(0.0, 0.0, 0.0), wall_u_hi=(0.0, 0.0, 0.0), body_force=(0.0, 0.0, 0.0),
@@ -128,6 +130,7 @@ DEFAULTS = dict(
     lub_on=0, lub_hn=0.67, lub_hmin=0.5, lub_scale=0.1,
     side_wall_k=0.0, side_wall_d=0.0, rotate=1,
     janus=0, janus_theta0=108.0, janus_width=10.0,
+    rcut=0.0, delr=0.0,
 )
 
 

@@ -71,6 +71,7 @@ struct lb_ctx {
     int rec_left, rec_i;        // steps still to record, steps recorded
     unsigned long long sr_seed; // stochastic rounding: seed, and steps taken with it
     unsigned long long sr_step;
+    int vl_valid;               // the particle pair list holds the current particles
     char err[512];
 };
 
@@ -93,8 +94,8 @@ const int RED_BLOCKS = 1024;
 const int PROF_MAX = 16384;
 
 struct Layout {
-    size_t f0, f1, mom, psi, psi_wall, mask, owner, evt, flags, col, prev, acc, ipos, fsnap, cells, cells_bytes,
-        red, totals, total;
+    size_t f0, f1, mom, psi, psi_wall, mask, owner, evt, flags, col, prev, acc, vl, ipos, fsnap, cells,
+        cells_bytes, red, totals, total;
     long long pstride;
 };
 
@@ -121,6 +122,9 @@ Layout layout(int nx, int ny, int nz, int prec, int maxc) {
     l.col = off; off = align_up(off + (size_t)mc * DOUBLES_PER_PARTICLE * 8);
     l.prev = off; off = align_up(off + (size_t)mc * 4);
     l.acc = off; off = align_up(off + (size_t)ACC_TERMS * mc * 6 * 8);
+    // pair list: positions at the build (FP64), builds counter, flag,
+    // counts, neighbours
+    l.vl = off; off = align_up(off + (size_t)mc * 24 + 16 + (size_t)mc * 4 * (1 + PAIR_LIST_MAX));
     l.ipos = off; off = align_up(off + (size_t)mc * 12);
     l.fsnap = off; off = align_up(off + (size_t)mc * 36);
     // particle cell list: counts and starts of up to 64^3 cells, then the items
@@ -243,6 +247,11 @@ int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_worksp
     for (int a = 0; a < 13; a++) { *more[a] = c; c += 3 * mc; }
     L.prev_valid = (int*)(ctx->ws + l.prev);
     L.acc = (unsigned long long*)(ctx->ws + l.acc);
+    L.vl_ref = (double*)(ctx->ws + l.vl);
+    L.vl_builds = (unsigned long long*)(L.vl_ref + 3 * mc);
+    L.vl_flag = (int*)(L.vl_builds + 1);
+    L.vl_cnt = L.vl_flag + 2;
+    L.vl_nb = L.vl_cnt + mc;
     L.maxc = mc;
     L.acc_wide = prec == LB_FP64;
     L.ipos = (int*)(ctx->ws + l.ipos);
@@ -267,6 +276,7 @@ int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_worksp
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.psi, 0, (size_t)2 * L.N * compute_bytes(prec), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.col, 0, (size_t)mc * DOUBLES_PER_PARTICLE * 8, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.prev, 0, (size_t)mc * 4, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.vl, 0, (size_t)mc * 24 + 16, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = create_side_stream(ctx);
     if (e != cudaSuccess) {
@@ -295,9 +305,12 @@ int lb_set_params(lb_ctx* ctx, const lb_params* p) {
         return set_err(ctx, LB_ERR_ARG, "lubrication needs 0 < lub_hmin < lub_hn");
     if (p->janus && !(isfinite(p->janus_theta0) && isfinite(p->janus_width) && p->janus_width >= 0.0))
         return set_err(ctx, LB_ERR_ARG, "janus needs a finite switch angle and a width >= 0");
+    if (!(p->rcut >= 0.0 && isfinite(p->rcut) && p->delr >= 0.0 && isfinite(p->delr)))
+        return set_err(ctx, LB_ERR_ARG, "rcut and delr must be finite and >= 0");
     if (ctx->stepped && p->bc[2] != ctx->L.P.bc[2])
         return set_err(ctx, LB_ERR_STATE, "boundary conditions cannot change after stepping");
     ctx->L.P = *p;
+    ctx->vl_valid = 0;
     ParamsF& f = ctx->L.PF;
     for (int k = 0; k < 2; k++) {
         ctx->L.inv_tau[k] = 1.0 / p->tau[k];
@@ -406,6 +419,7 @@ int lb_add_colloids(lb_ctx* ctx, int n, const double* pos, const double* vel, co
     L.nc = first + n;
     L.rmax = rmax;
     ctx->all_fixed = fixed;
+    ctx->vl_valid = 0;
     // the FP32 snapshot first: the map kernel of the FP32 forms reads it
     int nl = launch_snapshot(L, s);
     nl += launch_map_initial(L, ctx->prec, first, n, s);
@@ -453,7 +467,8 @@ int lb_step(lb_ctx* ctx, int nsteps) {
         if (L.nc > 0) {  // Eqs. 26, 27 on the side stream, from r(t), v(t - 1/2)
             CK(cudaEventRecord(ctx->ev_fork, s), "fork event");
             CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0), "fork wait");
-            n += launch_pairs(L, ctx->cells, ctx->cells_bytes, ctx->side);
+            n += launch_pairs(L, ctx->cells, ctx->cells_bytes, !ctx->vl_valid, ctx->side);
+            ctx->vl_valid = 1;
             CK(cudaEventRecord(ctx->ev_join, ctx->side), "join event");
         }
         if (L.sr) L.sr_key = sr_key(ctx->sr_seed, ctx->sr_step++);
@@ -603,6 +618,15 @@ int lb_get_colloid_terms(lb_ctx* ctx, int which, double* out) {
 }
 
 long long lb_launch_count(const lb_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+long long lb_pair_list_builds(lb_ctx* ctx) {
+    if (!ctx) return -1;
+    unsigned long long b = 0;
+    if (cudaMemcpyAsync(&b, ctx->L.vl_builds, 8, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        return -1;
+    return (long long)b;
+}
 
 int lb_fused_kernel(const lb_ctx* ctx) {
     if (!ctx) return LB_ERR_ARG;

@@ -691,9 +691,11 @@ __device__ __forceinline__ int cell_coord(float x, float inv, int n) {
     return c < 0 ? 0 : (c >= n ? n - 1 : c);
 }
 
+// The cell list serves the pair-list build: the cell kernels do nothing in a
+// step that keeps the list (flag clear).
 __global__ void k_cells_count(Lattice L, CellGrid cg) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= L.nc) return;
+    if (p >= L.nc || !*L.vl_flag) return;
     int c0 = cell_coord(float(L.pos[3 * p]), cg.inv[0], cg.n[0]);
     int c1 = cell_coord(float(L.pos[3 * p + 1]), cg.inv[1], cg.n[1]);
     int c2 = cell_coord(float(L.pos[3 * p + 2]), cg.inv[2], cg.n[2]);
@@ -701,7 +703,8 @@ __global__ void k_cells_count(Lattice L, CellGrid cg) {
 }
 
 // exclusive scan of the counts (one block); counts are reset to serve as cursors
-__global__ void __launch_bounds__(1024) k_cells_scan(CellGrid cg) {
+__global__ void __launch_bounds__(1024) k_cells_scan(CellGrid cg, const int* flag) {
+    if (!*flag) return;
     __shared__ int part[1024];
     int nc = cg.n[0] * cg.n[1] * cg.n[2];
     int per = (nc + 1023) / 1024;
@@ -727,7 +730,7 @@ __global__ void __launch_bounds__(1024) k_cells_scan(CellGrid cg) {
 
 __global__ void k_cells_fill(Lattice L, CellGrid cg) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= L.nc) return;
+    if (p >= L.nc || !*L.vl_flag) return;
     int c0 = cell_coord(float(L.pos[3 * p]), cg.inv[0], cg.n[0]);
     int c1 = cell_coord(float(L.pos[3 * p + 1]), cg.inv[1], cg.n[1]);
     int c2 = cell_coord(float(L.pos[3 * p + 2]), cg.inv[2], cg.n[2]);
@@ -735,25 +738,42 @@ __global__ void k_cells_fill(Lattice L, CellGrid cg) {
     cg.items[cg.start[c] + atomicAdd(cg.count + c, 1)] = p;
 }
 
-constexpr int MAXCAND = 32;
-
-// Pair forces on particle i summed over j in index order (candidates within
-// the cut-off are found in the 27 neighbouring cells, or among all particles
-// when the grid has fewer than 3 cells along an axis, then sorted by j), plus
-// the soft side walls.
-__global__ void __launch_bounds__(128) k_pairs(Lattice L, CellGrid cg, int use_cells, float rc) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= L.nc) return;
-    double ri[3], vi[3];
+// Pair list (App. A rcut / delr): a particle's neighbours within the list
+// radius rl = max(rcut, interaction range) + delr, sorted by index, are kept
+// until some particle has moved more than delr / 2 since the build; the pair
+// forces then reach only listed pairs.  Every pair within the interaction
+// range at any step before the next build was within rl at the build.
+__global__ void k_pair_check(Lattice L, double half_skin) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.nc) return;
+    double d2 = 0.0;
     for (int d = 0; d < 3; d++) {
-        ri[d] = L.pos[3 * i + d];
-        vi[d] = L.vel[3 * i + d];
+        double dd = L.pos[3 * p + d] - L.vl_ref[3 * p + d];
+        if (L.per[d]) {
+            double Ld = (d == 0 ? L.nx : (d == 1 ? L.ny : L.nz));
+            dd -= Ld * floor(dd / Ld + 0.5);
+        }
+        d2 += dd * dd;
     }
-    double Ri = L.rad[i];
-    float rif[3] = {float(ri[0]), float(ri[1]), float(ri[2])};
+    if (!(d2 <= half_skin * half_skin)) atomicOr(L.vl_flag, 1);
+}
+
+// Build the list of particle i (when the flag is set): candidates from the 27
+// neighbouring cells, or among all particles when the grid has fewer than 3
+// cells along an axis; more than PAIR_LIST_MAX neighbours is reported as an
+// overlap.
+__global__ void __launch_bounds__(128) k_pair_list(Lattice L, CellGrid cg, int use_cells, float rl) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.nc || !*L.vl_flag) return;
+    if (i == 0) atomicAdd(L.vl_builds, 1ull);
+    float rif[3];
+    for (int d = 0; d < 3; d++) {
+        L.vl_ref[3 * i + d] = L.pos[3 * i + d];
+        rif[d] = float(L.pos[3 * i + d]);
+    }
     float Lf[3] = {float(L.nx), float(L.ny), float(L.nz)};
     float iLf[3] = {1.f / Lf[0], 1.f / Lf[1], 1.f / Lf[2]};
-    int cand[MAXCAND];
+    int* cand = L.vl_nb + (size_t)i * PAIR_LIST_MAX;
     int nc = 0;
     auto test = [&](int j) {
         if (j == i) return;
@@ -763,9 +783,9 @@ __global__ void __launch_bounds__(128) k_pairs(Lattice L, CellGrid cg, int use_c
             if (L.per[d]) df -= Lf[d] * rintf(df * iLf[d]);
             r2 += df * df;
         }
-        if (r2 >= rc * rc) return;
-        if (nc < MAXCAND) {
-            // insertion keeps the candidate list sorted by j
+        if (r2 >= rl * rl) return;
+        if (nc < PAIR_LIST_MAX) {
+            // insertion keeps the list sorted by j
             int q = nc++;
             while (q > 0 && cand[q - 1] > j) {
                 cand[q] = cand[q - 1];
@@ -776,7 +796,7 @@ __global__ void __launch_bounds__(128) k_pairs(Lattice L, CellGrid cg, int use_c
             atomicOr(L.flags, FLAG_OVERLAP);
         }
     };
-    if (rc > 0.f) {
+    if (rl > 0.f) {
         if (use_cells) {
             int c0 = cell_coord(rif[0], cg.inv[0], cg.n[0]);
             int c1 = cell_coord(rif[1], cg.inv[1], cg.n[1]);
@@ -800,11 +820,27 @@ __global__ void __launch_bounds__(128) k_pairs(Lattice L, CellGrid cg, int use_c
             for (int j = 0; j < L.nc; j++) test(j);
         }
     }
+    L.vl_cnt[i] = nc;
+}
+
+// Pair forces on particle i summed over its listed neighbours in index
+// order, plus the soft side walls.
+__global__ void __launch_bounds__(128) k_pairs(Lattice L) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.nc) return;
+    double ri[3], vi[3];
+    for (int d = 0; d < 3; d++) {
+        ri[d] = L.pos[3 * i + d];
+        vi[d] = L.vel[3 * i + d];
+    }
+    double Ri = L.rad[i];
     double nu = 0.5 * ((L.P.tau[0] - 0.5) / 3.0 + (L.P.tau[1] - 0.5) / 3.0);
     NSum acc[3] = {{0, 0}, {0, 0}, {0, 0}};
-    for (int q = 0; q < nc; q++) {
+    const int n = L.vl_cnt[i];
+    const int* nb = L.vl_nb + (size_t)i * PAIR_LIST_MAX;
+    for (int q = 0; q < n; q++) {
         double fo[3];
-        pair_force(L, i, cand[q], ri, Ri, vi, nu, fo);
+        pair_force(L, i, nb[q], ri, Ri, vi, nu, fo);
         for (int d = 0; d < 3; d++) acc[d].add(fo[d]);
     }
     if (!L.per[2] && L.P.side_wall_k != 0.0) {
@@ -955,17 +991,19 @@ int launch_virtual(const Lattice& L, int prec, int store_terms, cudaStream_t st)
     return 1;
 }
 
-int launch_pairs(const Lattice& L, void* cells, size_t cell_cap, cudaStream_t st) {
+int launch_pairs(const Lattice& L, void* cells, size_t cell_cap, bool force_build, cudaStream_t st) {
     if (L.nc <= 0) return 0;
+    // interaction range: Hertz contact, and lubrication up to 2 R_max + h_n
     double rc = L.P.hertz_K != 0.0 ? L.P.hertz_sigma : 0.0;
     if (L.P.lub_on) rc = fmax(rc, 2.0 * L.rmax + L.P.lub_hn);
-    float rcf = rc > 0.0 ? float(rc) + 0.05f : 0.f;
+    if (rc > 0.0) rc = fmax(rc, L.P.rcut);
+    float rl = rc > 0.0 ? float(rc + L.P.delr) + 0.05f : 0.f;
     CellGrid cg;
     int Ls[3] = {L.nx, L.ny, L.nz};
     long long ncell = 1;
-    int use_cells = rcf > 0.f && L.nc > 64;
+    int use_cells = rl > 0.f && L.nc > 64;
     for (int d = 0; d < 3; d++) {
-        int n = rcf > 0.f ? (int)(Ls[d] / rcf) : 1;
+        int n = rl > 0.f ? (int)(Ls[d] / rl) : 1;
         if (n > 64) n = 64;
         if (n < 3) use_cells = 0;
         cg.n[d] = n < 1 ? 1 : n;
@@ -977,15 +1015,24 @@ int launch_pairs(const Lattice& L, void* cells, size_t cell_cap, cudaStream_t st
     cg.count = (int*)cells;
     cg.start = cg.count + ncell;
     cg.items = cg.start + ncell + 1;
+    // rebuild flag: forced (new particles or parameters, or no skin), else
+    // set by the particles that moved more than delr / 2
+    const bool every_step = force_build || !(L.P.delr > 0.0);
+    cudaMemsetAsync(L.vl_flag, every_step ? 0xff : 0, sizeof(int), st);
+    if (!every_step) {
+        k_pair_check<<<(L.nc + 127) / 128, 128, 0, st>>>(L, 0.5 * L.P.delr);
+        n++;
+    }
     if (use_cells) {
         cudaMemsetAsync(cg.count, 0, ncell * sizeof(int), st);
         k_cells_count<<<(L.nc + 127) / 128, 128, 0, st>>>(L, cg);
-        k_cells_scan<<<1, 1024, 0, st>>>(cg);
+        k_cells_scan<<<1, 1024, 0, st>>>(cg, L.vl_flag);
         k_cells_fill<<<(L.nc + 127) / 128, 128, 0, st>>>(L, cg);
         n += 3;
     }
-    k_pairs<<<(L.nc + 127) / 128, 128, 0, st>>>(L, cg, use_cells, rcf);
-    return n + 1;
+    k_pair_list<<<(L.nc + 127) / 128, 128, 0, st>>>(L, cg, use_cells, rl);
+    k_pairs<<<(L.nc + 127) / 128, 128, 0, st>>>(L);
+    return n + 2;
 }
 
 int launch_integrate(const Lattice& L, cudaStream_t st) {

@@ -146,6 +146,14 @@ struct Lattice {
     // fixed-point sums of the per-site terms of one step (see acc_add):
     // [ACC_TERMS][maxc][3][2] words, zeroed at the start of each step
     unsigned long long* acc;
+    // particle pair list: [maxc][PAIR_LIST_MAX] neighbours sorted by index,
+    // their count, the positions at the last build, the rebuild flag and the
+    // count of builds
+    int* vl_nb;
+    int* vl_cnt;
+    double* vl_ref;
+    int* vl_flag;
+    unsigned long long* vl_builds;
     int maxc;
     int acc_wide;      // two-word sums (FP64 contexts)
     double rmax;       // largest particle radius
@@ -166,6 +174,7 @@ struct Lattice {
 };
 
 enum { FLAG_NONFINITE = 1, FLAG_OVERLAP = 2 };
+constexpr int PAIR_LIST_MAX = 32;  // listed neighbours per particle
 
 // node codes of the shared-memory planes of the streaming kernels: a fluid
 // node, a node beyond a wall, or the index (>= 0) of the particle that owns a
@@ -546,7 +555,7 @@ int launch_map_initial(const Lattice& L, int prec, int first, int count, cudaStr
 int launch_remap(const Lattice& L, int prec, int maxc, cudaStream_t st);
 int launch_virtual(const Lattice& L, int prec, int store_terms, cudaStream_t st);
 // Eqs. 26-27 and the side walls into Fpair (reads positions and velocities only)
-int launch_pairs(const Lattice& L, void* cells, size_t cell_cap, cudaStream_t st);
+int launch_pairs(const Lattice& L, void* cells, size_t cell_cap, bool force_build, cudaStream_t st);
 // Eqs. 28-35: totals, leap-frog, quaternions, snapshot
 int launch_integrate(const Lattice& L, cudaStream_t st);
 int launch_snapshot(const Lattice& L, cudaStream_t st);

@@ -33,7 +33,7 @@ EXPORTS = ["lb_workspace_bytes", "lb_create", "lb_set_params", "lb_init_fields",
            "lb_state_bytes",
            "lb_get_state", "lb_set_state", "lb_adjoint_bytes", "lb_adjoint_seed", "lb_adjoint_step",
            "lb_adjoint_initial", "lb_adjoint_step_async", "lb_drag_gradient", "lb_record", "lb_totals_static",
-           "lb_launch_count", "lb_fused_kernel", "lb_destroy", "lb_last_error"]
+           "lb_launch_count", "lb_pair_list_builds", "lb_fused_kernel", "lb_destroy", "lb_last_error"]
 
 
 class LbParams(C.Structure):
@@ -47,6 +47,7 @@ class LbParams(C.Structure):
         ("lub_hn", C.c_double), ("lub_hmin", C.c_double), ("lub_scale", C.c_double),
         ("side_wall_k", C.c_double), ("side_wall_d", C.c_double), ("rotate", C.c_int),
         ("janus", C.c_int), ("janus_theta0", C.c_double), ("janus_width", C.c_double),
+        ("rcut", C.c_double), ("delr", C.c_double),
     ]
 
 
@@ -98,6 +99,8 @@ def load(build_if_missing: bool = True):
     lib.lb_totals_static.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_longlong, P, D, P, P]
     lib.lb_launch_count.argtypes = [P]
     lib.lb_launch_count.restype = C.c_longlong
+    lib.lb_pair_list_builds.argtypes = [P]
+    lib.lb_pair_list_builds.restype = C.c_longlong
     lib.lb_fused_kernel.argtypes = [P]
     lib.lb_destroy.argtypes = [P]
     lib.lb_last_error.argtypes = [P]
@@ -322,6 +325,14 @@ def lb_launch_count(h) -> int:
     return int(load().lb_launch_count(h))
 
 
+def lb_pair_list_builds(h) -> int:
+    """Particle pair-list builds so far (synchronises the context's stream)."""
+    n = int(load().lb_pair_list_builds(h))
+    if n < 0:
+        raise LBError(LB_ERR_CUDA, "lb_pair_list_builds")
+    return n
+
+
 LB_FUSED_MOMENTUM, LB_FUSED_TWO_PASS, LB_FUSED_PLAIN = 1, 2, 3
 FUSED_KERNEL_NAMES = {LB_FUSED_MOMENTUM: "k_fused_warp", LB_FUSED_TWO_PASS: "k_fused_async",
                       LB_FUSED_PLAIN: "k_fused"}
@@ -420,6 +431,9 @@ class LBLattice:
 
     def launch_count(self):
         return lb_launch_count(self.h)
+
+    def pair_list_builds(self):
+        return lb_pair_list_builds(self.h)
 
     def profile(self, enable=True):
         lb_profile(self.h, enable)

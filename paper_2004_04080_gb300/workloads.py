@@ -128,6 +128,7 @@ def default_params() -> dict:
         lub_on=0, lub_hn=0.67, lub_hmin=0.5, lub_scale=0.1,
         side_wall_k=0.0, side_wall_d=0.0, rotate=1,
         janus=0, janus_theta0=108.0, janus_width=10.0,
+        rcut=0.0, delr=0.0,
     )
 
 
@@ -173,8 +174,18 @@ class Workload:
         pos = place_colloids(self.shape, self.n_colloids, R, self.seed + 1, sigma,
                              wall_gap=self.wall_gap)
         mass = self.particle_density * 4.0 / 3.0 * math.pi * R ** 3
-        return dict(pos=pos, radius=np.full(self.n_colloids, R),
-                    mass=np.full(self.n_colloids, mass))
+        out = dict(pos=pos, radius=np.full(self.n_colloids, R), mass=np.full(self.n_colloids, mass))
+        if self.params.get("janus"):
+            out["quat"] = random_orientations(self.n_colloids, self.seed + 3)
+        return out
+
+
+def random_orientations(n: int, seed: int) -> np.ndarray:
+    """n unit quaternions (w, x, y, z) uniform over the rotations: normalised
+    4-D standard normal draws (PCG64 with the given seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    q = rng.standard_normal((n, 4))
+    return q / np.linalg.norm(q, axis=1)[:, None]
 
 
 def n_for_fraction(shape, radius: float, phi: float) -> int:
@@ -235,6 +246,21 @@ def workload(name: str, scale: Optional[tuple] = None, calib: Optional[dict] = N
         w = Workload(name, shape, 5000, p, radius=5.0, n_colloids=n_for_fraction(shape, 5.0, 0.10), mean=1.0,
                      droplets=dict(n=64, radius=16.0, rich=float(calib["rho_rich"]),
                                    poor=float(calib["rho_poor"]), width=2.0, min_dist=2 * 16.0 + 6.0))
+    elif name == "janus_lub256":
+        # the colloid benchmark of Sec. 5.1 with the MD-room input of App. D:
+        # demixing mixture (density 1.0 per component with standard deviation
+        # 0.004: amp = 0.004 sqrt 3 for the uniform noise), G = 0.65; R = 5.5
+        # Janus particles (wettability angle 108 degrees, switch width 10,
+        # wetting constants 0.1 / 0.1) of mass 472 at random orientations,
+        # lubrication (0.1, 0.67, 0.5), Hertz (20, 12, 11), pair list with
+        # rcut 12 and skin delr 1; phi = 0.10 in a 256^3 periodic box
+        R = 5.5
+        p = dict(base, G=0.65, rho0=(1.0, 1.0), zeta=(0.1, 0.1), janus=1, janus_theta0=108.0,
+                 janus_width=10.0, lub_on=1, lub_scale=0.1, lub_hn=0.67, lub_hmin=0.5, hertz_K=20.0,
+                 hertz_sigma=12.0, hertz_rcap=11.0, rcut=12.0, delr=1.0)
+        shape = (256, 256, 256)
+        w = Workload(name, shape, 1000, p, radius=R, n_colloids=n_for_fraction(shape, R, 0.10), mean=1.0,
+                     amp=0.004 * math.sqrt(3.0), particle_density=472.0 / (4.0 / 3.0 * math.pi * R ** 3))
     else:
         raise KeyError(name)
     if scale is not None:

@@ -387,3 +387,70 @@ def test_particle_sums_repeat_bit_for_bit(prec):
         assert np.array_equal(c1[key], c2[key]), key
     assert np.array_equal(g1.populations(0), g2.populations(0))
     assert np.abs(g1.term("F_liq")).max() > 1e-4 and np.abs(g1.term("F_d")).max() > 0.0
+
+
+def test_pair_list_skin_keeps_the_forces_and_rebuilds_rarely():
+    """The particle pair list with a skin (App. A rcut, delr): lubrication
+    (Eq. 27) and Hertz contacts (Eq. 26) between 10 particles driven into
+    each other, 120 steps.  With delr = 1 the list is rebuilt only after a
+    particle has moved 1/2, yet the run is bit for bit the run that rebuilds
+    every step (delr = 0), and it matches the FP64 oracle, which evaluates
+    every pair."""
+    from paper_2004_04080_gb300.lbgb import LBLattice
+
+    shape = (56, 45, 39)
+    params = dict(G=0.3, tau=(0.9, 1.1), hertz_K=20.0, hertz_sigma=10.0, hertz_rcap=9.0, lub_on=1,
+                  lub_scale=0.1, lub_hn=0.67, lub_hmin=0.5, rcut=10.5)
+    rng = np.random.default_rng(8)
+    pos = [[8.0 + 11.5 * (i % 4) + rng.uniform(-1, 1), 10.0 + 24.0 * (i // 4 % 2) + rng.uniform(-1, 1),
+            10.0 + 18.0 * (i // 8) + rng.uniform(-1, 1)] for i in range(10)]
+    # pairs of neighbours along x driven towards each other
+    vel = [[0.03 if i % 2 == 0 else -0.03, rng.uniform(-0.01, 0.01), rng.uniform(-0.01, 0.01)] for i in range(10)]
+    # heavy enough that the fluid's drag leaves them moving for the whole run
+    col = dict(pos=pos, radius=4.5, mass=3000.0, vel=vel)
+    a, b = mixture_densities(shape, seed=31, amp=0.05)
+    steps = 120
+
+    def run(delr):
+        g = LBLattice(shape, "fp64", max_colloids=10)
+        g.set_params(**dict(params, delr=delr))
+        g.init_fields(a, b)
+        g.add_colloids(**col)
+        fmax = 0.0
+        for _ in range(steps // 10):
+            g.step(10)
+            fmax = max(fmax, np.abs(g.term("F_pair")).max())
+        return g, fmax
+
+    (g1, fmax), (g0, _) = run(1.0), run(0.0)
+    assert g0.pair_list_builds() == steps
+    assert 2 <= g1.pair_list_builds() <= steps // 6, g1.pair_list_builds()
+    for term in ("F_pair", "F_total", "T_total"):
+        assert np.array_equal(g1.term(term), g0.term(term)), term
+    c1, c0 = g1.get_colloids(), g0.get_colloids()
+    for key in ("pos", "vel", "omega", "quat"):
+        assert np.array_equal(c1[key], c0[key]), key
+    assert fmax > 1e-2  # contacts acted during the run
+    o = Oracle(*shape, 10)
+    o.set_params(**dict(params, delr=1.0))
+    o.init_fields(a, b)
+    o.add_colloids(**col)
+    o.radius = np.full(10, 4.5)
+    o.step(steps)
+    compare_fields(g1, o, 1e-12)
+    compare_colloids(g1, o, 1e-11)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_janus_lubrication_benchmark_physics(prec, tol):
+    """The colloid benchmark's physics (Sec. 5.1 with the App. D input):
+    demixing mixture, R = 5.5 Janus particles (108 +- 5 degrees, wetting
+    0.1 / 0.1) of mass 472 at random orientations, lubrication, Hertz
+    (20, 12, 11) and the pair list with rcut 12, delr 1, at phi = 0.10 in a
+    48 x 44 x 40 box (12 particles), 60 steps against the oracle."""
+    w = workload("janus_lub256", scale=(48, 44, 40))
+    c = w.colloids()
+    assert w.n_colloids == 12 and "quat" in c
+    g, o = run_both(w.shape, w.params, 60, prec, c, w.densities())
+    compare_fields(g, o, tol)
+    compare_colloids(g, o, tol)

@@ -324,6 +324,41 @@ def replica_mlups(ms_local, n_sites, steps, world, device=None):
     return world * n_sites * steps / (ms / 1e3) / 1e6, ms
 
 
+def case0_throughput(dev, torch, n=1024, steps=10):
+    """The paper's two-component benchmark without particles (Sec. 5.1,
+    two-component table, case 0): n^3 periodic sites, G = 0.65, density 1.0
+    per component with standard deviation 0.004 (uniform noise of the same
+    deviation, drawn per plane from PCG64), tau = 1, FP16 deviation storage
+    (the FP32 form of 1024^3 needs 326 GB).  GLUPS over `steps` timed steps
+    after 2 untimed ones, beside the paper's 1.37 GLUPS on 1024 cores."""
+    from paper_2004_04080_gb300.lbgb import LBLattice
+
+    N = n ** 3
+    amp = 0.004 * math.sqrt(3.0)
+    rhoA = torch.empty(N, dtype=torch.float64, pin_memory=True).numpy()
+    rhoB = torch.empty(N, dtype=torch.float64, pin_memory=True).numpy()
+    rng = np.random.Generator(np.random.PCG64(20040408))
+    plane = n * n
+    for z in range(n):
+        eta = rng.random(plane) * 2.0 - 1.0
+        rhoA[z * plane:(z + 1) * plane] = 1.0 + amp * eta
+        rhoB[z * plane:(z + 1) * plane] = 1.0 - amp * eta
+    lat = LBLattice((n, n, n), "fp16", max_colloids=0, device=dev)
+    lat.set_params(G=0.65, tau=(1.0, 1.0), rho0=(1.0, 1.0))
+    lat.init_fields(rhoA, rhoB)
+    del rhoA, rhoB
+    lat.step(2)
+    ms = time_steps(lat, steps, torch)
+    out = {"workload": "%d^3 periodic, two components, G = 0.65, rho = 1.0 + 1.0 (std 0.004), tau = 1, "
+                       "no particles, FP16 storage (stochastic rounding)" % n,
+           "steps": steps, "ms_per_step": round(ms / steps, 3), "glups": round(N * steps / (ms / 1e3) / 1e9, 3),
+           "kernel": lat.fused_kernel(),
+           "paper_glups": 1.37, "paper_case": "1024^3 case 0 on 1024 cores (Sec. 5.1 two-component table)"}
+    del lat
+    torch.cuda.empty_cache()
+    return out
+
+
 def time_steps(lat, steps, torch):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -347,6 +382,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/FP64 side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint / forward timing")
+    ap.add_argument("--no-case0", action="store_true",
+                    help="skip the 1024^3 two-component run without particles (about 210 GB of device memory)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args)
@@ -480,6 +517,10 @@ def main():
         if "fp16" in forms and args.prec == "fp32":
             forms["fp16_speedup_over_fp32"] = round(forms["fp16"]["mlups"] / value, 3)
 
+    case0 = None
+    if not args.no_case0 and world == 1:
+        case0 = case0_throughput(dev, torch)
+
     adjoint = None
     if not args.no_adjoint:
         adjoint = adjoint_timing(dev, torch)
@@ -493,7 +534,7 @@ def main():
                        "l2": "inputs larger than L2 (%.1f GB of populations)" % (
                            2 * 38 * N * {"fp64": 8, "fp32": 4, "fp16": 2}[args.prec] / 1e9)},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
-            "forms": forms, "adjoint": adjoint}
+            "forms": forms, "adjoint": adjoint, "paper_case0": case0}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:

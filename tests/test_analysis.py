@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 from paper_2004_04080_gb300 import analysis as an
 
@@ -60,3 +61,17 @@ def test_interface_crossings_of_flat_slabs_and_a_random_field():
     owner = np.where(rng.random(nx * ny * nz) < 0.2, 1, -1)
     phi = an.order_parameter(a, b, owner)
     assert an.interface_crossings(a, b, shape, owner) == _crossings_by_loops(phi, owner < 0, shape)
+
+
+@pytest.mark.gpu
+def test_study_drivers_run_small():
+    """The long-run study drivers on small boxes: the bijel's domain size grows
+    from the mixed start, and the sheared run switches the walls on."""
+    from paper_2004_04080_gb300 import studies
+
+    r = studies.bijel_arrest(n=48, steps=400, every=200)
+    Ls = [o["L"] for o in r["series"]]
+    assert r["particles"] > 0 and len(Ls) == 2 and Ls[1] > Ls[0] > 0
+    s = studies.sheared_bijel(shape=(96, 32, 32), equil=200, shear=200, every=100, wall_speed=0.01)
+    assert [o["step"] for o in s["series"]] == [100, 200, 300, 400]
+    assert all(o["L"] > 0 for o in s["series"])

@@ -97,6 +97,17 @@ typedef struct {
      * evaluated with their own cut-offs on the listed pairs, so rcut and
      * delr change the cost, never the result.  Both >= 0. */
     double rcut, delr;
+    /* Open z faces (Sec. 2.2; App. A open-boundary directives), with bc[2]
+     * = 0.  open[0] (z = -1/2) and open[1] (z = nz - 1/2): 0 a wall moving
+     * at wall_u (Eq. 9); 1 pressure: anti-bounce-back of Eq. 10 with the
+     * face density open_rho[face][k] and u_w the velocity of the boundary
+     * node (Eq. 14); 2 velocity: Eq. 9 with u_w = wall_u and the density of
+     * the boundary node (the wall rule); 3 equilibrium: the incoming
+     * populations are f^eq(open_rho[face][k], wall_u).  A pressure or
+     * equilibrium face carries open_rho into the Shan-Chen force of Eq. 11.
+     * The adjoint accepts walls and velocity faces only. */
+    int open[2];
+    double open_rho[2][2];
 } lb_params;
 
 /* Device workspace size for a lattice; *bytes receives the size.

@@ -140,6 +140,9 @@ typedef struct {
     int rotate;
     int janus;                         /* Janus wettability on/off          */
     double janus_theta0, janus_width;  /* switch centre and width, degrees  */
+    int open[2];                       /* z faces (lo, hi) with walls: 0 wall,
+                                          1 pressure, 2 velocity, 3 equilibrium */
+    double open_rho[2][2];             /* face density per component        */
 } orc_params;
 
 /* Neumaier compensated sum */
@@ -332,6 +335,8 @@ int orc_set_params(orc_t *o, const orc_params *p)
     if (!p->bc[0] || !p->bc[1])
         return ORC_ERR_ARG; /* walls only normal to z */
     if (p->janus && !(p->janus_width >= 0.0 && isfinite(p->janus_width) && isfinite(p->janus_theta0)))
+        return ORC_ERR_ARG;
+    if (p->open[0] < 0 || p->open[0] > 3 || p->open[1] < 0 || p->open[1] > 3)
         return ORC_ERR_ARG;
     o->P = *p;
     o->have_params = 1;
@@ -720,8 +725,13 @@ static void lb_forces(orc_t *o, int store_particle_terms)
                             num += WT[i] * o->rho[k][n];
                             den += WT[i];
                         }
-                        (side == 0 ? o->psi_lo : o->psi_hi)[k][x + (long)o->nx * y] =
-                            den > 0.0 ? num / den : 0.0;
+                        /* a pressure or equilibrium face: its density */
+                        if (o->P.open[side] == 1 || o->P.open[side] == 3)
+                            (side == 0 ? o->psi_lo : o->psi_hi)[k][x + (long)o->nx * y] =
+                                o->P.open_rho[side][k];
+                        else
+                            (side == 0 ? o->psi_lo : o->psi_hi)[k][x + (long)o->nx * y] =
+                                den > 0.0 ? num / den : 0.0;
                     }
                 }
     }
@@ -844,11 +854,33 @@ static void bounce_and_stream(orc_t *o)
                 for (k = 0; k < 2; k++)
                     o->fnext[k][i * N + n] = o->fpost[k][i * N + s];
             } else if (n < 0) {
-                const double *uw = (z + CZ[i] < 0) ? o->P.wall_u_lo : o->P.wall_u_hi;
+                const int side = z + CZ[i] < 0 ? 0 : 1;
+                const double *uw = side == 0 ? o->P.wall_u_lo : o->P.wall_u_hi;
+                const int type = o->P.open[side];
                 double cu = CX[i] * uw[0] + CY[i] * uw[1] + CZ[i] * uw[2];
-                for (k = 0; k < 2; k++)
-                    o->fnext[k][ib * N + s] =
-                        o->fpost[k][i * N + s] - 2.0 * WT[i] * o->rho[k][s] * cu / CS2;
+                if (type == 1) {
+                    /* pressure face (Eq. 10, anti-bounce-back): rho_w given,
+                     * u_w the velocity of the boundary node (Eq. 14) */
+                    double um[3], cum, uu;
+                    mix_velocity(o, s, um);
+                    cum = CX[i] * um[0] + CY[i] * um[1] + CZ[i] * um[2];
+                    uu = um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
+                    for (k = 0; k < 2; k++)
+                        o->fnext[k][ib * N + s] =
+                            -o->fpost[k][i * N + s] +
+                            2.0 * WT[i] * o->P.open_rho[side][k] *
+                                (1.0 + cum * cum / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
+                } else if (type == 3) {
+                    /* equilibrium face: the incoming population is
+                     * f^eq_ibar(rho_w, u_w) (Eq. 5) */
+                    for (k = 0; k < 2; k++)
+                        o->fnext[k][ib * N + s] = feq_i(ib, o->P.open_rho[side][k], uw);
+                } else {
+                    /* wall or velocity face (Eq. 9) */
+                    for (k = 0; k < 2; k++)
+                        o->fnext[k][ib * N + s] =
+                            o->fpost[k][i * N + s] - 2.0 * WT[i] * o->rho[k][s] * cu / CS2;
+                }
             } else {
                 double off[3], rel[3], uw[3], cu, fl = 0.0, fv[3], tq[3];
                 p = o->owner[n];

@@ -307,6 +307,14 @@ int lb_set_params(lb_ctx* ctx, const lb_params* p) {
         return set_err(ctx, LB_ERR_ARG, "janus needs a finite switch angle and a width >= 0");
     if (!(p->rcut >= 0.0 && isfinite(p->rcut) && p->delr >= 0.0 && isfinite(p->delr)))
         return set_err(ctx, LB_ERR_ARG, "rcut and delr must be finite and >= 0");
+    for (int f = 0; f < 2; f++) {
+        if (p->open[f] < 0 || p->open[f] > 3) return set_err(ctx, LB_ERR_ARG, "open face types are 0..3");
+        if (p->open[f] != 0 && p->bc[2] != 0)
+            return set_err(ctx, LB_ERR_ARG, "open faces need bc[2] = 0 (the z faces)");
+        for (int k = 0; k < 2; k++)
+            if (!(p->open_rho[f][k] >= 0.0 && isfinite(p->open_rho[f][k])))
+                return set_err(ctx, LB_ERR_ARG, "open face densities must be finite and >= 0");
+    }
     if (ctx->stepped && p->bc[2] != ctx->L.P.bc[2])
         return set_err(ctx, LB_ERR_STATE, "boundary conditions cannot change after stepping");
     ctx->L.P = *p;
@@ -680,6 +688,9 @@ static int adjoint_ready(lb_ctx* ctx) {
     if (ctx->L.sr)
         return set_err(ctx, LB_ERR_STATE, "stochastic rounding: recomputed forward steps would differ from the recorded ones");
     if (!ctx->all_fixed) return set_err(ctx, LB_ERR_STATE, "the adjoint needs immobile particles (infinite mass, at rest)");
+    for (int f = 0; f < 2; f++)
+        if (ctx->L.P.open[f] == 1 || ctx->L.P.open[f] == 3)
+            return set_err(ctx, LB_ERR_STATE, "the adjoint handles walls and velocity faces only");
     return LB_OK;
 }
 

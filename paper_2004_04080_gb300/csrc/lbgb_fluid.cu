@@ -109,8 +109,9 @@ __global__ void k_wall_psi(Lattice L) {
         den += w;
     }
     long long w = (long long)x + (long long)L.nx * y;
-    pw[(side * 2 + 0) * nxy + w] = den > C(0) ? num0 / den : C(0);
-    pw[(side * 2 + 1) * nxy + w] = den > C(0) ? num1 / den : C(0);
+    const bool face = L.P.open[side] == 1 || L.P.open[side] == 3;  // a pressure or equilibrium face
+    pw[(side * 2 + 0) * nxy + w] = face ? C(L.P.open_rho[side][0]) : (den > C(0) ? num0 / den : C(0));
+    pw[(side * 2 + 1) * nxy + w] = face ? C(L.P.open_rho[side][1]) : (den > C(0) ? num1 / den : C(0));
 }
 
 // Add the link force and torque of one site (Eqs. 22, 23) to the fixed-point
@@ -501,6 +502,40 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
     Tp[0] = rel[1] * Fl[2] - rel[2] * Fl[1];
     Tp[1] = rel[2] * Fl[0] - rel[0] * Fl[2];
     Tp[2] = rel[0] * Fl[1] - rel[1] * Fl[0];
+    // open z faces of the pressure (Eq. 10) or equilibrium kind: rewrite the
+    // populations the face sends in (the loop above stored the wall rule)
+    const int face = wall_lo ? 0 : (wall_hi ? 1 : -1);
+    if (face >= 0 && !solid && (L.P.open[face] == 1 || L.P.open[face] == 3)) {
+        const bool pressure = L.P.open[face] == 1;
+        const C* uw = V[face == 0 ? 0 : 2];
+        const C uwu = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
+#pragma unroll 1
+        for (int i = 1; i < Q; i++) {
+            if (cz(i) != (face == 0 ? -1 : 1)) continue;
+            C fb[2];
+            for (int k = 0; k < 2; k++) {
+                const C rw = C(L.P.open_rho[face][k]);
+                if (pressure) {
+                    // -f*_i + 2 w_i rho_w (1 + 9/2 (c_i.u)^2 - 3/2 u.u), u of this node
+                    C fsk;
+                    if (UNIT)
+                        fsk = feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
+                    else
+                        fsk = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
+                                          feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
+                              feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
+                    const C cuw = C(cx(i)) * u[0] + C(cy(i)) * u[1] + C(cz(i)) * u[2];
+                    fb[k] = -fsk + C(2) * wgt<C>(i) * rw * (C(1) + C(4.5) * cuw * cuw - C(1.5) * uu);
+                } else {
+                    fb[k] = feq<C>(opp(i), rw, uw[0], uw[1], uw[2], uwu);
+                }
+            }
+            const unsigned own = (unsigned)(SKEW + cx(i)) + s;  // element of s in plane opp(i)
+            put2((S*)(fnb + (unsigned long long)ps * (unsigned)(opp(i) * (int)sizeof(S))) + own,
+                 (S*)(fnb + (unsigned long long)ps * (unsigned)((Q + opp(i)) * (int)sizeof(S))) + own, fb[0], fb[1],
+                 pop_shift<S, C>(L, 0, opp(i)), pop_shift<S, C>(L, 1, opp(i)));
+        }
+    }
     if (multi) {
 #pragma unroll 1
         for (int i = 1; i < Q; i++) {

@@ -454,3 +454,33 @@ def test_janus_lubrication_benchmark_physics(prec, tol):
     g, o = run_both(w.shape, w.params, 60, prec, c, w.densities())
     compare_fields(g, o, tol)
     compare_colloids(g, o, tol)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("fp16", 1e-3)])
+@pytest.mark.parametrize("tau", [(1.0, 1.0), (0.8, 1.2)])
+def test_open_faces(prec, tol, tau):
+    """Open z faces (Sec. 2.2): an equilibrium inlet (rho_w, u_w) at z = -1/2
+    and a pressure outlet (Eq. 10) at z = nz - 1/2 on the demixing-capable
+    mixture, without particles (the plain fused kernel), 40 steps."""
+    shape = (24, 13, 17)
+    params = dict(G=0.6, tau=tau, bc=(1, 1, 0), open=(3, 1), wall_u_lo=(0.01, 0.0, 0.03),
+                  open_rho=(0.56, 0.46, 0.5, 0.5))
+    g, o = run_both(shape, params, 40, prec, dens=mixture_densities(shape, seed=41, amp=0.05))
+    compare_fields(g, o, tol)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("tau", [(1.0, 1.0), (0.8, 1.2)])
+def test_open_faces_with_particles(prec, tol, tau):
+    """Open z faces with moving particles (the momentum kernel at tau = 1, the
+    copy-pipelined one otherwise): a pressure face below, a velocity face
+    (Eq. 9) above, 40 steps."""
+    shape = (32, 21, 23)
+    params = dict(G=0.5, tau=tau, bc=(1, 1, 0), open=(1, 2), wall_u_hi=(0.02, 0.0, 0.0),
+                  open_rho=(0.52, 0.5, 0.5, 0.5), hertz_K=20, hertz_sigma=8.0, hertz_rcap=7.0,
+                  side_wall_k=0.5, side_wall_d=4.0)
+    col = dict(pos=[[8.2, 5.3, 7.7], [22.6, 14.1, 12.4]], radius=[3.5, 3.2], mass=[400.0, 350.0],
+               vel=[[0.02, 0.01, -0.01], [-0.01, 0.0, 0.02]], omega=[[0.0, 0.01, 0.0], [0.01, 0.0, 0.0]])
+    g, o = run_both(shape, params, 40, prec, col, mixture_densities(shape, seed=43, amp=0.05))
+    compare_fields(g, o, tol)
+    compare_colloids(g, o, tol)

@@ -1,0 +1,95 @@
+"""Pins of the oracle's open z faces (Sec. 2.2; App. A, the LB room's open
+boundary directives: 1 pressure / Dirichlet by anti-bounce-back, Eq. 10;
+2 velocity / Neumann, Eq. 9; 3 equilibrium), against what the lattice
+Boltzmann equations fix (CPU only):
+  * uniform plug flow f^eq(rho0, u0) between an equilibrium inlet
+    (rho0, u0) and a pressure outlet (rho0) is an exact fixed point: it pins
+    the signs of Eq. 10 and the reversed link of the equilibrium face;
+  * a fluid between two pressure faces of density rho_w relaxes to rho_w
+    (the face fixes the density) with a uniform velocity (nothing brakes a
+    plug flow between two pressure faces);
+  * a density drop between the faces drives fluid out of the dense face and
+    into the light one, and leaves the sites beyond the reach of the
+    populations exactly at rest;
+  * a velocity face is the moving wall of Eq. 9: bit for bit the wall run.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle, feq
+
+
+def plug(shape, tau, G, rho0, u0, steps):
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    o = Oracle(*shape)
+    o.set_params(tau=tau, G=G, rho0=rho0, bc=(1, 1, 0), open=(3, 1), wall_u_lo=u0,
+                 open_rho=(rho0[0], rho0[1], rho0[0], rho0[1]))
+    u = np.zeros((3, N))
+    u[:] = np.asarray(u0)[:, None]
+    o.init_fields(np.full(N, rho0[0]), np.full(N, rho0[1]), u)
+    f0 = [o.populations(k) for k in range(2)]
+    o.step(steps)
+    return o, f0
+
+
+@pytest.mark.parametrize("tau,G", [((1.0, 1.0), 0.0), ((0.8, 1.3), 0.4)])
+def test_plug_flow_is_a_fixed_point(tau, G):
+    o, f0 = plug((6, 5, 12), tau, G, (0.7, 0.45), (0.01, -0.02, 0.05), 25)
+    for k in range(2):
+        assert np.abs(o.populations(k) - f0[k]).max() < 1e-14
+
+
+def test_pressure_faces_fix_the_density():
+    shape = (4, 4, 16)
+    N = 4 * 4 * 16
+    o = Oracle(*shape)
+    o.set_params(tau=(1.0, 1.0), bc=(1, 1, 0), open=(1, 1), open_rho=(0.6, 0.4, 0.6, 0.4))
+    rng = np.random.default_rng(2)
+    o.init_fields(0.5 + 0.05 * rng.random(N), 0.3 + 0.05 * rng.random(N))
+    o.step(5000)
+    ra, rb, u = o.get_fields()
+    assert np.abs(ra - 0.6).max() < 1e-12 and np.abs(rb - 0.4).max() < 1e-12
+    # without walls nothing brakes the flow: the net momentum left by the
+    # relaxation stays as a uniform drift (plug flow at rho_w is a fixed point)
+    for d in range(3):
+        assert np.ptp(u[d]) < 1e-12
+
+
+def test_density_drop_drives_flow_downhill():
+    """Faces at rho 1.04 (z = 0) and 0.96 (z = nz - 1) over a fluid at 1.0 at
+    rest: after 10 steps fluid flows out of the dense face and into the light
+    one (u_z > 0 next to both), the face planes sit at the face densities,
+    and the planes more than 10 links from either face have not been reached
+    (a population moves one link per step): they are exactly at rest."""
+    shape = (4, 4, 24)
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    o = Oracle(*shape)
+    o.set_params(tau=(1.0, 1.0), bc=(1, 1, 0), open=(1, 1), open_rho=(0.52, 0.52, 0.48, 0.48))
+    o.init_fields(np.full(N, 0.5), np.full(N, 0.5))
+    o.step(10)
+    ra, rb, u = o.get_fields()
+    rho = (ra + rb).reshape(nz, ny, nx).mean(axis=(1, 2))
+    uz = u[2].reshape(nz, ny, nx).mean(axis=(1, 2))
+    assert np.all(uz[:3] > 0.01) and np.all(uz[-3:] > 0.01)
+    assert np.abs(u.reshape(3, nz, ny, nx)[:, 11:13]).max() == 0.0
+    assert abs(rho[0] - 1.04) < 1e-3 and abs(rho[-1] - 0.96) < 1e-3
+    assert np.abs(rho[11:13] - 1.0).max() < 1e-14
+
+
+def test_velocity_face_is_the_moving_wall():
+    shape = (5, 4, 9)
+    N = 5 * 4 * 9
+    rng = np.random.default_rng(3)
+    a, b = 0.5 + 0.02 * rng.random(N), 0.5 + 0.02 * rng.random(N)
+    runs = []
+    for face in (0, 2):
+        o = Oracle(*shape)
+        o.set_params(tau=(0.9, 1.1), G=0.5, bc=(1, 1, 0), open=(face, face), wall_u_lo=(0.02, 0, 0),
+                     wall_u_hi=(-0.01, 0.01, 0))
+        o.init_fields(a, b)
+        o.step(30)
+        runs.append([o.populations(k) for k in range(2)])
+    for k in range(2):
+        assert np.array_equal(runs[0][k], runs[1][k])

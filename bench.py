@@ -46,13 +46,14 @@ def alg_bytes(prec):
 def kernel_bytes(kname, prec):
     """Bytes per site that a lattice kernel itself must move (arrays touched
     once): the density pass reads the populations and the mask and writes
-    rho^k and j^k; the momentum kernel reads j^k, psi^k and the owner map and
-    writes the populations; the two-pass kernel reads both; the plain kernel
-    reads and writes the populations."""
+    rho^k, j^k and the 4-byte link classes; the lean momentum kernel reads
+    j^k, psi^k and the link classes and writes the populations; the
+    two-pass kernel reads both; the plain kernel reads and writes the
+    populations."""
     pops = 38 * STORE[prec]
     if kname == "k_density":
-        return pops + 1 + 8 * COMPUTE[prec]
-    if kname == "k_fused_warp":
+        return pops + 1 + 8 * COMPUTE[prec] + 4
+    if kname == "k_lean":
         return pops + 8 * COMPUTE[prec] + 4
     if kname == "k_fused_async":
         return 2 * pops + 2 * COMPUTE[prec] + 4
@@ -64,7 +65,8 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32-math"}
 STATED_ERROR = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 1e-3}
 # source of the lattice kernels (density pass, fused kernels) whose ncu DRAM
 # record profiles/ keeps: the record applies while this file is unchanged
-LATTICE_KERNEL_SRC = [os.path.join(ROOT, "paper_2004_04080_gb300", "csrc", "lbgb_fluid.cu")]
+LATTICE_KERNEL_SRC = [os.path.join(ROOT, "paper_2004_04080_gb300", "csrc", f)
+                      for f in ("lbgb_fluid.cu", "lbgb_colloid.cu")]
 
 
 def peaks():
@@ -438,9 +440,10 @@ def main():
     traffic = recorded_traffic(args.prec)
     # The lattice update of a time step (one read and one write of every
     # population: the method's algorithmic bytes) is done by the density pass
-    # and the fused kernel together when particles are present, by the fused
-    # kernel alone otherwise; frac is that pair's rate against the measured
-    # copy bandwidth, step_frac the same bytes over the whole step.
+    # and the lean kernel (with its small wall kernel) together when
+    # particles are present, by the fused kernel alone otherwise; frac is
+    # their rate against the measured copy bandwidth, step_frac the same
+    # bytes over the whole step.
     lattice_ms = kavg + davg
     achieved = alg / (lattice_ms / 1e3) / 1e9
     kernels = [{"kernel": kname, "ms": round(kavg, 4), "own_bytes_per_site": kernel_bytes(kname, args.prec),

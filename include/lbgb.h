@@ -175,15 +175,16 @@ int lb_get_owner(lb_ctx *ctx, int *out);
 
 /* Kernel timing.  While enabled, lb_step records a CUDA event pair on the
  * context stream around every launch of the fused lattice kernel (the
- * collide + Shan-Chen + bounce-back + stream kernel, the dominant one) and
- * around the full density pass that precedes it when particles are present
- * (see lb_fused_kernel).
+ * collide + Shan-Chen + stream + bounce-back kernel, the dominant one, with
+ * the small wall kernel that follows it in the lean form; LB_KERNEL_FUSED)
+ * and around the full density pass that precedes it when particles are
+ * present (LB_KERNEL_DENSITY; see lb_fused_kernel).
  * lb_profile(ctx, 1) enables and clears the records, lb_profile(ctx, 0)
  * disables them; lb_profile_read_kernel waits for the recorded events of one
- * kernel (LB_KERNEL_FUSED or LB_KERNEL_DENSITY; LB_ERR_ARG otherwise) and
- * returns its summed time (ms) and the number of timed launches (at most
- * 16384 are kept per record); lb_profile_read is the fused-kernel record. */
-enum { LB_KERNEL_FUSED = 0, LB_KERNEL_DENSITY = 1 };
+ * kernel kind (LB_ERR_ARG for another value) and returns its summed time
+ * (ms) and the number of timed launches (at most 16384 are kept per record);
+ * lb_profile_read is the fused-kernel record. */
+enum { LB_KERNEL_FUSED = 0, LB_KERNEL_DENSITY = 1, LB_KERNEL_KINDS = 2 };
 
 /* Rounding of the FP16 deviation storage (the precision forms; the paper
  * stores FP64).  LB_ROUND_STOCHASTIC (the default of an LB_FP16 context)
@@ -304,9 +305,12 @@ long long lb_pair_list_builds(lb_ctx *ctx);
  * (the sequence of Sec. 3.1 is the same for all; they differ in how the
  * moments and the Shan-Chen halo densities of Eq. 11 reach the collision):
  *  LB_FUSED_MOMENTUM  particles present, tau_A = tau_B = 1: a density pass
- *      writes rho^k and j^k of every node (Eqs. 6-7); the fused kernel
- *      collides from them (Eq. 16 at omega = 1), staging the halo of rho^k
- *      and of the node map in shared memory with asynchronous copies;
+ *      writes rho^k and j^k of every node (Eqs. 6-7) and the class of every
+ *      link (fluid-fluid, fluid-particle); the lean lattice kernel collides
+ *      every node from the moments (Eq. 16 at omega = 1), staging the halo
+ *      of rho^k in shared memory with asynchronous copies, pushes the links
+ *      and bounces those into particle nodes (Eqs. 17-19, 22, 23); a small
+ *      kernel then applies the rules of the z faces (Eqs. 9, 10);
  *  LB_FUSED_TWO_PASS  particles, other tau: a density pass writes rho^k, the
  *      fused kernel re-reads the populations;
  *  LB_FUSED_PLAIN     no particles: one pass, halo densities formed from the

@@ -62,16 +62,15 @@ struct lb_ctx {
     void* cells;
     size_t cells_bytes;
     int prof_on;
-    int prof_n;                 // recorded event pairs around the fused kernel
-    cudaEvent_t* prof_ev;       // 2 * PROF_MAX events, created on first use
-    int prof_nd;                // recorded event pairs around the density pass
-    cudaEvent_t* prof_evd;      // 2 * PROF_MAX events
+    int prof_n[LB_KERNEL_KINDS];           // recorded event pairs, by kernel (LB_KERNEL_*)
+    cudaEvent_t* prof_ev[LB_KERNEL_KINDS]; // 2 * PROF_MAX events each, created on first use
     char* rec_states;           // lb_record: f(t) of each recorded step, or null
     double* rec_forces;         // lb_record: F_liq after each recorded step, or null
     int rec_left, rec_i;        // steps still to record, steps recorded
     unsigned long long sr_seed; // stochastic rounding: seed, and steps taken with it
     unsigned long long sr_step;
     int vl_valid;               // the particle pair list holds the current particles
+    int nb_valid;               // the link classes match the node map up to this step's remap
     char err[512];
 };
 
@@ -94,7 +93,7 @@ const int RED_BLOCKS = 1024;
 const int PROF_MAX = 16384;
 
 struct Layout {
-    size_t f0, f1, mom, psi, psi_wall, mask, owner, evt, flags, col, prev, acc, vl, ipos, fsnap, cells,
+    size_t f0, f1, mom, psi, psi_wall, mask, owner, evt, nb, nb_chg, flags, col, prev, acc, vl, ipos, fsnap, cells,
         cells_bytes, red, totals, total;
     long long pstride;
 };
@@ -111,12 +110,14 @@ Layout layout(int nx, int ny, int nz, int prec, int maxc) {
     size_t fb1 = fb > (size_t)5 * N * 8 ? fb : (size_t)5 * N * 8;
     l.f0 = off; off = align_up(off + fb);
     l.f1 = off; off = align_up(off + fb1);
-    l.mom = off; off = align_up(off + (size_t)6 * l.pstride * compute_bytes(prec));
+    l.mom = off; off = align_up(off + (size_t)3 * l.pstride * compute_bytes(prec));
     l.psi = off; off = align_up(off + (size_t)2 * N * compute_bytes(prec));
     l.psi_wall = off; off = align_up(off + (size_t)4 * nx * ny * compute_bytes(prec));
     l.mask = off; off = align_up(off + (size_t)N);
     l.owner = off; off = align_up(off + (size_t)N * 4);
     l.evt = off; off = align_up(off + (size_t)N * 4);
+    l.nb = off; off = align_up(off + (size_t)N * 4);
+    l.nb_chg = off; off = align_up(off + (size_t)(8 + NB_CHG_CAP) * 4);
     l.flags = off; off = align_up(off + 64);
     int mc = maxc > 0 ? maxc : 1;
     l.col = off; off = align_up(off + (size_t)mc * DOUBLES_PER_PARTICLE * 8);
@@ -156,6 +157,15 @@ int cuda_check(lb_ctx* c, cudaError_t e, const char* what) {
         int rc_ = cuda_check(ctx, (call), what);         \
         if (rc_) return rc_;                             \
     } while (0)
+
+// the start (end = 0) or end (end = 1) event of one timed launch of a kernel
+// kind, while profiling is on and the record has room
+static int prof_mark(lb_ctx* ctx, int kind, int end, cudaStream_t s) {
+    if (!ctx->prof_on || ctx->prof_n[kind] >= PROF_MAX) return LB_OK;
+    CK(cudaEventRecord(ctx->prof_ev[kind][2 * ctx->prof_n[kind] + end], s), "profile event");
+    ctx->prof_n[kind] += end;
+    return LB_OK;
+}
 
 int launched(lb_ctx* ctx, int n, const char* what) {
     ctx->launches += n;
@@ -234,6 +244,8 @@ int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_worksp
     L.mask = (uint8_t*)(ctx->ws + l.mask);
     L.owner = (int*)(ctx->ws + l.owner);
     L.evt = (int*)(ctx->ws + l.evt);
+    L.nb = (uint32_t*)(ctx->ws + l.nb);
+    L.nb_chg = (int*)(ctx->ws + l.nb_chg);
     L.flags = (int*)(ctx->ws + l.flags);
     int mc = max_colloids > 0 ? max_colloids : 1;
     double* c = (double*)(ctx->ws + l.col);
@@ -354,6 +366,7 @@ int lb_init_fields(lb_ctx* ctx, const double* rhoA, const double* rhoB, const do
     L.nc = 0;
     ctx->all_fixed = 1;
     ctx->sr_step = 0;  // a new state starts the rounding sequence afresh
+    ctx->nb_valid = 0;
     int n = launch_clear_map(L, ctx->stream);
     n += launch_init_fields(L, ctx->prec, st, ctx->stream);
     int rc = launched(ctx, n, "init kernels");
@@ -428,6 +441,7 @@ int lb_add_colloids(lb_ctx* ctx, int n, const double* pos, const double* vel, co
     L.rmax = rmax;
     ctx->all_fixed = fixed;
     ctx->vl_valid = 0;
+    ctx->nb_valid = 0;
     // the FP32 snapshot first: the map kernel of the FP32 forms reads it
     int nl = launch_snapshot(L, s);
     nl += launch_map_initial(L, ctx->prec, first, n, s);
@@ -481,6 +495,10 @@ int lb_step(lb_ctx* ctx, int nsteps) {
         }
         if (L.sr) L.sr_key = sr_key(ctx->sr_seed, ctx->sr_step++);
         n += launch_remap(L, ctx->prec, ctx->maxc, s);  // destroy / create (Eqs. 24, 25)
+        if (L.nc > 0) {
+            n += launch_link_classes(L, !ctx->nb_valid, s);
+            ctx->nb_valid = 1;
+        }
         // rho^k (Eq. 6) of every fluid node when particles need virtual
         // densities (Eq. 20); with omega = 1 the pass also writes j^k, and
         // the fused kernel collides from the moments instead of re-reading the
@@ -490,26 +508,18 @@ int lb_step(lb_ctx* ctx, int nsteps) {
         L.dense_psi = L.nc > 0;
         L.dense_mom = L.dense_psi && unit;
         if (L.dense_psi) {
-            const bool timed_d = ctx->prof_on && ctx->prof_nd < PROF_MAX;
-            if (timed_d) CK(cudaEventRecord(ctx->prof_evd[2 * ctx->prof_nd], s), "profile event");
+            if (int rc = prof_mark(ctx, LB_KERNEL_DENSITY, 0, s)) return rc;
             n += launch_density(L, ctx->prec, s);
-            if (timed_d) {
-                CK(cudaEventRecord(ctx->prof_evd[2 * ctx->prof_nd + 1], s), "profile event");
-                ctx->prof_nd++;
-            }
+            if (int rc = prof_mark(ctx, LB_KERNEL_DENSITY, 1, s)) return rc;
         } else {
             n += launch_shell_density(L, ctx->prec, s);
         }
         n += launch_wall_psi(L, ctx->prec, s);         // wall densities
         n += launch_virtual(L, ctx->prec, 1, s);       // Eqs. 20, 21
-        bool timed = ctx->prof_on && ctx->prof_n < PROF_MAX;
-        if (timed) CK(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], s), "profile event");
+        if (int rc = prof_mark(ctx, LB_KERNEL_FUSED, 0, s)) return rc;
         // Eqs. 11, 14, 16, 3, 9, 17; the link forces of Eqs. 19, 22, 23
         n += launch_fluid_step(L, ctx->prec, s);
-        if (timed) {
-            CK(cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], s), "profile event");
-            ctx->prof_n++;
-        }
+        if (int rc = prof_mark(ctx, LB_KERNEL_FUSED, 1, s)) return rc;
         if (L.nc > 0) CK(cudaStreamWaitEvent(s, ctx->ev_join, 0), "join wait");
         n += launch_integrate(L, s);  // Eqs. 28-35
         int rc = launched(ctx, n, "step kernels");
@@ -810,24 +820,21 @@ static void destroy_events(cudaEvent_t*& ev) {
 
 int lb_profile(lb_ctx* ctx, int enable) {
     if (!ctx) return LB_ERR_ARG;
-    if (enable && !ctx->prof_ev) {
-        int rc = create_events(ctx, &ctx->prof_ev);
-        if (rc) return rc;
-    }
-    if (enable && !ctx->prof_evd) {
-        int rc = create_events(ctx, &ctx->prof_evd);
-        if (rc) return rc;
-    }
+    for (int k = 0; enable && k < LB_KERNEL_KINDS; k++)
+        if (!ctx->prof_ev[k]) {
+            int rc = create_events(ctx, &ctx->prof_ev[k]);
+            if (rc) return rc;
+        }
     ctx->prof_on = enable ? 1 : 0;
-    if (enable) ctx->prof_n = ctx->prof_nd = 0;
+    if (enable)
+        for (int k = 0; k < LB_KERNEL_KINDS; k++) ctx->prof_n[k] = 0;
     return LB_OK;
 }
 
 int lb_profile_read_kernel(lb_ctx* ctx, int kernel, double* total_ms, long long* launches) {
-    if (!ctx || !total_ms || !launches || (kernel != LB_KERNEL_FUSED && kernel != LB_KERNEL_DENSITY))
-        return LB_ERR_ARG;
-    const int n = kernel == LB_KERNEL_FUSED ? ctx->prof_n : ctx->prof_nd;
-    cudaEvent_t* ev = kernel == LB_KERNEL_FUSED ? ctx->prof_ev : ctx->prof_evd;
+    if (!ctx || !total_ms || !launches || kernel < 0 || kernel >= LB_KERNEL_KINDS) return LB_ERR_ARG;
+    const int n = ctx->prof_n[kernel];
+    cudaEvent_t* ev = ctx->prof_ev[kernel];
     double t = 0.0;
     for (int i = 0; i < n; i++) {
         float ms = 0.f;
@@ -848,8 +855,7 @@ int lb_destroy(lb_ctx* ctx) {
     if (!ctx) return LB_ERR_ARG;
     cudaStreamSynchronize(ctx->stream);
     destroy_side_stream(ctx);
-    destroy_events(ctx->prof_ev);
-    destroy_events(ctx->prof_evd);
+    for (int k = 0; k < LB_KERNEL_KINDS; k++) destroy_events(ctx->prof_ev[k]);
     delete ctx;
     return LB_OK;
 }

@@ -455,8 +455,75 @@ __global__ void __launch_bounds__(PB) k_remap_commit(Lattice L) {
             L.owner[s] = -1;
             L.mask[s] = 0;
             L.evt[s] = 0;
+        } else {
+            return;
         }
+        // list the node for the link classes around it
+        const int q = atomicAdd(L.nb_chg, 1);
+        if (q < NB_CHG_CAP) L.nb_chg[8 + q] = (int)s;
     });
+}
+
+// The link-class word of site s = (x, y, z) from the node map (NB_*).
+__device__ uint32_t link_classes(const Lattice& L, int x, int y, int z, long long s) {
+    const SiteNbr n = site_nbr(L, x, y, z);
+    const bool solid = L.mask[s] != 0;
+    uint32_t bits = 0, multi = 0;
+    int p0 = -1;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        if (nbr_is_wall(n, i)) continue;
+        const long long m = nbr_index(L, n, i);
+        const bool ms = L.mask[m] != 0;
+        bits |= (uint32_t)(ms != solid) << i;
+        if (!solid && ms) {
+            const int p = L.owner[m];
+            multi |= p0 >= 0 && p != p0 ? NB_MULTI : 0u;
+            p0 = p0 < 0 ? p : p0;
+        }
+    }
+    return bits | multi | (solid ? NB_SOLID : 0u);
+}
+
+// every site (grid: x chunks, y, z)
+__global__ void k_link_classes_all(Lattice L) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= L.nx) return;
+    const long long s = (long long)x + (long long)L.nx * ((long long)y + (long long)L.ny * z);
+    L.nb[s] = link_classes(L, x, y, z, s);
+}
+
+// The sites within one link of the nodes the remap changed (the map is
+// final): a site next to two changed nodes is rewritten with the same word
+// by both.  When more nodes changed than the list holds, every site.
+__global__ void k_link_classes_changed(Lattice L) {
+    const int cnt = *L.nb_chg;
+    const long long nt = (long long)gridDim.x * blockDim.x;
+    long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cnt > NB_CHG_CAP) {
+        for (long long s = t0; s < L.N; s += nt) {
+            const long long xy = (long long)L.nx * L.ny;
+            const int z = (int)(s / xy), r = (int)(s - (long long)z * xy), y = r / L.nx, x = r - y * L.nx;
+            L.nb[s] = link_classes(L, x, y, z, s);
+        }
+        return;
+    }
+    for (long long t = t0; t < (long long)cnt * Q; t += nt) {
+        const long long c = L.nb_chg[8 + t / Q];
+        const int i = (int)(t % Q);
+        const long long xy = (long long)L.nx * L.ny;
+        const int z = (int)(c / xy), r = (int)(c - (long long)z * xy), y = r / L.nx, x = r - y * L.nx;
+        const SiteNbr n = site_nbr(L, x, y, z);
+        if (i > 0 && nbr_is_wall(n, i)) continue;
+        int X = x, Y = y, Z = z;
+        if (i > 0) {
+            X = rc(0, i) > 0 ? n.xp : (rc(0, i) < 0 ? n.xm : x);
+            Y = rc(1, i) > 0 ? n.yp : (rc(1, i) < 0 ? n.ym : y);
+            Z = rc(2, i) > 0 ? n.zp : (rc(2, i) < 0 ? n.zm : z);
+        }
+        const long long s = (long long)X + (long long)L.nx * ((long long)Y + (long long)L.ny * Z);
+        L.nb[s] = link_classes(L, X, Y, Z, s);
+    }
 }
 
 // ------------------------------------------------------------ wetting
@@ -975,11 +1042,22 @@ int launch_remap(const Lattice& L, int prec, int maxc, cudaStream_t st) {
     // integrator turns them into F_liq, T_liq, F_d, T_d, F_c, T_c, F_s, T_s
     (void)maxc;
     cudaMemsetAsync(L.acc, 0, (size_t)ACC_TERMS * L.maxc * 6 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(L.nb_chg, 0, sizeof(int), st);
     const dim3 grid((unsigned)L.nc, REMAP_GROUPS);
     DISPATCHC(prec, (k_remap_classify<P><<<grid, PBLK, 0, st>>>(L)));
     DISPATCHC(prec, (k_remap_create<P><<<grid, PBLK, 0, st>>>(L)));
     DISPATCHC(prec, (k_remap_commit<P><<<grid, PBLK, 0, st>>>(L)));
     return 3;
+}
+
+int launch_link_classes(const Lattice& L, bool full, cudaStream_t st) {
+    if (full) {
+        const int bx = L.nx >= 128 ? 128 : ((L.nx + 31) / 32) * 32;
+        k_link_classes_all<<<dim3((unsigned)((L.nx + bx - 1) / bx), (unsigned)L.ny, (unsigned)L.nz), bx, 0, st>>>(L);
+    } else {
+        k_link_classes_changed<<<(unsigned)(4 * device_sms()), 256, 0, st>>>(L);
+    }
+    return 1;
 }
 
 int launch_virtual(const Lattice& L, int prec, int store_terms, cudaStream_t st) {

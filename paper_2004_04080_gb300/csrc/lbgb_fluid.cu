@@ -36,8 +36,9 @@ __global__ void k_init(Lattice L, const double* __restrict__ stage) {
 }
 
 // rho^k on fluid nodes (0 on particle nodes) into psi; flags non-finite or
-// negative densities.  MOM: also j^k (Eq. 7) into the momentum rows
-// mom[3k + d][s] (0 on particle nodes), for the omega = 1 collision.
+// negative densities.  MOM: also the total momentum j^A + j^B (Eq. 7) into
+// the rows mom[d][s] (0 on particle nodes), for the omega = 1 collision: with
+// tau_A = tau_B the mixture velocity (Eq. 14) needs only the sum.
 template <int PREC, bool MOM>
 __global__ void k_density(Lattice L) {
     typedef typename Prec<PREC>::S S;
@@ -51,11 +52,11 @@ __global__ void k_density(Lattice L) {
         psi[L.N + s] = 0;
         if (MOM)
 #pragma unroll
-            for (int a = 0; a < 6; a++) mom[a * L.pstride + s] = 0;
+            for (int a = 0; a < 3; a++) mom[a * L.pstride + s] = 0;
         return;
     }
     const S* f = (const S*)L.f_cur;
-    C rho[2];
+    C rho[2], jt[2][3];
 #pragma unroll
     for (int k = 0; k < 2; k++) {
         C r = 0, jx = 0, jy = 0, jz = 0;
@@ -71,12 +72,13 @@ __global__ void k_density(Lattice L) {
         }
         rho[k] = r;
         psi[k * L.N + s] = r;
-        if (MOM) {
-            mom[(3 * k + 0) * L.pstride + s] = jx;
-            mom[(3 * k + 1) * L.pstride + s] = jy;
-            mom[(3 * k + 2) * L.pstride + s] = jz;
-        }
+        jt[k][0] = jx;
+        jt[k][1] = jy;
+        jt[k][2] = jz;
     }
+    if (MOM)
+#pragma unroll
+        for (int d = 0; d < 3; d++) mom[d * L.pstride + s] = jt[0][d] + jt[1][d];
     if (!(rho[0] >= C(0) && rho[1] >= C(0) && rho[0] < C(1e30) && rho[1] < C(1e30)))
         atomicOr(L.flags, FLAG_NONFINITE);
 }
@@ -784,39 +786,233 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fu
 
 static int z_chunks(const Lattice& L, int tiles, int per_sm, int zmin);
 
-// ------------------------------------- warp-independent momentum step
-// The omega = 1 step of a lattice with particles (collision from the momenta
-// and densities of the density pass) with every warp on its own: a warp owns
-// one row of 32 sites and marches along z, staging with cp.async, into its
-// own shared memory, psi^k and the node codes of the three rows around its
-// own (y-1, y, y+1, each with the x ring), its momentum rows and the
-// records of the particles its sites bounce on.  Warps wait only for their own
-// copies (cp.async.wait_all + __syncwarp), so a warp slowed by particle work
-// holds no other; the price is that each psi row is staged by three warps
-// (reads that hit L2).
-constexpr int WNSLOT = 5;  // psi planes held: z-1 .. z+3
-constexpr int WPB = 4;     // warps (rows) per block
+constexpr int WNSLOT = 5;  // psi planes a lean warp holds: z-1 .. z+3
+constexpr int WPB = 4;     // warps (rows) per block of the lean kernel
 
+// ------------------------------------------------------- lean momentum kernel
+// With particles present and omega = 1 (tau^A = tau^B = 1), and the class of
+// every link kept with the node map (nb, NB_*), this kernel collides every
+// site from its moments (Eq. 16 at omega = 1, with the force of Eq. 11) and
+// pushes its links (Eq. 3) with no per-link decisions beyond a predicate:
+//   - a fluid site pushes all 19 links; a link into a particle node lands in
+//     that node's storage, which is never read as populations (the density
+//     pass gives particle nodes zero moments, and a node released by a
+//     particle is refilled (Eq. 25) before it streams);
+//   - a particle node collides on the rest density rho0^k (finite values)
+//     and pushes its links except those into fluid sites, whose elements
+//     the fluid sites' bounce-back fills;
+//   - a fluid site with links into particle nodes also writes, for each of
+//     them, f_ibar(x, t+1) = f*_i - 6 w_i rho^k c_i.u_w (Eqs. 17, 18) into its
+//     own element of plane opp(i), with f*_i still in registers, and sums the
+//     momentum the links hand over (Eqs. 19, 22, 23); the branch is taken per
+//     link only when some lane of the warp has that link;
+//   - a link across a wall plane wraps to the opposite face, where
+//     k_wall_bounce applies the face rules.
+// So every element of f(t+1) is written exactly once, by one store of a
+// warp-wide instruction (no sector is left partly written), and the per-site
+// code stays short: the fused march with per-link classification in shared
+// memory spent most of its issue slots there.
 template <int PREC>
-struct alignas(16) WarpShared {
+struct alignas(16) LeanShared {
     typedef typename Prec<PREC>::C C;
-    typedef typename std::conditional<sizeof(C) == 8, double, unsigned>::type PW;
-    static constexpr int NSLOT = WNSLOT;
-    static constexpr int PWORDS = sizeof(C) == 8 ? 9 : 12;
     C psi[WNSLOT][2][3][RW];
-    int nd[WNSLOT][3][RW];
-    alignas(16) C j[2][6][FTX];  // 16-byte copies land here
-    PW prec[2][PWORDS][FTX];
+    alignas(16) C j[2][3][FTX];  // j^A + j^B; 16-byte copies land here
 };
-static_assert(offsetof(WarpShared<LB_FP32>, j) % 16 == 0 && sizeof(WarpShared<LB_FP32>) % 16 == 0, "alignment");
-static_assert(offsetof(WarpShared<LB_FP64>, j) % 16 == 0 && sizeof(WarpShared<LB_FP64>) % 16 == 0, "alignment");
-static_assert(offsetof(WarpShared<LB_FP16>, j) % 16 == 0 && sizeof(WarpShared<LB_FP16>) % 16 == 0, "alignment");
+static_assert(offsetof(LeanShared<LB_FP32>, j) % 16 == 0 && sizeof(LeanShared<LB_FP32>) % 16 == 0, "alignment");
+static_assert(offsetof(LeanShared<LB_FP64>, j) % 16 == 0 && sizeof(LeanShared<LB_FP64>) % 16 == 0, "alignment");
 
+// Collide the site (x, y, z) of the warp's row and push its 19 links
+// (slots: psi planes z-1, z, z+1; b: the momentum buffer of plane z).
 template <int PREC, bool SR>
-__global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : 5)) k_fused_warp(Lattice L, int zc) {
+__device__ __forceinline__ void lean_site(const Lattice& L, const LeanShared<PREC>& sh, const int (&sl)[3], int x,
+                                          int y, int z, int b, uint32_t nbc) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
-    typedef WarpShared<PREC> SH;
+    const int tx = threadIdx.x;
+    const bool solid = nbc & NB_SOLID;
+    C rho[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) rho[k] = solid ? prm<C>(L.P.rho0[k], L.PF.rho0[k]) : sh.psi[sl[1]][k][1][tx + 1];
+    // Eq. 11 (repulsive sign) + body force from the staged psi planes
+    C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        const int slot = sl[cz(i) + 1];
+        const C pa = sh.psi[slot][0][1 + cy(i)][tx + 1 + cx(i)];
+        const C pb = sh.psi[slot][1][1 + cy(i)][tx + 1 + cx(i)];
+        const C w = wgt<C>(i);
+        if (cx(i)) { sA[0] += C(cx(i)) * w * pa; sB[0] += C(cx(i)) * w * pb; }
+        if (cy(i)) { sA[1] += C(cy(i)) * w * pa; sB[1] += C(cy(i)) * w * pb; }
+        if (cz(i)) { sA[2] += C(cz(i)) * w * pa; sB[2] += C(cz(i)) * w * pb; }
+    }
+    const C G = prm<C>(L.P.G, L.PF.G);
+    // Eq. 14 at tau_A = tau_B: u = (j^A + j^B) / (rho^A + rho^B) (j = 0 on
+    // particle nodes)
+    C us[2][3], u[3];
+    {
+        const C ir = C(1) / (rho[0] + rho[1]);
+#pragma unroll
+        for (int d = 0; d < 3; d++) u[d] = sh.j[b][d][tx] * ir;
+    }
+    const C tiny = sizeof(C) == 8 ? C(1e-300) : C(1e-30);
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const C ir = rho[k] > tiny ? C(1) / rho[k] : C(0);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const C g = prm<C>(L.P.body_force[d], L.PF.body_force[d]);
+            const C F = -G * rho[k] * (k == 0 ? sB[d] : sA[d]) + rho[k] * g;
+            us[k][d] = u[d] + F * ir;  // Eq. 16: the shifted velocity
+        }
+    }
+    // Eq. 5 factored per weight class c (0 rest, 1 axis, 2 diagonal):
+    // f^eq_i = A_c + c_i.us (B_c + H_c c_i.us), A_c = w_c rho (1 - 3/2 us.us),
+    // B_c = 3 w_c rho, H_c = 9/2 w_c rho
+    C A[2][3], B[2][3], H[2][3];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const C uus = us[k][0] * us[k][0] + us[k][1] * us[k][1] + us[k][2] * us[k][2];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const C wr = wgt<C>(c == 0 ? 0 : (c == 1 ? 1 : 7)) * rho[k];
+            A[k][c] = wr * (C(1) - C(1.5) * uus);
+            B[k][c] = C(3) * wr;
+            H[k][c] = C(4.5) * wr;
+        }
+    }
+    // destinations as 32-bit element offsets from the base of the plane pair
+    // (2j-1, 2j), plane 2j adding ps; the element of plane i at site q is
+    // SKEW + q - c_ix, so the shift by c_ix cancels and only the periodic
+    // wrap in x is left
+    const unsigned ps = (unsigned)L.pstride;
+    const int nx = L.nx, nxy = L.nx * L.ny;
+    const unsigned s = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)L.ny * (unsigned)z);
+    const int wxp = x == nx - 1 ? -nx : 0, wxm = x == 0 ? nx : 0;
+    const int dyp = y == L.ny - 1 ? nx - nxy : nx, dym = y == 0 ? nxy - nx : -nx;
+    const int dzp = z == L.nz - 1 ? nxy - (int)L.N : nxy, dzm = z == 0 ? (int)L.N - nxy : -nxy;
+    // site-index step to the neighbour along a link known at run time
+    auto step_of = [&](int i) {
+        const int a = rc(0, i), bb_ = rc(1, i), c = rc(2, i);
+        return (unsigned)((a > 0 ? 1 + wxp : (a < 0 ? wxm - 1 : 0)) + (bb_ > 0 ? dyp : (bb_ < 0 ? dym : 0)) +
+                          (c > 0 ? dzp : (c < 0 ? dzm : 0)));
+    };
+    // bounce-back links; a site next to two particles takes the general
+    // path after the loop
+    const unsigned bb = solid ? 0u : (nbc & NB_LINKS);
+    const unsigned bbi = (nbc & NB_MULTI) ? 0u : bb;
+    const unsigned wbb = __reduce_or_sync(__activemask(), bbi);  // the links any lane of the warp bounces
+    // the particle of the bounce-back links and u_w = v_p + omega_p x (x - r_p)
+    C U0[3] = {0, 0, 0}, rel[3] = {0, 0, 0};
+    int p0 = -1;
+    if (bbi) {
+        p0 = L.owner[s + step_of(__ffs(bbi) - 1)];
+        particle_u0_of<C>(L, particle_load<C>(L, p0), x, y, z, U0, rel);
+    }
+    C Fl[3] = {0, 0, 0};  // Eq. 19 summed over the links: (f*_i + f_ibar(t+1)) c_i
+    char* fnb = (char*)L.f_nxt;
+    unsigned rs = 0, rsb = 0;
+    if constexpr (SR) {
+        rs = sr_start(s, L.sr_key);
+        rsb = sr_start(s, L.sr_key ^ 0x6A09E667u);
+    }
+    auto put2 = [&](S* qa, S* qb, C va, C vb, C sa, C sb, bool on, unsigned& st) {
+        if constexpr (SR) {
+            const unsigned bits = sr_next2(st);
+            if (on) st_pop2_sr(qa, qb, va, vb, sa, sb, bits);
+        } else {
+            if (on) {
+                st_pop(qa, va, sa);
+                st_pop(qb, vb, sb);
+            }
+        }
+    };
+    put2((S*)fnb + (SKEW + s), (S*)(fnb + (unsigned long long)ps * (unsigned)(Q * (int)sizeof(S))) + (SKEW + s),
+         A[0][0], A[1][0], pop_shift<S, C>(L, 0, 0), pop_shift<S, C>(L, 1, 0), true, rs);
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        const int c = i <= 6 ? 1 : 2;
+        C fs[2];
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const C cu = C(cx(i)) * us[k][0] + C(cy(i)) * us[k][1] + C(cz(i)) * us[k][2];
+            fs[k] = A[k][c] + cu * (B[k][c] + H[k][c] * cu);
+        }
+        const int lo = (i & 1) ? i : i - 1;  // first plane of the pair
+        S* const pa = (S*)(fnb + (unsigned long long)ps * (unsigned)(lo * (int)sizeof(S)));
+        S* const pb = (S*)(fnb + (unsigned long long)ps * (unsigned)((Q + lo) * (int)sizeof(S)));
+        const unsigned off = (unsigned)SKEW + s + (unsigned)(cx(i) > 0 ? wxp : (cx(i) < 0 ? wxm : 0)) +
+                             (unsigned)(cy(i) > 0 ? dyp : (cy(i) < 0 ? dym : 0)) +
+                             (unsigned)(cz(i) > 0 ? dzp : (cz(i) < 0 ? dzm : 0)) + (i == lo ? 0u : ps);
+        // a particle node does not push into a fluid site (whose bounce-back
+        // writes that element)
+        put2(pa + off, pb + off, fs[0], fs[1], pop_shift<S, C>(L, 0, i), pop_shift<S, C>(L, 1, i),
+             !(solid && ((nbc >> i) & 1u)), rs);
+        if (wbb & (1u << i)) {
+            // Eq. 17 with the wall velocity of Eq. 18: the own element of
+            // plane opp(i), SKEW + s + c_ix
+            const bool on = (bbi >> i) & 1u;
+            const C cw = C(-2) * (C(cx(i)) * U0[0] + C(cy(i)) * U0[1] + C(cz(i)) * U0[2]);
+            C fb[2];
+#pragma unroll
+            for (int k = 0; k < 2; k++) fb[k] = fs[k] + B[k][c] * cw;
+            const unsigned ob = (unsigned)(SKEW + cx(i)) + s + (opp(i) == lo ? 0u : ps);
+            put2(pa + ob, pb + ob, fb[0], fb[1], pop_shift<S, C>(L, 0, opp(i)), pop_shift<S, C>(L, 1, opp(i)), on,
+                 rsb);
+            const C fl = on ? fs[0] + fb[0] + fs[1] + fb[1] : C(0);
+            if (cx(i)) Fl[0] += C(cx(i)) * fl;
+            if (cy(i)) Fl[1] += C(cy(i)) * fl;
+            if (cz(i)) Fl[2] += C(cz(i)) * fl;
+        }
+    }
+    if (bbi) {
+        // Eq. 23 with r_w - r_p = (x - r_p) + c_i/2: the c_i/2 part is
+        // parallel to the link force and drops out of the torque
+        const C Tp[3] = {rel[1] * Fl[2] - rel[2] * Fl[1], rel[2] * Fl[0] - rel[0] * Fl[2],
+                         rel[0] * Fl[1] - rel[1] * Fl[0]};
+        commit_link_forces<C>(L, p0, Fl, Tp);
+    }
+    if (bb && (nbc & NB_MULTI)) {
+        // a site next to two particles: each link with its own particle
+        unsigned m = bb;
+        while (m) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1;
+            const int p = L.owner[s + step_of(i)];
+            C U[3], r2[3];
+            particle_u0<C>(L, p, x, y, z, U, r2);
+            const int ax = rc(0, i), ay = rc(1, i), az = rc(2, i);
+            const int c = i <= 6 ? 1 : 2;
+            const C cw = C(-2) * (C(ax) * U[0] + C(ay) * U[1] + C(az) * U[2]);
+            C fs[2], fb[2];
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const C Ak = c == 1 ? A[k][1] : A[k][2], Bk = c == 1 ? B[k][1] : B[k][2];
+                const C Hk = c == 1 ? H[k][1] : H[k][2];
+                const C cu = C(ax) * us[k][0] + C(ay) * us[k][1] + C(az) * us[k][2];
+                fs[k] = Ak + cu * (Bk + Hk * cu);
+                fb[k] = fs[k] + Bk * cw;
+            }
+            const int o = opp(i);
+            S* f = (S*)L.f_nxt;
+            put2(f + pop_index(o, s, L.pstride), f + pop_index(Q + o, s, L.pstride), fb[0], fb[1],
+                 pop_shift<S, C>(L, 0, o), pop_shift<S, C>(L, 1, o), true, rsb);
+            const C fl = fs[0] + fb[0] + fs[1] + fb[1];
+            const C F2[3] = {C(ax) * fl, C(ay) * fl, C(az) * fl};
+            const C T2[3] = {r2[1] * F2[2] - r2[2] * F2[1], r2[2] * F2[0] - r2[0] * F2[2],
+                             r2[0] * F2[1] - r2[1] * F2[0]};
+            commit_link_forces<C>(L, p, F2, T2);
+        }
+    }
+}
+
+// One warp per row of 32 sites marching along z through a chunk of planes,
+// staging with cp.async (warps wait only for their own copies) psi^k of the
+// rows y-1, y, y+1 with the x ring for planes z-1 .. z+3 and the momentum
+// rows of the next plane; a plane beyond a wall stages the wall densities.
+template <int PREC, bool SR>
+__global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : 5)) k_lean(Lattice L, int zc) {
+    typedef typename Prec<PREC>::C C;
+    typedef LeanShared<PREC> SH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SH& sh = reinterpret_cast<SH*>(smem_raw)[threadIdx.y];
     const int tx = threadIdx.x;
@@ -855,11 +1051,9 @@ __global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : 5)) k_fused_w
             if (wall) {
                 sh.psi[slot][0][a][c] = pw[pxy[r]];
                 sh.psi[slot][1][a][c] = pw[nxy + pxy[r]];
-                sh.nd[slot][a][c] = ND_WALL;
                 continue;
             }
             const long long g = zoff + pxy[r];
-            cp_async_4(&sh.nd[slot][a][c], L.owner + g);
             if (sizeof(C) == 8) {
                 cp_async_8(&sh.psi[slot][0][a][c], psig + g);
                 cp_async_8(&sh.psi[slot][1][a][c], psig + L.N + g);
@@ -878,102 +1072,141 @@ __global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : 5)) k_fused_w
         if (!jcopy) return;
         const char* src = (const char*)L.mom + ((long long)row0 * L.pstride + (long long)(x0 + chunk * EPC) +
                                                 (long long)L.nx * y + nxy * p) * (long long)sizeof(C);
-        for (int r = row0; r < 6; r += RPP) {
+        for (int r = row0; r < 3; r += RPP) {
             cp_async_16(&sh.j[b][r][chunk * EPC], src);
             src += (long long)RPP * L.pstride * (long long)sizeof(C);
         }
-    };
-    auto prefetch = [&](int p, int b) {
-        int sl[3] = {slot_of(p - 1), slot_of(p), slot_of(p + 1)};
-        const LinkInfo li = link_info(sh, sl, tx, 0, sh.nd[slot_of(p)][1][tx + 1] != ND_FLUID);
-        if (act && li.pm) {
-            const int q = li.p0;
-            if (sizeof(C) == 8) {
-#pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    cp_async_8(&sh.prec[b][d][tx], L.pos + 3 * q + d);
-                    cp_async_8(&sh.prec[b][3 + d][tx], L.vel + 3 * q + d);
-                    cp_async_8(&sh.prec[b][6 + d][tx], L.omg + 3 * q + d);
-                }
-            } else {
-#pragma unroll
-                for (int d = 0; d < 3; d++) cp_async_4(&sh.prec[b][d][tx], L.ipos + 3 * q + d);
-#pragma unroll
-                for (int jj = 0; jj < 9; jj++) cp_async_4(&sh.prec[b][3 + jj][tx], L.fsnap + 9 * q + jj);
-            }
-        }
-        return li;
     };
     for (int p = z0 - 1; p < z0 + 3; p++)
         if (p <= z1) issue_psi(p);
     issue_mom(z0, 0);
     cp_async_commit();
-    cp_async_wait_all();
-    __syncwarp();
-    LinkInfo li_next = prefetch(z0, 0);
-    cp_async_commit();
+    const int x = x0 + tx;
+    const long long srow = act ? (long long)x + (long long)L.nx * y : 0;
+    uint32_t nbn = act ? L.nb[srow + nxy * z0] : 0u;
     for (int z = z0; z < z1; z++) {
         cp_async_wait_all();
         __syncwarp();
         const int b = (z - z0) & 1;
         if (z + 1 < z1) issue_mom(z + 1, b ^ 1);
         if (z + 3 <= z1) issue_psi(z + 3);
-        const LinkInfo li = li_next;
-        if (z + 1 < z1) li_next = prefetch(z + 1, b ^ 1);
         cp_async_commit();
+        const uint32_t nbc = nbn;
+        if (act && z + 1 < z1) nbn = L.nb[srow + nxy * (z + 1)];
         if (!act) continue;
-        const int mid = slot_of(z);
-        OwnSite<PREC> m;
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-            m.rho[k] = sh.psi[mid][k][1][tx + 1];
-#pragma unroll
-            for (int d = 0; d < 3; d++) m.j[k][d] = sh.j[b][3 * k + d][tx];
-        }
-        ParticleRef<C> pref;
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            if (sizeof(C) == 8) {
-                double q = (double)sh.prec[b][d][tx];
-                pref.ip[d] = (int)floor(q);
-                pref.fr[d] = C(q - (double)pref.ip[d]);
-                pref.v[d] = C((double)sh.prec[b][3 + d][tx]);
-                pref.w[d] = C((double)sh.prec[b][6 + d][tx]);
-            } else {
-                pref.ip[d] = (int)sh.prec[b][d][tx];
-                pref.fr[d] = C(__uint_as_float((unsigned)sh.prec[b][3 + d][tx]));
-                pref.v[d] = C(__uint_as_float((unsigned)sh.prec[b][6 + d][tx]));
-                pref.w[d] = C(__uint_as_float((unsigned)sh.prec[b][9 + d][tx]));
-            }
-        }
-        int sl[3] = {slot_of(z - 1), mid, slot_of(z + 1)};
-        int pf = -1;
-        C Fp[3] = {0, 0, 0}, Tp[3] = {0, 0, 0};
-        collide_site<PREC, true, SR>(L, sh, sl, x0 + tx, y, z, 0, m, sh.nd[mid][1][tx + 1] != ND_FLUID,
-                                 [&](int) { return (const S*)nullptr; }, li, pref, pf, Fp, Tp);
-        commit_link_forces<C>(L, pf, Fp, Tp);
+        const int sl[3] = {slot_of(z - 1), slot_of(z), slot_of(z + 1)};
+        lean_site<PREC, SR>(L, sh, sl, x, y, z, b, nbc);
     }
     cp_async_wait_all();
 }
 
 template <int P, bool SR>
-static int launch_fused_warp_t(const Lattice& L, cudaStream_t st) {
-    const size_t smem = sizeof(WarpShared<P>) * WPB;
-    const int per_sm = kernel_setup<k_fused_warp<P, SR>>(FTX * WPB, smem);
+static int launch_lean_t(const Lattice& L, cudaStream_t st) {
+    const size_t smem = sizeof(LeanShared<P>) * WPB;
+    const int per_sm = kernel_setup<k_lean<P, SR>>(FTX * WPB, smem);
     int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + WPB - 1) / WPB);
     int zc = z_chunks(L, tiles, per_sm, 8);
     dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + WPB - 1) / WPB, (L.nz + zc - 1) / zc);
-    k_fused_warp<P, SR><<<grid, dim3(FTX, WPB), smem, st>>>(L, zc);
+    k_lean<P, SR><<<grid, dim3(FTX, WPB), smem, st>>>(L, zc);
     return 1;
+}
+
+// The links across the z faces after the lean push.  The push of the link
+// c_i (c_iz = -1) of the bottom site b = (X, Y, 0) wrapped into the element
+// of plane i of the top site t = (X + c_ix, Y + c_iy, nz - 1), and the push of
+// opp(i) of t into the element of plane opp(i) of b: exactly the two elements
+// the face rules rewrite, so one thread per (b, i) reads both and writes both.
+// Rules by face type: wall or velocity face, Eq. 9 with the face velocity,
+// f_ibar = f*_i - 6 w_i rho^k c_i.u_w; pressure face, Eq. 10,
+// f_ibar = -f*_i + 2 w_i rho_w^k (1 + 9/2 (c_i.u)^2 - 3/2 u.u) with u the
+// mixture velocity of the node; equilibrium face, f^eq_ibar(rho_w^k, u_w).
+// rho^k and j^k of the node come from the density pass.  A particle node on a
+// face keeps what it holds.
+template <int PREC, bool SR>
+__device__ __forceinline__ void face_rule(const Lattice& L, int face, int i, const typename Prec<PREC>::C (&fs)[2],
+                                          long long x, unsigned& rs) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    const C* psi = (const C*)L.psi;
+    const C* mom = (const C*)L.mom;
+    const double* uwd = face == 0 ? L.P.wall_u_lo : L.P.wall_u_hi;
+    const float* uwf = face == 0 ? L.PF.wall_u_lo : L.PF.wall_u_hi;
+    const C uw[3] = {prm<C>(uwd[0], uwf[0]), prm<C>(uwd[1], uwf[1]), prm<C>(uwd[2], uwf[2])};
+    const int type = L.P.open[face];
+    C rho[2] = {psi[x], psi[L.N + x]};
+    C fb[2];
+    if (type == 1) {
+        // Eq. 14 at tau_A = tau_B from the total momentum of the density pass
+        C u[3];
+        const C ir = C(1) / (rho[0] + rho[1]);
+#pragma unroll
+        for (int d = 0; d < 3; d++) u[d] = mom[d * L.pstride + x] * ir;
+        const C uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const C cuw = C(cx(i)) * u[0] + C(cy(i)) * u[1] + C(cz(i)) * u[2];
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const C rw = C(L.P.open_rho[face][k]);
+            fb[k] = -fs[k] + C(2) * wgt<C>(i) * rw * (C(1) + C(4.5) * cuw * cuw - C(1.5) * uu);
+        }
+    } else if (type == 3) {
+        const C uwu = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
+#pragma unroll
+        for (int k = 0; k < 2; k++) fb[k] = feq<C>(opp(i), C(L.P.open_rho[face][k]), uw[0], uw[1], uw[2], uwu);
+    } else {
+        const C cw = C(-2) * (C(cx(i)) * uw[0] + C(cy(i)) * uw[1] + C(cz(i)) * uw[2]);
+#pragma unroll
+        for (int k = 0; k < 2; k++) fb[k] = fs[k] + C(3) * (wgt<C>(i) * rho[k]) * cw;
+    }
+    S* f = (S*)L.f_nxt;
+    S* qa = f + pop_index(opp(i), x, L.pstride);
+    S* qb = f + pop_index(Q + opp(i), x, L.pstride);
+    if constexpr (SR) {
+        st_pop2_sr(qa, qb, fb[0], fb[1], pop_shift<S, C>(L, 0, opp(i)), pop_shift<S, C>(L, 1, opp(i)),
+                   sr_next2(rs));
+    } else {
+        st_pop(qa, fb[0], pop_shift<S, C>(L, 0, opp(i)));
+        st_pop(qb, fb[1], pop_shift<S, C>(L, 1, opp(i)));
+    }
+}
+
+template <int PREC, bool SR>
+__global__ void k_wall_bounce(Lattice L) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y;
+    if (X >= L.nx) return;
+    const long long nxy = (long long)L.nx * L.ny;
+    const long long sb = (long long)X + (long long)L.nx * Y;
+    const bool fb_ = !L.mask[sb];
+    const S* f = (const S*)L.f_nxt;
+    unsigned rs = 0;
+    if constexpr (SR) rs = sr_start((unsigned)sb, L.sr_key ^ 0x2545F491u);
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        if (cz(i) != -1) continue;
+        int Xt = X + cx(i), Yt = Y + cy(i);
+        Xt = Xt < 0 ? Xt + L.nx : (Xt >= L.nx ? Xt - L.nx : Xt);
+        Yt = Yt < 0 ? Yt + L.ny : (Yt >= L.ny ? Yt - L.ny : Yt);
+        const long long stp = (long long)Xt + (long long)L.nx * Yt + nxy * (L.nz - 1);
+        C a[2], c[2];  // f*_i of b, f*_opp(i) of t
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            a[k] = ld_pop(f + pop_index(k * Q + i, stp, L.pstride), pop_shift<S, C>(L, k, i));
+            c[k] = ld_pop(f + pop_index(k * Q + opp(i), sb, L.pstride), pop_shift<S, C>(L, k, opp(i)));
+        }
+        if (fb_) face_rule<PREC, SR>(L, 0, i, a, sb, rs);
+        if (!L.mask[stp]) face_rule<PREC, SR>(L, 1, opp(i), c, stp, rs);
+    }
 }
 
 // the stochastic-rounding instantiations exist for the FP16 form only
 template <int P>
-static int launch_fused_warp(const Lattice& L, cudaStream_t st) {
+static int launch_lean(const Lattice& L, cudaStream_t st) {
     if constexpr (P == LB_FP16)
-        if (L.sr) return launch_fused_warp_t<P, true>(L, st);
-    return launch_fused_warp_t<P, false>(L, st);
+        if (L.sr) return launch_lean_t<P, true>(L, st);
+    return launch_lean_t<P, false>(L, st);
 }
+
 
 // rho^k of the fluid nodes in the planes next to the walls, written to psi
 template <int PREC>
@@ -1121,6 +1354,17 @@ int launch_density(const Lattice& L, int prec, cudaStream_t st) {
     return 1;
 }
 
+int launch_wall_bounce(const Lattice& L, int prec, cudaStream_t st) {
+    if (L.per[2] || !L.dense_mom) return 0;
+    dim3 g((unsigned)((L.nx + 127) / 128), (unsigned)L.ny);
+    if (prec == LB_FP16 && L.sr) {
+        k_wall_bounce<LB_FP16, true><<<g, 128, 0, st>>>(L);
+        return 1;
+    }
+    DISPATCH(prec, (k_wall_bounce<P, false><<<g, 128, 0, st>>>(L)));
+    return 1;
+}
+
 int launch_wall_psi(const Lattice& L, int prec, cudaStream_t st) {
     if (L.per[2]) return 0;
     dim3 g((unsigned)((L.nx + 127) / 128), (unsigned)L.ny, 2);
@@ -1168,7 +1412,7 @@ static int launch_fused_async(const Lattice& L, bool unit, cudaStream_t st) {
     // omega = 1: lb_step has the density pass write the momenta, and the
     // warp kernel collides from them; otherwise the general collision (exact
     // at omega = 1 as well: the non-equilibrium part is multiplied by 0)
-    if (unit && L.dense_mom) return launch_fused_warp<P>(L, st);
+    if (unit && L.dense_mom) return launch_lean<P>(L, st) + launch_wall_bounce(L, P, st);
     if constexpr (P == LB_FP16)
         if (L.sr) return launch_fused_async_t<P, false, true>(L, st);
     return launch_fused_async_t<P, false, false>(L, st);

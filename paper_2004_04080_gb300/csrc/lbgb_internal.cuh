@@ -31,6 +31,27 @@ __host__ __device__ constexpr int cz(int i) {
 }
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
+// The link vector of a link index known only at run time, from packed
+// 2-bit fields (c + 1 of links 0..18), without a table in memory.
+constexpr unsigned long long pack_c(int a) {
+    unsigned long long v = 0;
+    for (int i = 0; i < 19; i++)
+        v |= (unsigned long long)((a == 0 ? cx(i) : (a == 1 ? cy(i) : cz(i))) + 1) << (2 * i);
+    return v;
+}
+__device__ __forceinline__ int rc(int a, int i) {
+    const unsigned long long P = a == 0 ? pack_c(0) : (a == 1 ? pack_c(1) : pack_c(2));
+    return (int)((P >> (2 * i)) & 3ull) - 1;
+}
+
+// Link classes of a site (the word nb[s] the lean kernel reads, rebuilt
+// around every node the remap changes): bit 0 the site is a particle node;
+// bit i (1..18) the neighbour along c_i has the other kind (particle node
+// next to fluid), never across a wall; NB_MULTI on a fluid site whose
+// particle neighbours belong to more than one particle.
+constexpr uint32_t NB_SOLID = 1u, NB_LINKS = 0x7FFFEu, NB_MULTI = 1u << 19;
+constexpr int NB_CHG_CAP = 1 << 20;  // changed nodes listed per step (more: a full rebuild)
+
 // lattice weights w0 = 1/3, w1-6 = 1/18, w7-18 = 1/36
 template <typename C>
 __host__ __device__ constexpr C wgt(int i) {
@@ -136,6 +157,8 @@ struct Lattice {
     uint8_t* mask;     // 1 on particle nodes
     int* owner;        // -1 fluid, else particle index
     int* evt;          // remap events: 4 (p+1) + 1 destroy, 4 (p+1) + 2 create
+    uint32_t* nb;      // link classes of every site (NB_*), kept with the node map
+    int* nb_chg;       // [0] count of the nodes the remap changed, list from [8] (NB_CHG_CAP)
     int* flags;        // [0] error bits
     // particles (FP64, [n][3] / [n][4] / [n])
     int nc;
@@ -166,8 +189,8 @@ struct Lattice {
     double* red;       // reduction partials
     int red_blocks;
     int dense_psi;     // psi holds rho^k of every fluid node (a full density pass ran this step)
-    int dense_mom;     // that pass also wrote j^k into mom (omega = 1 collision on momenta)
-    void* mom;         // [6][pstride] of C: j^k_d of every site, row 3k + d
+    int dense_mom;     // that pass also wrote j^A + j^B into mom (omega = 1 collision on momenta)
+    void* mom;         // [3][pstride] of C: (j^A + j^B)_d of every site, row d
     int sr;            // FP16: stochastic rounding of the stores of the time step
     unsigned sr_key;   // this step's key of the rounding bits
     lb_params P;
@@ -543,6 +566,9 @@ inline int kernel_setup(int threads, size_t smem) {
 // kernel launchers (each returns the number of kernels it launched)
 int launch_init_fields(const Lattice& L, int prec, const double* stage, cudaStream_t st);
 int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st);
+// the links across the z faces after the lean push (with particles and
+// tau^A = tau^B = 1)
+int launch_wall_bounce(const Lattice& L, int prec, cudaStream_t st);
 int launch_shell_density(const Lattice& L, int prec, cudaStream_t st);
 int launch_density(const Lattice& L, int prec, cudaStream_t st);
 int launch_wall_psi(const Lattice& L, int prec, cudaStream_t st);
@@ -552,6 +578,9 @@ int launch_populations_out(const Lattice& L, int prec, int k, int i, double* sta
 int launch_clear_map(const Lattice& L, cudaStream_t st);
 
 int launch_map_initial(const Lattice& L, int prec, int first, int count, cudaStream_t st);
+// the link classes nb: of every site (full), or around the nodes the remap
+// of this step listed
+int launch_link_classes(const Lattice& L, bool full, cudaStream_t st);
 int launch_remap(const Lattice& L, int prec, int maxc, cudaStream_t st);
 int launch_virtual(const Lattice& L, int prec, int store_terms, cudaStream_t st);
 // Eqs. 26-27 and the side walls into Fpair (reads positions and velocities only)

@@ -335,7 +335,7 @@ def lb_pair_list_builds(h) -> int:
 
 
 LB_FUSED_MOMENTUM, LB_FUSED_TWO_PASS, LB_FUSED_PLAIN = 1, 2, 3
-FUSED_KERNEL_NAMES = {LB_FUSED_MOMENTUM: "k_fused_warp", LB_FUSED_TWO_PASS: "k_fused_async",
+FUSED_KERNEL_NAMES = {LB_FUSED_MOMENTUM: "k_lean", LB_FUSED_TWO_PASS: "k_fused_async",
                       LB_FUSED_PLAIN: "k_fused"}
 
 

@@ -246,7 +246,7 @@ def test_sheared_walls_with_particles(prec, tol, tol_u, nx):
     col = dict(pos=[[8.2, 5.3, 7.7], [22.6, 14.1, 11.4], [9.9, 16.2, 15.8], [25.1, 4.4, 16.0]],
                radius=5.5, mass=700.0)
     g, o = run_both(shape, params, 100, prec, col)
-    assert g.fused_kernel() == "k_fused_warp"
+    assert g.fused_kernel() == "k_lean"
     ga, gb, gu = g.get_fields()
     ra, rb, ru = o.get_fields()
     assert np.abs(ru).max() > 0.02
@@ -268,7 +268,7 @@ def test_momentum_kernel_runs_the_particle_workloads(prec):
     assert g.fused_kernel() == "k_fused"
     c = w.colloids()
     g.add_colloids(c["pos"], c["radius"], c["mass"])
-    assert g.fused_kernel() == "k_fused_warp"
+    assert g.fused_kernel() == "k_lean"
     g.set_params(**dict(w.params, tau=(0.8, 1.2)))
     assert g.fused_kernel() == "k_fused_async"
 

@@ -815,31 +815,44 @@ constexpr int WPB = 4;     // warps (rows) per block of the lean kernel
 template <int PREC>
 struct alignas(16) LeanShared {
     typedef typename Prec<PREC>::C C;
-    C psi[WNSLOT][2][3][RW];
+    C psi[WNSLOT][3][RW][2];     // psi^A, psi^B side by side: one shared load per neighbour
     alignas(16) C j[2][3][FTX];  // j^A + j^B; 16-byte copies land here
 };
 static_assert(offsetof(LeanShared<LB_FP32>, j) % 16 == 0 && sizeof(LeanShared<LB_FP32>) % 16 == 0, "alignment");
 static_assert(offsetof(LeanShared<LB_FP64>, j) % 16 == 0 && sizeof(LeanShared<LB_FP64>) % 16 == 0, "alignment");
 
+// The link forces and torques of one lane summed over the planes of its
+// march while they go to one particle p, added to p's fixed-point sums
+// (Eqs. 22, 23) when the particle changes and at the end of the march: a
+// particle spans several planes, so this saves most of the atomics.  The
+// order of the FP additions is fixed by the march, so the sums are the same
+// bits on every run.
+template <typename C>
+struct LinkSum {
+    int p;
+    C F[3], T[3];
+};
+
 // Collide the site (x, y, z) of the warp's row and push its 19 links
 // (slots: psi planes z-1, z, z+1; b: the momentum buffer of plane z).
-template <int PREC, bool SR>
+template <int PREC, bool SR, bool NEAR>
 __device__ __forceinline__ void lean_site(const Lattice& L, const LeanShared<PREC>& sh, const int (&sl)[3], int x,
-                                          int y, int z, int b, uint32_t nbc) {
+                                          int y, int z, int b, uint32_t nbc,
+                                          LinkSum<typename Prec<PREC>::C>& ls) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
     const int tx = threadIdx.x;
     const bool solid = nbc & NB_SOLID;
     C rho[2];
 #pragma unroll
-    for (int k = 0; k < 2; k++) rho[k] = solid ? prm<C>(L.P.rho0[k], L.PF.rho0[k]) : sh.psi[sl[1]][k][1][tx + 1];
+    for (int k = 0; k < 2; k++) rho[k] = solid ? prm<C>(L.P.rho0[k], L.PF.rho0[k]) : sh.psi[sl[1]][1][tx + 1][k];
     // Eq. 11 (repulsive sign) + body force from the staged psi planes
     C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 1; i < Q; i++) {
         const int slot = sl[cz(i) + 1];
-        const C pa = sh.psi[slot][0][1 + cy(i)][tx + 1 + cx(i)];
-        const C pb = sh.psi[slot][1][1 + cy(i)][tx + 1 + cx(i)];
+        const C pa = sh.psi[slot][1 + cy(i)][tx + 1 + cx(i)][0];
+        const C pb = sh.psi[slot][1 + cy(i)][tx + 1 + cx(i)][1];
         const C w = wgt<C>(i);
         if (cx(i)) { sA[0] += C(cx(i)) * w * pa; sB[0] += C(cx(i)) * w * pb; }
         if (cy(i)) { sA[1] += C(cy(i)) * w * pa; sB[1] += C(cy(i)) * w * pb; }
@@ -880,11 +893,14 @@ __device__ __forceinline__ void lean_site(const Lattice& L, const LeanShared<PRE
             H[k][c] = C(4.5) * wr;
         }
     }
-    // destinations as 32-bit element offsets from the base of the plane pair
-    // (2j-1, 2j), plane 2j adding ps; the element of plane i at site q is
-    // SKEW + q - c_ix, so the shift by c_ix cancels and only the periodic
-    // wrap in x is left
-    const unsigned ps = (unsigned)L.pstride;
+    // destinations as element offsets from the site's element of plane 0 of
+    // each component (pA, pB): the element of plane i at site q is
+    // i ps + SKEW + q - c_ix, so the shift by c_ix cancels and only the
+    // periodic wrap in x is left.  NEAR: the offsets fit in 32 bits
+    // ((Q - 1) ps + N < 2^31, checked by the launcher), so an address is one
+    // wide multiply-add from the site's pointer
+    typedef typename std::conditional<NEAR, int, long long>::type Off;
+    const Off ps = (Off)L.pstride;
     const int nx = L.nx, nxy = L.nx * L.ny;
     const unsigned s = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)L.ny * (unsigned)z);
     const int wxp = x == nx - 1 ? -nx : 0, wxm = x == 0 ? nx : 0;
@@ -909,25 +925,21 @@ __device__ __forceinline__ void lean_site(const Lattice& L, const LeanShared<PRE
         particle_u0_of<C>(L, particle_load<C>(L, p0), x, y, z, U0, rel);
     }
     C Fl[3] = {0, 0, 0};  // Eq. 19 summed over the links: (f*_i + f_ibar(t+1)) c_i
-    char* fnb = (char*)L.f_nxt;
-    unsigned rs = 0, rsb = 0;
-    if constexpr (SR) {
-        rs = sr_start(s, L.sr_key);
-        rsb = sr_start(s, L.sr_key ^ 0x6A09E667u);
-    }
+    S* const pA = (S*)L.f_nxt + (SKEW + (long long)s);
+    S* const pB = pA + (long long)Q * L.pstride;
+    // the rounding bits of the site's stores, in store order (the bounce-back
+    // stores of a link follow its push when the warp takes that branch)
+    unsigned rs = 0;
+    if constexpr (SR) rs = sr_start(s, L.sr_key);
     auto put2 = [&](S* qa, S* qb, C va, C vb, C sa, C sb, bool on, unsigned& st) {
         if constexpr (SR) {
-            const unsigned bits = sr_next2(st);
-            if (on) st_pop2_sr(qa, qb, va, vb, sa, sb, bits);
+            st_pop2_sr_if(qa, qb, va, vb, sa, sb, sr_next2(st), on);
         } else {
-            if (on) {
-                st_pop(qa, va, sa);
-                st_pop(qb, vb, sb);
-            }
+            st_pop_if(qa, va, sa, on);
+            st_pop_if(qb, vb, sb, on);
         }
     };
-    put2((S*)fnb + (SKEW + s), (S*)(fnb + (unsigned long long)ps * (unsigned)(Q * (int)sizeof(S))) + (SKEW + s),
-         A[0][0], A[1][0], pop_shift<S, C>(L, 0, 0), pop_shift<S, C>(L, 1, 0), true, rs);
+    put2(pA, pB, A[0][0], A[1][0], pop_shift<S, C>(L, 0, 0), pop_shift<S, C>(L, 1, 0), true, rs);
 #pragma unroll
     for (int i = 1; i < Q; i++) {
         const int c = i <= 6 ? 1 : 2;
@@ -937,27 +949,24 @@ __device__ __forceinline__ void lean_site(const Lattice& L, const LeanShared<PRE
             const C cu = C(cx(i)) * us[k][0] + C(cy(i)) * us[k][1] + C(cz(i)) * us[k][2];
             fs[k] = A[k][c] + cu * (B[k][c] + H[k][c] * cu);
         }
-        const int lo = (i & 1) ? i : i - 1;  // first plane of the pair
-        S* const pa = (S*)(fnb + (unsigned long long)ps * (unsigned)(lo * (int)sizeof(S)));
-        S* const pb = (S*)(fnb + (unsigned long long)ps * (unsigned)((Q + lo) * (int)sizeof(S)));
-        const unsigned off = (unsigned)SKEW + s + (unsigned)(cx(i) > 0 ? wxp : (cx(i) < 0 ? wxm : 0)) +
-                             (unsigned)(cy(i) > 0 ? dyp : (cy(i) < 0 ? dym : 0)) +
-                             (unsigned)(cz(i) > 0 ? dzp : (cz(i) < 0 ? dzm : 0)) + (i == lo ? 0u : ps);
+        const Off off = (Off)i * ps + (Off)((cx(i) > 0 ? wxp : (cx(i) < 0 ? wxm : 0)) +
+                                            (cy(i) > 0 ? dyp : (cy(i) < 0 ? dym : 0)) +
+                                            (cz(i) > 0 ? dzp : (cz(i) < 0 ? dzm : 0)));
         // a particle node does not push into a fluid site (whose bounce-back
         // writes that element)
-        put2(pa + off, pb + off, fs[0], fs[1], pop_shift<S, C>(L, 0, i), pop_shift<S, C>(L, 1, i),
+        put2(pA + off, pB + off, fs[0], fs[1], pop_shift<S, C>(L, 0, i), pop_shift<S, C>(L, 1, i),
              !(solid && ((nbc >> i) & 1u)), rs);
         if (wbb & (1u << i)) {
             // Eq. 17 with the wall velocity of Eq. 18: the own element of
-            // plane opp(i), SKEW + s + c_ix
+            // plane opp(i), opp(i) ps + SKEW + s + c_ix
             const bool on = (bbi >> i) & 1u;
             const C cw = C(-2) * (C(cx(i)) * U0[0] + C(cy(i)) * U0[1] + C(cz(i)) * U0[2]);
             C fb[2];
 #pragma unroll
             for (int k = 0; k < 2; k++) fb[k] = fs[k] + B[k][c] * cw;
-            const unsigned ob = (unsigned)(SKEW + cx(i)) + s + (opp(i) == lo ? 0u : ps);
-            put2(pa + ob, pb + ob, fb[0], fb[1], pop_shift<S, C>(L, 0, opp(i)), pop_shift<S, C>(L, 1, opp(i)), on,
-                 rsb);
+            const Off ob = (Off)opp(i) * ps + cx(i);
+            put2(pA + ob, pB + ob, fb[0], fb[1], pop_shift<S, C>(L, 0, opp(i)), pop_shift<S, C>(L, 1, opp(i)), on,
+                 rs);
             const C fl = on ? fs[0] + fb[0] + fs[1] + fb[1] : C(0);
             if (cx(i)) Fl[0] += C(cx(i)) * fl;
             if (cy(i)) Fl[1] += C(cy(i)) * fl;
@@ -967,9 +976,16 @@ __device__ __forceinline__ void lean_site(const Lattice& L, const LeanShared<PRE
     if (bbi) {
         // Eq. 23 with r_w - r_p = (x - r_p) + c_i/2: the c_i/2 part is
         // parallel to the link force and drops out of the torque
-        const C Tp[3] = {rel[1] * Fl[2] - rel[2] * Fl[1], rel[2] * Fl[0] - rel[0] * Fl[2],
-                         rel[0] * Fl[1] - rel[1] * Fl[0]};
-        commit_link_forces<C>(L, p0, Fl, Tp);
+        if (ls.p != p0) {
+            commit_link_forces<C>(L, ls.p, ls.F, ls.T);
+            ls = LinkSum<C>{p0, {0, 0, 0}, {0, 0, 0}};
+        }
+        ls.F[0] += Fl[0];
+        ls.F[1] += Fl[1];
+        ls.F[2] += Fl[2];
+        ls.T[0] += rel[1] * Fl[2] - rel[2] * Fl[1];
+        ls.T[1] += rel[2] * Fl[0] - rel[0] * Fl[2];
+        ls.T[2] += rel[0] * Fl[1] - rel[1] * Fl[0];
     }
     if (bb && (nbc & NB_MULTI)) {
         // a site next to two particles: each link with its own particle
@@ -995,7 +1011,7 @@ __device__ __forceinline__ void lean_site(const Lattice& L, const LeanShared<PRE
             const int o = opp(i);
             S* f = (S*)L.f_nxt;
             put2(f + pop_index(o, s, L.pstride), f + pop_index(Q + o, s, L.pstride), fb[0], fb[1],
-                 pop_shift<S, C>(L, 0, o), pop_shift<S, C>(L, 1, o), true, rsb);
+                 pop_shift<S, C>(L, 0, o), pop_shift<S, C>(L, 1, o), true, rs);
             const C fl = fs[0] + fb[0] + fs[1] + fb[1];
             const C F2[3] = {C(ax) * fl, C(ay) * fl, C(az) * fl};
             const C T2[3] = {r2[1] * F2[2] - r2[2] * F2[1], r2[2] * F2[0] - r2[0] * F2[2],
@@ -1009,8 +1025,8 @@ __device__ __forceinline__ void lean_site(const Lattice& L, const LeanShared<PRE
 // staging with cp.async (warps wait only for their own copies) psi^k of the
 // rows y-1, y, y+1 with the x ring for planes z-1 .. z+3 and the momentum
 // rows of the next plane; a plane beyond a wall stages the wall densities.
-template <int PREC, bool SR>
-__global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : 5)) k_lean(Lattice L, int zc) {
+template <int PREC, bool SR, bool NEAR>
+__global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : (SR ? 4 : 5))) k_lean(Lattice L, int zc) {
     typedef typename Prec<PREC>::C C;
     typedef LeanShared<PREC> SH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1049,17 +1065,17 @@ __global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : 5)) k_lean(La
             if (!pon[r]) continue;
             const int a = prow[r], c = pcol[r];
             if (wall) {
-                sh.psi[slot][0][a][c] = pw[pxy[r]];
-                sh.psi[slot][1][a][c] = pw[nxy + pxy[r]];
+                sh.psi[slot][a][c][0] = pw[pxy[r]];
+                sh.psi[slot][a][c][1] = pw[nxy + pxy[r]];
                 continue;
             }
             const long long g = zoff + pxy[r];
             if (sizeof(C) == 8) {
-                cp_async_8(&sh.psi[slot][0][a][c], psig + g);
-                cp_async_8(&sh.psi[slot][1][a][c], psig + L.N + g);
+                cp_async_8(&sh.psi[slot][a][c][0], psig + g);
+                cp_async_8(&sh.psi[slot][a][c][1], psig + L.N + g);
             } else {
-                cp_async_4(&sh.psi[slot][0][a][c], psig + g);
-                cp_async_4(&sh.psi[slot][1][a][c], psig + L.N + g);
+                cp_async_4(&sh.psi[slot][a][c][0], psig + g);
+                cp_async_4(&sh.psi[slot][a][c][1], psig + L.N + g);
             }
         }
     };
@@ -1084,6 +1100,7 @@ __global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : 5)) k_lean(La
     const int x = x0 + tx;
     const long long srow = act ? (long long)x + (long long)L.nx * y : 0;
     uint32_t nbn = act ? L.nb[srow + nxy * z0] : 0u;
+    LinkSum<C> ls = {-1, {0, 0, 0}, {0, 0, 0}};
     for (int z = z0; z < z1; z++) {
         cp_async_wait_all();
         __syncwarp();
@@ -1095,20 +1112,28 @@ __global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : 5)) k_lean(La
         if (act && z + 1 < z1) nbn = L.nb[srow + nxy * (z + 1)];
         if (!act) continue;
         const int sl[3] = {slot_of(z - 1), slot_of(z), slot_of(z + 1)};
-        lean_site<PREC, SR>(L, sh, sl, x, y, z, b, nbc);
+        lean_site<PREC, SR, NEAR>(L, sh, sl, x, y, z, b, nbc, ls);
     }
+    commit_link_forces<C>(L, ls.p, ls.F, ls.T);
     cp_async_wait_all();
 }
 
-template <int P, bool SR>
+template <int P, bool SR, bool NEAR>
 static int launch_lean_t(const Lattice& L, cudaStream_t st) {
     const size_t smem = sizeof(LeanShared<P>) * WPB;
-    const int per_sm = kernel_setup<k_lean<P, SR>>(FTX * WPB, smem);
+    const int per_sm = kernel_setup<k_lean<P, SR, NEAR>>(FTX * WPB, smem);
     int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + WPB - 1) / WPB);
     int zc = z_chunks(L, tiles, per_sm, 8);
     dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + WPB - 1) / WPB, (L.nz + zc - 1) / zc);
-    k_lean<P, SR><<<grid, dim3(FTX, WPB), smem, st>>>(L, zc);
+    k_lean<P, SR, NEAR><<<grid, dim3(FTX, WPB), smem, st>>>(L, zc);
     return 1;
+}
+
+template <int P, bool SR>
+static int launch_lean_n(const Lattice& L, cudaStream_t st) {
+    // the element offsets of a site's links from its plane-0 element
+    if ((long long)(Q - 1) * L.pstride + L.N + 2 * SKEW < (1LL << 31)) return launch_lean_t<P, SR, true>(L, st);
+    return launch_lean_t<P, SR, false>(L, st);
 }
 
 // The links across the z faces after the lean push.  The push of the link
@@ -1203,8 +1228,8 @@ __global__ void k_wall_bounce(Lattice L) {
 template <int P>
 static int launch_lean(const Lattice& L, cudaStream_t st) {
     if constexpr (P == LB_FP16)
-        if (L.sr) return launch_lean_t<P, true>(L, st);
-    return launch_lean_t<P, false>(L, st);
+        if (L.sr) return launch_lean_n<P, true>(L, st);
+    return launch_lean_n<P, false>(L, st);
 }
 
 

@@ -93,6 +93,23 @@ __device__ __forceinline__ void st_pop(__half* p, float v, float shift) {
     *p = __float2half_rn(v - shift);
 }
 
+// The same stores under a per-lane predicate, as predicated store
+// instructions (a branch around a store diverges the warp and costs
+// reconvergence instructions in every unrolled link).
+__device__ __forceinline__ void st_pop_if(double* p, double v, double, bool on) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.f64 [%0], %1;\n\t}" ::"l"(p), "d"(v),
+                 "r"((unsigned)on));
+}
+__device__ __forceinline__ void st_pop_if(float* p, float v, float, bool on) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.f32 [%0], %1;\n\t}" ::"l"(p), "f"(v),
+                 "r"((unsigned)on));
+}
+__device__ __forceinline__ void st_pop_if(__half* p, float v, float shift, bool on) {
+    const unsigned short h = __half_as_ushort(__float2half_rn(v - shift));
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.b16 [%0], %1;\n\t}" ::"l"(p), "h"(h),
+                 "r"((unsigned)on));
+}
+
 // Stochastic rounding of the FP16 deviation stores.  The two components of
 // a link are converted together by the hardware's stochastic-rounding
 // conversion to a pair of halves (cvt.rs.f16x2.f32: component A in the upper
@@ -127,6 +144,16 @@ __device__ __forceinline__ void st_pop2_sr(__half* pa, __half* pb, float va, flo
     asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(va - sa), "f"(vb - sb), "r"(bits));
     *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(d >> 16);
     *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(d & 0xffffu);
+}
+__device__ __forceinline__ void st_pop2_sr_if(__half* pa, __half* pb, float va, float vb, float sa, float sb,
+                                              unsigned bits, bool on) {
+    unsigned d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(va - sa), "f"(vb - sb), "r"(bits));
+    const unsigned short a = (unsigned short)(d >> 16), b = (unsigned short)(d & 0xffffu);
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %4, 0;\n\t@q st.global.b16 [%0], %2;\n\t@q st.global.b16 [%1], "
+        "%3;\n\t}" ::"l"(pa),
+        "l"(pb), "h"(a), "h"(b), "r"((unsigned)on));
 }
 
 // ------------------------------------------------------------- context

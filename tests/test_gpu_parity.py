@@ -65,11 +65,16 @@ def compare_fields(g, o, tol, u_scale=1.0):
     return ea, eb, eu
 
 
-def compare_colloids(g, o, tol, term_tol=None):
+def compare_colloids(g, o, tol, term_tol=None, event_mom=0.0):
     """Particle state absolute; the force and torque terms absolute, or with
     ``term_tol`` relative to each term's largest value, floored at one
     lattice momentum unit for a force and at R_max such units for a torque
-    (the lever arm of the link forces)."""
+    (the lever arm of the link forces).  ``event_mom`` is the momentum of one
+    node refill (Eq. 25) that the terms holding the refills (F_c and the
+    totals) may differ by in addition: a refill is a discrete event, and a
+    state that carries the error of a reduced-precision form can create a node
+    one step earlier or later than the oracle, which moves that node's whole
+    momentum from one step's F_c to the next one's."""
     gc, rc = g.get_colloids(), o.get_colloids()
     for key in ("pos", "vel", "omega", "quat"):
         err = np.abs(gc[key] - rc[key]).max()
@@ -82,7 +87,22 @@ def compare_colloids(g, o, tol, term_tol=None):
             assert err < tol, (term, err)
         else:
             floor = rmax if term.startswith("T") else 1.0
-            assert err / max(np.abs(ref).max(), floor) < term_tol, (term, err)
+            event = 0.0
+            if term in ("F_c", "F_total"):
+                event = event_mom
+            elif term == "T_total":
+                event = rmax * event_mom
+            assert (err - event) / max(np.abs(ref).max(), floor) < term_tol, (term, err, event)
+
+
+def refill_momentum(o):
+    """Momentum of one created node (Eq. 25), bounded from the oracle's state:
+    the largest total density of the lattice times the fastest surface speed
+    |v_p| + |omega_p| R_p of a particle."""
+    ra, rb, _ = o.get_fields()
+    c = o.get_colloids()
+    speed = np.linalg.norm(c["vel"], axis=1) + np.linalg.norm(c["omega"], axis=1) * np.asarray(o.radius)
+    return float((ra + rb).max() * speed.max())
 
 
 def test_fp64_small_workload_100_steps():
@@ -185,12 +205,16 @@ def test_reduced_precision_demixing_droplets(prec, tol, term_tol):
     nearly balanced by F_s); in FP16 storage they are sums over the ~300
     links of a particle of terms of the fields, which carry the 1e-3 error of
     the form, and are compared relative to their scale at 1e-2 (measured: 1e-3
-    for F_liq, 3e-3 for T_liq with the lever-arm floor)."""
+    for F_liq, 4e-3 for T_liq with the lever-arm floor).  In FP16 the refill
+    term F_c at the compared step differs from the oracle's by one node's
+    momentum in about half of the rounding seeds (measured 8.9e-3 against
+    3e-5 otherwise): a node created one step apart; that event is allowed
+    on F_c and the totals (refill_momentum)."""
     shape = (44, 38, 34)
     params, dens, col = pickering_like(shape)
     g, o = run_both(shape, params, 60, prec, col, dens=dens)
     compare_fields(g, o, tol)
-    compare_colloids(g, o, tol, term_tol)
+    compare_colloids(g, o, tol, term_tol, event_mom=refill_momentum(o) if prec == "fp16" else 0.0)
 
 
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 1e-3)])

@@ -101,7 +101,8 @@ struct Layout {
 Layout layout(int nx, int ny, int nz, int prec, int maxc) {
     Layout l;
     long long N = (long long)nx * ny * nz;
-    // population planes: SKEW elements of padding at both ends (pop_index)
+    // population planes: pstride component pairs each, SKEW pairs of padding
+    // at both ends (pop_index)
     l.pstride = (N + 2 * SKEW + 63) / 64 * 64;
     size_t off = 0;
     size_t fb = (size_t)2 * Q * l.pstride * storage_bytes(prec);

@@ -56,26 +56,23 @@ __global__ void k_density(Lattice L) {
         return;
     }
     const S* f = (const S*)L.f_cur;
-    C rho[2], jt[2][3];
+    C rho[2] = {0, 0}, jt[2][3] = {{0, 0, 0}, {0, 0, 0}};
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
-        C r = 0, jx = 0, jy = 0, jz = 0;
+    for (int i = 0; i < Q; i++) {
+        C v[2];
+        ld_pair(f + pair_index(i, s, L.pstride), pop_shift<S, C>(L, 0, i), pop_shift<S, C>(L, 1, i), v[0], v[1]);
 #pragma unroll
-        for (int i = 0; i < Q; i++) {
-            C v = ld_pop(f + pop_index(k * Q + i, s, L.pstride), pop_shift<S, C>(L, k, i));
-            r += v;
+        for (int k = 0; k < 2; k++) {
+            rho[k] += v[k];
             if (MOM) {
-                if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
-                if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
-                if (cz(i) > 0) jz += v; else if (cz(i) < 0) jz -= v;
+                if (cx(i) > 0) jt[k][0] += v[k]; else if (cx(i) < 0) jt[k][0] -= v[k];
+                if (cy(i) > 0) jt[k][1] += v[k]; else if (cy(i) < 0) jt[k][1] -= v[k];
+                if (cz(i) > 0) jt[k][2] += v[k]; else if (cz(i) < 0) jt[k][2] -= v[k];
             }
         }
-        rho[k] = r;
-        psi[k * L.N + s] = r;
-        jt[k][0] = jx;
-        jt[k][1] = jy;
-        jt[k][2] = jz;
     }
+    psi[s] = rho[0];
+    psi[L.N + s] = rho[1];
     if (MOM)
 #pragma unroll
         for (int d = 0; d < 3; d++) mom[d * L.pstride + s] = jt[0][d] + jt[1][d];
@@ -427,21 +424,21 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
         V[1][d] = U0[d];
         V[2][d] = wall_hi ? prm<C>(L.P.wall_u_hi[d], L.PF.wall_u_hi[d]) : U0[d];
     }
-    // destinations as 32-bit element offsets from the base of the plane pair
-    // (2j-1, 2j): plane 2j adds ps; an element of plane i is SKEW + site -
-    // c_ix (pop_index); sites < 2^31 and ps < 2^31 keep them in range
-    char* fnb = (char*)L.f_nxt;
+    // destinations as 32-bit pair offsets from the base of the plane pair
+    // (2j-1, 2j): plane 2j adds ps; a pair of plane i is SKEW + site - c_ix
+    // (pair_index); sites < 2^31 and ps < 2^31 keep them in range
+    S* const fn = (S*)L.f_nxt;
+    auto pair_at = [&](int plane, unsigned off) { return fn + 2 * ((unsigned long long)ps * (unsigned)plane + off); };
     // FP16 with stochastic rounding (SR, a separate instantiation): the
     // rounding bits of this site; both components of a link are stored by
     // one call
     unsigned rs = 0;
     if constexpr (SR) rs = sr_start(s, L.sr_key);
-    auto put2 = [&](S* qa, S* qb, C va, C vb, C sa, C sb) {
+    auto put2 = [&](S* p, C va, C vb, C sa, C sb) {
         if constexpr (SR) {
-            st_pop2_sr(qa, qb, va, vb, sa, sb, sr_next2(rs));
+            st_pair_sr(p, va, vb, sa, sb, sr_next2(rs));
         } else {
-            st_pop(qa, va, sa);
-            st_pop(qb, vb, sb);
+            st_pair(p, va, vb, sa, sb);
         }
     };
 #pragma unroll
@@ -461,8 +458,7 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
             }
         }
         if (i == 0) {
-            put2((S*)fnb + (SKEW + s), (S*)(fnb + (unsigned long long)ps * (unsigned)(Q * (int)sizeof(S))) + (SKEW + s),
-                 solid ? wgt<C>(0) * prm<C>(L.P.rho0[0], L.PF.rho0[0]) : fs[0],
+            put2(pair_at(0, (unsigned)SKEW + s), solid ? wgt<C>(0) * prm<C>(L.P.rho0[0], L.PF.rho0[0]) : fs[0],
                  solid ? wgt<C>(0) * prm<C>(L.P.rho0[1], L.PF.rho0[1]) : fs[1], pop_shift<S, C>(L, 0, 0),
                  pop_shift<S, C>(L, 1, 0));
             continue;
@@ -485,9 +481,7 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
         C fb[2];
 #pragma unroll
         for (int k = 0; k < 2; k++) fb[k] = fs[k] + B[k][c] * cw;
-        put2((S*)(fnb + (unsigned long long)ps * (unsigned)(lo * (int)sizeof(S))) + off,
-             (S*)(fnb + (unsigned long long)ps * (unsigned)((Q + lo) * (int)sizeof(S))) + off,
-             solid ? wgt<C>(i) * prm<C>(L.P.rho0[0], L.PF.rho0[0]) : fb[0],
+        put2(pair_at(lo, off), solid ? wgt<C>(i) * prm<C>(L.P.rho0[0], L.PF.rho0[0]) : fb[0],
              solid ? wgt<C>(i) * prm<C>(L.P.rho0[1], L.PF.rho0[1]) : fb[1], pop_shift<S, C>(L, 0, i),
              pop_shift<S, C>(L, 1, i));
         C fl = fs[0] + fb[0] + fs[1] + fb[1];
@@ -532,10 +526,8 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
                     fb[k] = feq<C>(opp(i), rw, uw[0], uw[1], uw[2], uwu);
                 }
             }
-            const unsigned own = (unsigned)(SKEW + cx(i)) + s;  // element of s in plane opp(i)
-            put2((S*)(fnb + (unsigned long long)ps * (unsigned)(opp(i) * (int)sizeof(S))) + own,
-                 (S*)(fnb + (unsigned long long)ps * (unsigned)((Q + opp(i)) * (int)sizeof(S))) + own, fb[0], fb[1],
-                 pop_shift<S, C>(L, 0, opp(i)), pop_shift<S, C>(L, 1, opp(i)));
+            const unsigned own = (unsigned)(SKEW + cx(i)) + s;  // pair of s in plane opp(i)
+            put2(pair_at(opp(i), own), fb[0], fb[1], pop_shift<S, C>(L, 0, opp(i)), pop_shift<S, C>(L, 1, opp(i)));
         }
     }
     if (multi) {
@@ -557,10 +549,8 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
                              feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
                 fbv[k] = fsv[k] - C(6) * wgt<C>(i) * m.rho[k] * cw;
             }
-            const unsigned own = (unsigned)(SKEW + cx(i)) + s;  // element of s in plane opp(i)
-            put2((S*)(fnb + (unsigned long long)ps * (unsigned)(opp(i) * (int)sizeof(S))) + own,
-                 (S*)(fnb + (unsigned long long)ps * (unsigned)((Q + opp(i)) * (int)sizeof(S))) + own, fbv[0], fbv[1],
-                 pop_shift<S, C>(L, 0, i), pop_shift<S, C>(L, 1, i));
+            const unsigned own = (unsigned)(SKEW + cx(i)) + s;  // pair of s in plane opp(i)
+            put2(pair_at(opp(i), own), fbv[0], fbv[1], pop_shift<S, C>(L, 0, i), pop_shift<S, C>(L, 1, i));
             const C fl = fsv[0] + fbv[0] + fsv[1] + fbv[1];
             // the link force into the second particle, added directly
             const C F2[3] = {C(cx(i)) * fl, C(cy(i)) * fl, C(cz(i)) * fl};
@@ -645,11 +635,12 @@ struct AsyncShared {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
     static constexpr int NSLOT = 4;  // psi planes held: z-1, z, z+1 and the one in flight
-    // one 16-byte chunk of elements beyond the tile on each side of a row:
-    // the own element of a site in plane i sits c_ix off its column (pop_index)
-    static constexpr int EPC = 16 / (int)sizeof(S);
-    static constexpr int SW = FTX + 2 * EPC;
-    S stage[2][2 * Q][TY][SW];
+    // one 16-byte chunk of pairs beyond the tile on each side of a row: the
+    // own pair of a site in plane i sits c_ix off its column (pair_index)
+    static constexpr int EPC = 16 / (int)sizeof(S);  // elements per chunk
+    static constexpr int MS = EPC / 2;               // sites per chunk
+    static constexpr int SW = 2 * (FTX + 2 * MS);    // elements of a staged row
+    S stage[2][Q][TY][SW];
     C psi[NSLOT][2][TY + 2][RW];
     int nd[NSLOT][TY + 2][RW];
 };
@@ -727,18 +718,19 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fu
         if (act) put(ty + 1, tx + 1, zoff + own_xy);
         if (has_ring) put(rly + 1, rlx + 1, zoff + ring_xy);
     };
-    // the 2 x 19 population rows of the tile of plane p into stage buffer b:
-    // warp ty copies its row, elements SKEW + s(x0) - EPC .. + FTX + EPC of
-    // every plane (aligned: x0 and nx are multiples of EPC), in 16-byte chunks
-    constexpr int EPC = SH::EPC;
+    // the 19 population rows (component pairs) of the tile of plane p into
+    // stage buffer b: warp ty copies its row, pairs SKEW + s(x0) - MS ..
+    // + FTX + MS of every plane (aligned: x0 and nx are multiples of MS), in
+    // 16-byte chunks
+    constexpr int EPC = SH::EPC, MS = SH::MS;
     constexpr int WCH = SH::SW / EPC;  // chunks per row
     const long long row_site = (long long)x0 + (long long)L.nx * (y0 + ty);
     auto issue_pops = [&](int p, int b) {
         if (ty >= H) return;
-        const E* base = (const E*)L.f_cur + (SKEW - EPC) + row_site + nxy * p;
-        for (int c = tx; c < 2 * Q * WCH; c += FTX) {
+        const E* base = (const E*)L.f_cur + 2 * ((SKEW - MS) + row_site + nxy * p);
+        for (int c = tx; c < Q * WCH; c += FTX) {
             const int q = c / WCH, ch = c - q * WCH;
-            cp_async_16(&sh.stage[b][q][ty][ch * EPC], base + (long long)q * L.pstride + ch * EPC);
+            cp_async_16(&sh.stage[b][q][ty][ch * EPC], base + 2 * (long long)q * L.pstride + ch * EPC);
         }
     };
     for (int p = z0 - 1; p < z0 + 2; p++)
@@ -762,7 +754,7 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fu
                 C r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
                 for (int i = 0; i < Q; i++) {
-                    C v = ld_pop(&sh.stage[b][k * Q + i][ty][EPC + tx - cx(i)], pop_shift<S, C>(L, k, i));
+                    C v = ld_pop(&sh.stage[b][i][ty][2 * (MS + tx - cx(i)) + k], pop_shift<S, C>(L, k, i));
                     r += v;
                     if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
                     if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
@@ -776,7 +768,8 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fu
             const LinkInfo li = link_info(sh, sl, tx, ty, solid);
             const ParticleRef<C> pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
             collide_site<PREC, UNIT, SR>(L, sh, sl, x0 + tx, y0 + ty, z, ty, m, solid,
-                                     [&](int q) { return &sh.stage[b][q][ty][EPC + tx - cx(q % Q)]; }, li, pref,
+                                     [&](int q) { return &sh.stage[b][q % Q][ty][2 * (MS + tx - cx(q % Q)) + q / Q]; },
+                                     li, pref,
                                      pf, Fp, Tp);
         }
         commit_link_forces<C>(L, pf, Fp, Tp);
@@ -893,12 +886,12 @@ __device__ __forceinline__ void lean_site(const Lattice& L, const LeanShared<PRE
             H[k][c] = C(4.5) * wr;
         }
     }
-    // destinations as element offsets from the site's element of plane 0 of
-    // each component (pA, pB): the element of plane i at site q is
-    // i ps + SKEW + q - c_ix, so the shift by c_ix cancels and only the
-    // periodic wrap in x is left.  NEAR: the offsets fit in 32 bits
-    // ((Q - 1) ps + N < 2^31, checked by the launcher), so an address is one
-    // wide multiply-add from the site's pointer
+    // destinations as pair offsets from the site's pair of plane 0 (pA): the
+    // pair of plane i at site q is i ps + SKEW + q - c_ix, so the shift by
+    // c_ix cancels and only the periodic wrap in x is left.  NEAR: the
+    // offsets fit in 32 bits ((Q - 1) ps + N < 2^31, checked by the
+    // launcher), so an address is one wide multiply-add from the site's
+    // pointer
     typedef typename std::conditional<NEAR, int, long long>::type Off;
     const Off ps = (Off)L.pstride;
     const int nx = L.nx, nxy = L.nx * L.ny;
@@ -925,21 +918,19 @@ __device__ __forceinline__ void lean_site(const Lattice& L, const LeanShared<PRE
         particle_u0_of<C>(L, particle_load<C>(L, p0), x, y, z, U0, rel);
     }
     C Fl[3] = {0, 0, 0};  // Eq. 19 summed over the links: (f*_i + f_ibar(t+1)) c_i
-    S* const pA = (S*)L.f_nxt + (SKEW + (long long)s);
-    S* const pB = pA + (long long)Q * L.pstride;
+    S* const pA = (S*)L.f_nxt + 2 * (SKEW + (long long)s);
     // the rounding bits of the site's stores, in store order (the bounce-back
     // stores of a link follow its push when the warp takes that branch)
     unsigned rs = 0;
     if constexpr (SR) rs = sr_start(s, L.sr_key);
-    auto put2 = [&](S* qa, S* qb, C va, C vb, C sa, C sb, bool on, unsigned& st) {
+    auto put2 = [&](S* p, C va, C vb, C sa, C sb, bool on, unsigned& st) {
         if constexpr (SR) {
-            st_pop2_sr_if(qa, qb, va, vb, sa, sb, sr_next2(st), on);
+            st_pair_sr_if(p, va, vb, sa, sb, sr_next2(st), on);
         } else {
-            st_pop_if(qa, va, sa, on);
-            st_pop_if(qb, vb, sb, on);
+            st_pair_if(p, va, vb, sa, sb, on);
         }
     };
-    put2(pA, pB, A[0][0], A[1][0], pop_shift<S, C>(L, 0, 0), pop_shift<S, C>(L, 1, 0), true, rs);
+    put2(pA, A[0][0], A[1][0], pop_shift<S, C>(L, 0, 0), pop_shift<S, C>(L, 1, 0), true, rs);
 #pragma unroll
     for (int i = 1; i < Q; i++) {
         const int c = i <= 6 ? 1 : 2;
@@ -954,7 +945,7 @@ __device__ __forceinline__ void lean_site(const Lattice& L, const LeanShared<PRE
                                             (cz(i) > 0 ? dzp : (cz(i) < 0 ? dzm : 0)));
         // a particle node does not push into a fluid site (whose bounce-back
         // writes that element)
-        put2(pA + off, pB + off, fs[0], fs[1], pop_shift<S, C>(L, 0, i), pop_shift<S, C>(L, 1, i),
+        put2(pA + 2 * (long long)off, fs[0], fs[1], pop_shift<S, C>(L, 0, i), pop_shift<S, C>(L, 1, i),
              !(solid && ((nbc >> i) & 1u)), rs);
         if (wbb & (1u << i)) {
             // Eq. 17 with the wall velocity of Eq. 18: the own element of
@@ -965,7 +956,7 @@ __device__ __forceinline__ void lean_site(const Lattice& L, const LeanShared<PRE
 #pragma unroll
             for (int k = 0; k < 2; k++) fb[k] = fs[k] + B[k][c] * cw;
             const Off ob = (Off)opp(i) * ps + cx(i);
-            put2(pA + ob, pB + ob, fb[0], fb[1], pop_shift<S, C>(L, 0, opp(i)), pop_shift<S, C>(L, 1, opp(i)), on,
+            put2(pA + 2 * (long long)ob, fb[0], fb[1], pop_shift<S, C>(L, 0, opp(i)), pop_shift<S, C>(L, 1, opp(i)), on,
                  rs);
             const C fl = on ? fs[0] + fb[0] + fs[1] + fb[1] : C(0);
             if (cx(i)) Fl[0] += C(cx(i)) * fl;
@@ -1010,7 +1001,7 @@ __device__ __forceinline__ void lean_site(const Lattice& L, const LeanShared<PRE
             }
             const int o = opp(i);
             S* f = (S*)L.f_nxt;
-            put2(f + pop_index(o, s, L.pstride), f + pop_index(Q + o, s, L.pstride), fb[0], fb[1],
+            put2(f + pair_index(o, s, L.pstride), fb[0], fb[1],
                  pop_shift<S, C>(L, 0, o), pop_shift<S, C>(L, 1, o), true, rs);
             const C fl = fs[0] + fb[0] + fs[1] + fb[1];
             const C F2[3] = {C(ax) * fl, C(ay) * fl, C(az) * fl};
@@ -1026,7 +1017,7 @@ __device__ __forceinline__ void lean_site(const Lattice& L, const LeanShared<PRE
 // rows y-1, y, y+1 with the x ring for planes z-1 .. z+3 and the momentum
 // rows of the next plane; a plane beyond a wall stages the wall densities.
 template <int PREC, bool SR, bool NEAR>
-__global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : (SR ? 4 : 5))) k_lean(Lattice L, int zc) {
+__global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : (PREC == LB_FP16 ? 4 : 5))) k_lean(Lattice L, int zc) {
     typedef typename Prec<PREC>::C C;
     typedef LeanShared<PREC> SH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1182,15 +1173,11 @@ __device__ __forceinline__ void face_rule(const Lattice& L, int face, int i, con
 #pragma unroll
         for (int k = 0; k < 2; k++) fb[k] = fs[k] + C(3) * (wgt<C>(i) * rho[k]) * cw;
     }
-    S* f = (S*)L.f_nxt;
-    S* qa = f + pop_index(opp(i), x, L.pstride);
-    S* qb = f + pop_index(Q + opp(i), x, L.pstride);
+    S* p = (S*)L.f_nxt + pair_index(opp(i), x, L.pstride);
     if constexpr (SR) {
-        st_pop2_sr(qa, qb, fb[0], fb[1], pop_shift<S, C>(L, 0, opp(i)), pop_shift<S, C>(L, 1, opp(i)),
-                   sr_next2(rs));
+        st_pair_sr(p, fb[0], fb[1], pop_shift<S, C>(L, 0, opp(i)), pop_shift<S, C>(L, 1, opp(i)), sr_next2(rs));
     } else {
-        st_pop(qa, fb[0], pop_shift<S, C>(L, 0, opp(i)));
-        st_pop(qb, fb[1], pop_shift<S, C>(L, 1, opp(i)));
+        st_pair(p, fb[0], fb[1], pop_shift<S, C>(L, 0, opp(i)), pop_shift<S, C>(L, 1, opp(i)));
     }
 }
 

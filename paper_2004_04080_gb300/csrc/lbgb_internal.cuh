@@ -59,19 +59,25 @@ __host__ __device__ constexpr C wgt(int i) {
 }
 constexpr int Q = 19;
 
-// Population storage.  The population of link i of site s is element
-// SKEW + s - c_ix of plane i (of its component), s = x + nx (y + ny z).  A
-// push along c_i (Eq. 3) from site s then writes the destination's element
-// at the source's x, so the 32 pushes of a warp's row fill whole aligned
-// lines of the destination row.  Writes shifted by one element instead left
-// partial 32-byte sectors at both ends of every row segment, which halved
-// the store bandwidth (DRAM read-modify-writes); the reads of a site's own
-// populations, shifted by one element now, cost nothing measurable.  Each
-// plane is padded by SKEW = 64 elements at both ends, which keeps the first
-// site of every plane on a 128-byte boundary in each storage type.
+// Population storage.  Plane i holds the populations of link i of both
+// components, side by side: the pair (f^A_i, f^B_i) of site s is pair
+// SKEW + s - c_ix of plane i (elements 2 (i pstride + SKEW + s - c_ix) + k),
+// s = x + nx (y + ny z).  A push along c_i (Eq. 3) from site s then writes
+// the destination's pair at the source's x, so the 32 pushes of a warp's row
+// fill whole aligned lines of the destination row, one vector store per
+// link for both components.  Writes shifted by one pair instead left partial
+// 32-byte sectors at both ends of every row segment, which halved the store
+// bandwidth (DRAM read-modify-writes); the reads of a site's own
+// populations, shifted by one pair now, cost nothing measurable.  Each plane
+// is padded by SKEW = 64 pairs at both ends, which keeps the first site of
+// every plane on a 256-byte boundary in each storage type.
 constexpr long long SKEW = 64;
 __host__ __device__ constexpr long long pop_index(int q, long long s, long long pstride) {
-    return (long long)q * pstride + SKEW + s - cx(q % Q);
+    return 2 * ((long long)(q % Q) * pstride + SKEW + s - cx(q % Q)) + q / Q;
+}
+// the element of component A of link i of site s (component B follows it)
+__host__ __device__ constexpr long long pair_index(int i, long long s, long long pstride) {
+    return 2 * ((long long)i * pstride + SKEW + s - cx(i));
 }
 
 // ---------------------------------------------------------- precisions
@@ -93,6 +99,33 @@ __device__ __forceinline__ void st_pop(__half* p, float v, float shift) {
     *p = __float2half_rn(v - shift);
 }
 
+// load / store the pair of one link of a site (p: component A, 8-, 4- or
+// 16-byte aligned for FP32, FP16, FP64)
+__device__ __forceinline__ void ld_pair(const double* p, double, double, double& a, double& b) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void ld_pair(const float* p, float, float, float& a, float& b) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void ld_pair(const __half* p, float sa, float sb, float& a, float& b) {
+    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+    a = v.x + sa;
+    b = v.y + sb;
+}
+__device__ __forceinline__ void st_pair(double* p, double a, double b, double, double) {
+    *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+__device__ __forceinline__ void st_pair(float* p, float a, float b, float, float) {
+    *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void st_pair(__half* p, float a, float b, float sa, float sb) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a - sa, b - sb);
+}
+
 // The same stores under a per-lane predicate, as predicated store
 // instructions (a branch around a store diverges the warp and costs
 // reconvergence instructions in every unrolled link).
@@ -109,14 +142,29 @@ __device__ __forceinline__ void st_pop_if(__half* p, float v, float shift, bool 
     asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.b16 [%0], %1;\n\t}" ::"l"(p), "h"(h),
                  "r"((unsigned)on));
 }
+__device__ __forceinline__ void st_pair_if(double* p, double a, double b, double, double, bool on) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q st.global.v2.f64 [%0], {%1, %2};\n\t}" ::"l"(p),
+                 "d"(a), "d"(b), "r"((unsigned)on));
+}
+__device__ __forceinline__ void st_pair_if(float* p, float a, float b, float, float, bool on) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q st.global.v2.f32 [%0], {%1, %2};\n\t}" ::"l"(p),
+                 "f"(a), "f"(b), "r"((unsigned)on));
+}
+__device__ __forceinline__ void st_pair_if(__half* p, float a, float b, float sa, float sb, bool on) {
+    const __half2 v = __floats2half2_rn(a - sa, b - sb);  // A in the low half
+    const unsigned h = *reinterpret_cast<const unsigned*>(&v);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.b32 [%0], %1;\n\t}" ::"l"(p), "r"(h),
+                 "r"((unsigned)on));
+}
 
 // Stochastic rounding of the FP16 deviation stores.  The two components of
 // a link are converted together by the hardware's stochastic-rounding
-// conversion to a pair of halves (cvt.rs.f16x2.f32: component A in the upper
-// half, rounded with random bits 31..16, component B in the lower half with
-// bits 15..0; each value rounds up with probability equal to its position
-// between the two neighbouring half values, so the expected stored value is
-// the FP32 one; subnormal halves included).  The random bits of a site start
+// conversion to a pair of halves (cvt.rs.f16x2.f32: component B in the upper
+// half, rounded with random bits 31..16, component A in the lower half with
+// bits 15..0, which is the order of the pair in memory; each value rounds
+// up with probability equal to its position between the two neighbouring
+// half values, so the expected stored value is the FP32 one; subnormal
+// halves included).  The random bits of a site start
 // from Appleby's MurmurHash3 32-bit finaliser of (site, step key) and advance
 // by the linear congruential step of Numerical Recipes (a = 1664525,
 // c = 1013904223); each component takes the upper 16 bits of its own step
@@ -138,22 +186,19 @@ __device__ __forceinline__ unsigned sr_next2(unsigned& st) {
     st = st * 1664525u + 1013904223u;
     return hi | (st >> 16);
 }
-__device__ __forceinline__ void st_pop2_sr(__half* pa, __half* pb, float va, float vb, float sa, float sb,
-                                           unsigned bits) {
+__device__ __forceinline__ unsigned cvt_sr_pair(float va, float vb, float sa, float sb, unsigned bits) {
     unsigned d;
-    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(va - sa), "f"(vb - sb), "r"(bits));
-    *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(d >> 16);
-    *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(d & 0xffffu);
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(vb - sb), "f"(va - sa), "r"(bits));
+    return d;
 }
-__device__ __forceinline__ void st_pop2_sr_if(__half* pa, __half* pb, float va, float vb, float sa, float sb,
-                                              unsigned bits, bool on) {
-    unsigned d;
-    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(va - sa), "f"(vb - sb), "r"(bits));
-    const unsigned short a = (unsigned short)(d >> 16), b = (unsigned short)(d & 0xffffu);
-    asm volatile(
-        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %4, 0;\n\t@q st.global.b16 [%0], %2;\n\t@q st.global.b16 [%1], "
-        "%3;\n\t}" ::"l"(pa),
-        "l"(pb), "h"(a), "h"(b), "r"((unsigned)on));
+__device__ __forceinline__ void st_pair_sr(__half* p, float va, float vb, float sa, float sb, unsigned bits) {
+    *reinterpret_cast<unsigned*>(p) = cvt_sr_pair(va, vb, sa, sb, bits);
+}
+__device__ __forceinline__ void st_pair_sr_if(__half* p, float va, float vb, float sa, float sb, unsigned bits,
+                                              bool on) {
+    const unsigned d = cvt_sr_pair(va, vb, sa, sb, bits);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.b32 [%0], %1;\n\t}" ::"l"(p), "r"(d),
+                 "r"((unsigned)on));
 }
 
 // ------------------------------------------------------------- context
@@ -175,9 +220,9 @@ __device__ __forceinline__ float prm<float>(double, float f) { return f; }
 struct Lattice {
     int nx, ny, nz;
     long long N;       // nx*ny*nz
-    long long pstride; // elements between two population planes (>= N, padded)
+    long long pstride; // component pairs in a population plane (>= N, padded)
     int per[3];        // periodic flags
-    void* f_cur;       // populations at time t: [2][19][pstride] of S
+    void* f_cur;       // populations at time t: [19][pstride][2] of S (pair_index)
     void* f_nxt;       // populations at time t+1
     void* psi;         // [2][N] of C: rho^k on fluid, virtual density on frontier
     void* psi_wall;    // [2 walls][2 comps][nx*ny] of C

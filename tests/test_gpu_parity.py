@@ -274,10 +274,47 @@ def test_sheared_walls_with_particles(prec, tol, tol_u, nx):
     ga, gb, gu = g.get_fields()
     ra, rb, ru = o.get_fields()
     assert np.abs(ru).max() > 0.02
-    assert np.array_equal(g.owner(), o.owner())
-    assert rel(ga, ra) < tol and rel(gb, rb) < tol
-    assert rel(gu, ru) < tol_u, rel(gu, ru)
-    compare_colloids(g, o, tol)
+    keep = np.ones(ga.shape, dtype=bool)
+    if prec == "fp16":
+        keep = event_mask(g, o, shape, [5.5] * 4)
+    else:
+        assert np.array_equal(g.owner(), o.owner())
+    assert rel(ga[keep], ra[keep]) < tol and rel(gb[keep], rb[keep]) < tol
+    assert rel(gu[:, keep], ru[:, keep]) < tol_u, rel(gu[:, keep], ru[:, keep])
+    # FP16: the force and torque terms at 1e-2 of their scale, as in the
+    # droplet case (a node created a step apart changes the links of its
+    # particle: 3e-3 of F_liq measured in such a run)
+    compare_colloids(g, o, tol, 1e-2 if prec == "fp16" else None)
+
+
+def event_mask(g, o, shape, radius):
+    """Sites to compare the fields on, for a reduced-precision run against
+    the oracle.  The particle positions carry the error of the form (about
+    2e-5 here in FP16), so a node whose distance to a centre lies that close
+    to R can be created or destroyed (Eqs. 24-25) a step apart from the
+    oracle, and then holds a density of order one in one run and none in the
+    other.  At most two such nodes are allowed, each within 0.1 of a
+    particle's surface; the sites within two links of them (where the
+    different bounce-back surface has reached by the compared step) are left
+    out, and the owner map must agree everywhere else."""
+    go, oo = g.owner(), o.owner()
+    diff = np.flatnonzero(go != oo)
+    assert len(diff) <= 2, len(diff)
+    nx, ny, nz = shape
+    pos = o.get_colloids()["pos"]
+    keep = np.ones(go.shape, dtype=bool)
+    for s in diff:
+        x, y, z = s % nx, (s // nx) % ny, s // (nx * ny)
+        d = np.array([x, y, z], dtype=float) - pos
+        for a, n in enumerate(shape):
+            d[:, a] -= n * np.round(d[:, a] / n)
+        gap = np.abs(np.linalg.norm(d, axis=1) - np.asarray(radius)).min()
+        assert gap < 0.1, (s, gap)
+        for dz in range(-2, 3):
+            for dy in range(-2, 3):
+                for dx in range(-2, 3):
+                    keep[(x + dx) % nx + nx * ((y + dy) % ny + ny * ((z + dz) % nz))] = False
+    return keep
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])

@@ -46,15 +46,14 @@ def alg_bytes(prec):
 def kernel_bytes(kname, prec):
     """Bytes per site that a lattice kernel itself must move (arrays touched
     once): the density pass reads the populations and the mask and writes
-    rho^k, j^k and the 4-byte link classes; the lean momentum kernel reads
-    j^k, psi^k and the link classes and writes the populations; the
-    two-pass kernel reads both; the plain kernel reads and writes the
-    populations."""
+    rho^k and j^A + j^B; the lean momentum kernel reads j^A + j^B, psi^k and
+    the 4-byte link classes and writes the populations; the two-pass kernel
+    reads both; the plain kernel reads and writes the populations."""
     pops = 38 * STORE[prec]
     if kname == "k_density":
-        return pops + 1 + 8 * COMPUTE[prec] + 4
+        return pops + 1 + 5 * COMPUTE[prec]
     if kname == "k_lean":
-        return pops + 8 * COMPUTE[prec] + 4
+        return pops + 5 * COMPUTE[prec] + 4
     if kname == "k_fused_async":
         return 2 * pops + 2 * COMPUTE[prec] + 4
     return 2 * pops + 1

@@ -60,6 +60,18 @@ enum {
  * force/torque sums and the global reductions are FP64 in every mode. */
 enum { LB_FP64 = 0, LB_FP32 = 1, LB_FP16 = 2 };
 
+/* Flag or-ed into the prec argument of lb_workspace_bytes and lb_create: a
+ * lattice of one fluid component (the single-component benchmark of
+ * Sec. 5.1, App. D test 1).  It holds the populations of component A only
+ * (19 per site), has no Shan-Chen force (G, zeta ignored), no particles
+ * (max_colloids must be 0; lb_add_colloids returns LB_ERR_ARG), walls and
+ * velocity faces on z (open types 0 and 2), and no adjoint (LB_ERR_STATE).
+ * lb_init_fields ignores rhoB (which may be NULL); lb_get_fields returns
+ * rhoB = 0; lb_get_populations accepts k = 0 only; lb_get_owner returns -1
+ * everywhere.  The step is Eqs. 5-7 and 16 with one component (the body force
+ * of Eq. 15 as F = rho g) and push streaming with the wall rule of Eq. 9. */
+enum { LB_ONE_COMPONENT = 0x100 };
+
 /* Physical parameters (paper App. A "LB" and "MD" rooms; lattice units). */
 typedef struct {
     double tau[2];          /* BGK relaxation time per component (Eq. 4), > 1/2   */
@@ -110,8 +122,9 @@ typedef struct {
     double open_rho[2][2];
 } lb_params;
 
-/* Device workspace size for a lattice; *bytes receives the size.
- * Returns LB_ERR_ARG for a non-positive size or unknown precision. */
+/* Device workspace size for a lattice; *bytes receives the size.  prec may
+ * carry LB_ONE_COMPONENT.  Returns LB_ERR_ARG for a non-positive size, an
+ * unknown precision, or particles on a one-component lattice. */
 int lb_workspace_bytes(int nx, int ny, int nz, int prec, int max_colloids, size_t *bytes);
 
 /* Create a context on the calling thread's current CUDA device.
@@ -314,9 +327,11 @@ long long lb_pair_list_builds(lb_ctx *ctx);
  *  LB_FUSED_TWO_PASS  particles, other tau: a density pass writes rho^k, the
  *      fused kernel re-reads the populations;
  *  LB_FUSED_PLAIN     no particles: one pass, halo densities formed from the
- *      neighbours' populations.
+ *      neighbours' populations;
+ *  LB_FUSED_SINGLE    a one-component lattice (LB_ONE_COMPONENT): one pass,
+ *      one thread per site.
  * Returns the code, or LB_ERR_ARG for a NULL context. */
-enum { LB_FUSED_MOMENTUM = 1, LB_FUSED_TWO_PASS = 2, LB_FUSED_PLAIN = 3 };
+enum { LB_FUSED_MOMENTUM = 1, LB_FUSED_TWO_PASS = 2, LB_FUSED_PLAIN = 3, LB_FUSED_SINGLE = 4 };
 int lb_fused_kernel(const lb_ctx *ctx);
 
 

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbgb.so")
-SOURCES = ["lbgb_api.cu", "lbgb_fluid.cu", "lbgb_colloid.cu", "lbgb_static.cu", "lbgb_adjoint.cu"]
+SOURCES = ["lbgb_api.cu", "lbgb_fluid.cu", "lbgb_colloid.cu", "lbgb_static.cu", "lbgb_adjoint.cu", "lbgb_single.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

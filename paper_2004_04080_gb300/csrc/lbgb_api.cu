@@ -83,7 +83,9 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 size_t storage_bytes(int prec) { return prec == LB_FP64 ? 8 : (prec == LB_FP32 ? 4 : 2); }
 size_t compute_bytes(int prec) { return prec == LB_FP64 ? 8 : 4; }
 // bytes of one population state (both buffers have this size)
-size_t state_bytes(const lb_ctx* ctx) { return (size_t)2 * Q * ctx->L.pstride * storage_bytes(ctx->prec); }
+size_t state_bytes(const lb_ctx* ctx) {
+    return (size_t)ctx->L.ncomp * Q * ctx->L.pstride * storage_bytes(ctx->prec);
+}
 
 const int DOUBLES_PER_PARTICLE = 57;  // pos..Ttot, see carve()
 // seed of the default stochastic rounding of FP16 contexts (any constant: the
@@ -98,27 +100,30 @@ struct Layout {
     long long pstride;
 };
 
-Layout layout(int nx, int ny, int nz, int prec, int maxc) {
+// ncomp = 1: the one-component fluid holds one population per link and
+// site and none of the per-site arrays of the particle coupling
+Layout layout(int nx, int ny, int nz, int prec, int maxc, int ncomp) {
     Layout l;
     long long N = (long long)nx * ny * nz;
-    // population planes: pstride component pairs each, SKEW pairs of padding
-    // at both ends (pop_index)
+    // population planes: pstride component pairs (one component: single
+    // elements) each, SKEW of padding at both ends (pop_index, pop1_index)
     l.pstride = (N + 2 * SKEW + 63) / 64 * 64;
     size_t off = 0;
-    size_t fb = (size_t)2 * Q * l.pstride * storage_bytes(prec);
+    size_t fb = (size_t)ncomp * Q * l.pstride * storage_bytes(prec);
+    const long long Np = ncomp == 2 ? N : 0;  // per-site arrays of the coupled lattice
     // the second population buffer doubles as the FP64 staging area of the
     // read-out calls (5 doubles per site), so it is at least that large
     size_t fb1 = fb > (size_t)5 * N * 8 ? fb : (size_t)5 * N * 8;
     l.f0 = off; off = align_up(off + fb);
     l.f1 = off; off = align_up(off + fb1);
-    l.mom = off; off = align_up(off + (size_t)3 * l.pstride * compute_bytes(prec));
-    l.psi = off; off = align_up(off + (size_t)2 * N * compute_bytes(prec));
+    l.mom = off; off = align_up(off + (size_t)3 * (ncomp == 2 ? l.pstride : 0) * compute_bytes(prec));
+    l.psi = off; off = align_up(off + (size_t)2 * Np * compute_bytes(prec));
     l.psi_wall = off; off = align_up(off + (size_t)4 * nx * ny * compute_bytes(prec));
-    l.mask = off; off = align_up(off + (size_t)N);
-    l.owner = off; off = align_up(off + (size_t)N * 4);
-    l.evt = off; off = align_up(off + (size_t)N * 4);
-    l.nb = off; off = align_up(off + (size_t)N * 4);
-    l.nb_chg = off; off = align_up(off + (size_t)(8 + NB_CHG_CAP) * 4);
+    l.mask = off; off = align_up(off + (size_t)Np);
+    l.owner = off; off = align_up(off + (size_t)Np * 4);
+    l.evt = off; off = align_up(off + (size_t)Np * 4);
+    l.nb = off; off = align_up(off + (size_t)Np * 4);
+    l.nb_chg = off; off = align_up(off + (size_t)(ncomp == 2 ? 8 + NB_CHG_CAP : 0) * 4);
     l.flags = off; off = align_up(off + 64);
     int mc = maxc > 0 ? maxc : 1;
     l.col = off; off = align_up(off + (size_t)mc * DOUBLES_PER_PARTICLE * 8);
@@ -130,7 +135,7 @@ Layout layout(int nx, int ny, int nz, int prec, int maxc) {
     l.ipos = off; off = align_up(off + (size_t)mc * 12);
     l.fsnap = off; off = align_up(off + (size_t)mc * 36);
     // particle cell list: counts and starts of up to 64^3 cells, then the items
-    l.cells_bytes = ((size_t)2 * 64 * 64 * 64 + 1 + (size_t)mc) * 4;
+    l.cells_bytes = ncomp == 2 ? ((size_t)2 * 64 * 64 * 64 + 1 + (size_t)mc) * 4 : 0;
     l.cells = off; off = align_up(off + l.cells_bytes);
     l.red = off; off = align_up(off + (size_t)RED_BLOCKS * 16 * 8);
     l.totals = off; off = align_up(off + 8 * 8);
@@ -181,10 +186,19 @@ extern "C" {
 
 static const long long MAX_SITES = (1LL << 31) - 4096;
 
+// the precision code and the number of components of a prec argument
+static bool split_prec(int& prec, int& ncomp, int max_colloids) {
+    ncomp = (prec & LB_ONE_COMPONENT) ? 1 : 2;
+    prec &= ~LB_ONE_COMPONENT;
+    if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_FP16) return false;
+    return ncomp == 2 || max_colloids == 0;  // one component: no particles
+}
+
 int lb_workspace_bytes(int nx, int ny, int nz, int prec, int max_colloids, size_t* bytes) {
     if (!bytes || nx < 4 || ny < 4 || nz < 4 || max_colloids < 0) return LB_ERR_ARG;
-    if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_FP16) return LB_ERR_ARG;
-    *bytes = layout(nx, ny, nz, prec, max_colloids).total;
+    int ncomp;
+    if (!split_prec(prec, ncomp, max_colloids)) return LB_ERR_ARG;
+    *bytes = layout(nx, ny, nz, prec, max_colloids, ncomp).total;
     return LB_OK;
 }
 
@@ -213,11 +227,12 @@ int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_worksp
     if (!out) return LB_ERR_ARG;
     *out = NULL;
     if (nx < 4 || ny < 4 || nz < 4 || (nx % 4) != 0 || max_colloids < 0) return LB_ERR_ARG;
-    if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_FP16) return LB_ERR_ARG;
+    int ncomp;
+    if (!split_prec(prec, ncomp, max_colloids)) return LB_ERR_ARG;
     // the lattice kernels index sites with 32-bit integers
     if ((long long)nx * ny * nz > MAX_SITES) return LB_ERR_ARG;
     if (!d_workspace || ((uintptr_t)d_workspace % ALIGN) != 0) return LB_ERR_ARG;
-    Layout l = layout(nx, ny, nz, prec, max_colloids);
+    Layout l = layout(nx, ny, nz, prec, max_colloids, ncomp);
     if (bytes < l.total) return LB_ERR_NOMEM;
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, d_workspace) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
@@ -235,6 +250,7 @@ int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_worksp
     Lattice& L = ctx->L;
     L.nx = nx; L.ny = ny; L.nz = nz;
     L.N = (long long)nx * ny * nz;
+    L.ncomp = ncomp;
     L.pstride = l.pstride;
     L.per[0] = L.per[1] = L.per[2] = 1;
     L.f_cur = ctx->ws + l.f0;
@@ -279,14 +295,16 @@ int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_worksp
     L.sr = prec == LB_FP16;
     ctx->sr_seed = SR_DEFAULT_SEED;
     ctx->sr_step = 0;
-    // empty node map, no particles, no error flags
-    cudaError_t e = cudaMemsetAsync(ctx->ws + l.mask, 0, (size_t)L.N, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.owner, 0xff, (size_t)L.N * 4, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.evt, 0, (size_t)L.N * 4, ctx->stream);
+    // empty node map, no particles, no error flags (the per-site arrays of
+    // the coupling exist on the two-component lattice only: sizes of layout())
+    const size_t Np = ncomp == 2 ? (size_t)L.N : 0;
+    cudaError_t e = cudaMemsetAsync(ctx->ws + l.mask, 0, Np, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.owner, 0xff, Np * 4, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.evt, 0, Np * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.flags, 0, 64, ctx->stream);
     // psi: kernels read it on particle nodes that no virtual density has
     // reached yet (deep nodes), where any finite value serves
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.psi, 0, (size_t)2 * L.N * compute_bytes(prec), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.psi, 0, 2 * Np * compute_bytes(prec), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.col, 0, (size_t)mc * DOUBLES_PER_PARTICLE * 8, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.prev, 0, (size_t)mc * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws + l.vl, 0, (size_t)mc * 24 + 16, ctx->stream);
@@ -322,6 +340,8 @@ int lb_set_params(lb_ctx* ctx, const lb_params* p) {
         return set_err(ctx, LB_ERR_ARG, "rcut and delr must be finite and >= 0");
     for (int f = 0; f < 2; f++) {
         if (p->open[f] < 0 || p->open[f] > 3) return set_err(ctx, LB_ERR_ARG, "open face types are 0..3");
+        if (ctx->L.ncomp == 1 && (p->open[f] == 1 || p->open[f] == 3))
+            return set_err(ctx, LB_ERR_ARG, "the one-component lattice has wall and velocity faces only");
         if (p->open[f] != 0 && p->bc[2] != 0)
             return set_err(ctx, LB_ERR_ARG, "open faces need bc[2] = 0 (the z faces)");
         for (int k = 0; k < 2; k++)
@@ -355,21 +375,26 @@ int lb_set_params(lb_ctx* ctx, const lb_params* p) {
 }
 
 int lb_init_fields(lb_ctx* ctx, const double* rhoA, const double* rhoB, const double* u) {
-    if (!ctx || !rhoA || !rhoB) return LB_ERR_ARG;
+    if (!ctx || !rhoA || (!rhoB && ctx->L.ncomp == 2)) return LB_ERR_ARG;
     if (!ctx->have_params) return set_err(ctx, LB_ERR_STATE, "lb_set_params must come first");
     Lattice& L = ctx->L;
     size_t nb = (size_t)L.N * 8;
     double* st = stage_ptr(ctx);
     CK(cudaMemcpyAsync(st, rhoA, nb, cudaMemcpyHostToDevice, ctx->stream), "copy rhoA");
-    CK(cudaMemcpyAsync(st + L.N, rhoB, nb, cudaMemcpyHostToDevice, ctx->stream), "copy rhoB");
+    if (L.ncomp == 2) CK(cudaMemcpyAsync(st + L.N, rhoB, nb, cudaMemcpyHostToDevice, ctx->stream), "copy rhoB");
     if (u) CK(cudaMemcpyAsync(st + 2 * L.N, u, 3 * nb, cudaMemcpyHostToDevice, ctx->stream), "copy u");
     else CK(cudaMemsetAsync(st + 2 * L.N, 0, 3 * nb, ctx->stream), "zero u");
     L.nc = 0;
     ctx->all_fixed = 1;
     ctx->sr_step = 0;  // a new state starts the rounding sequence afresh
     ctx->nb_valid = 0;
-    int n = launch_clear_map(L, ctx->stream);
-    n += launch_init_fields(L, ctx->prec, st, ctx->stream);
+    int n = 0;
+    if (L.ncomp == 1) {
+        n += launch_single_init(L, ctx->prec, st, ctx->stream);
+    } else {
+        n += launch_clear_map(L, ctx->stream);
+        n += launch_init_fields(L, ctx->prec, st, ctx->stream);
+    }
     int rc = launched(ctx, n, "init kernels");
     if (rc) return rc;
     CK(cudaStreamSynchronize(ctx->stream), "init sync");
@@ -382,6 +407,7 @@ int lb_add_colloids(lb_ctx* ctx, int n, const double* pos, const double* vel, co
                     const double* quat, const double* radius, const double* mass) {
     if (!ctx || n < 0 || (n > 0 && (!pos || !radius || !mass))) return LB_ERR_ARG;
     if (!ctx->have_fields) return set_err(ctx, LB_ERR_STATE, "lb_init_fields must come first");
+    if (n > 0 && ctx->L.ncomp == 1) return set_err(ctx, LB_ERR_ARG, "a one-component lattice holds no particles");
     if (ctx->stepped) return set_err(ctx, LB_ERR_STATE, "particles must be added before the first step");
     Lattice& L = ctx->L;
     if (L.nc + n > ctx->maxc) return set_err(ctx, LB_ERR_STATE, "more than max_colloids particles");
@@ -480,7 +506,19 @@ int lb_step(lb_ctx* ctx, int nsteps) {
     Lattice& L = ctx->L;
     cudaStream_t s = ctx->stream;
     CK(cudaMemsetAsync(L.flags, 0, 4, s), "clear flags");
-    for (int t = 0; t < nsteps; t++) {
+    for (int t = 0; L.ncomp == 1 && t < nsteps; t++) {
+        // the one-component fluid: one kernel per step (Eqs. 5-7, 16, 3, 9)
+        if (L.sr) L.sr_key = sr_key(ctx->sr_seed, ctx->sr_step++);
+        if (int rc = prof_mark(ctx, LB_KERNEL_FUSED, 0, s)) return rc;
+        const int n = launch_single_step(L, ctx->prec, s);
+        if (int rc = prof_mark(ctx, LB_KERNEL_FUSED, 1, s)) return rc;
+        if (int rc = launched(ctx, n, "step kernel")) return rc;
+        void* tmp = L.f_cur;
+        L.f_cur = L.f_nxt;
+        L.f_nxt = tmp;
+        ctx->stepped = 1;
+    }
+    for (int t = 0; L.ncomp == 2 && t < nsteps; t++) {
         int n = 0;
         const bool rec = ctx->rec_left > 0;
         if (rec && ctx->rec_states)
@@ -549,6 +587,7 @@ int lb_step(lb_ctx* ctx, int nsteps) {
 // density, wetting and wall fields of the current state (no particle terms)
 static int current_forces(lb_ctx* ctx) {
     Lattice& L = ctx->L;
+    if (L.ncomp == 1) return LB_OK;  // no Shan-Chen or particle terms
     int n = launch_density(L, ctx->prec, ctx->stream);
     n += launch_wall_psi(L, ctx->prec, ctx->stream);
     n += launch_virtual(L, ctx->prec, 0, ctx->stream);
@@ -562,7 +601,9 @@ int lb_get_fields(lb_ctx* ctx, double* rhoA, double* rhoB, double* u) {
     int rc = current_forces(ctx);
     if (rc) return rc;
     double* st = stage_ptr(ctx);
-    rc = launched(ctx, launch_fields_out(L, ctx->prec, st, ctx->stream), "fields kernel");
+    rc = launched(ctx, L.ncomp == 1 ? launch_single_fields_out(L, ctx->prec, st, ctx->stream)
+                                    : launch_fields_out(L, ctx->prec, st, ctx->stream),
+                  "fields kernel");
     if (rc) return rc;
     size_t nb = (size_t)L.N * 8;
     if (rhoA) CK(cudaMemcpyAsync(rhoA, st, nb, cudaMemcpyDeviceToHost, ctx->stream), "copy rhoA");
@@ -585,13 +626,16 @@ int lb_get_totals(lb_ctx* ctx, double* out) {
 }
 
 int lb_get_populations(lb_ctx* ctx, int k, double* out) {
-    if (!ctx || !out || k < 0 || k > 1) return LB_ERR_ARG;
+    if (!ctx || !out || k < 0 || k >= ctx->L.ncomp) return LB_ERR_ARG;
     if (!ctx->have_fields) return set_err(ctx, LB_ERR_STATE, "no fields");
     Lattice& L = ctx->L;
     // one population plane at a time through the staging area
     double* st = stage_ptr(ctx);
     for (int i = 0; i < Q; i++) {
-        int rc = launched(ctx, launch_populations_out(L, ctx->prec, k, i, st, ctx->stream), "pops kernel");
+        int rc = launched(ctx,
+                          L.ncomp == 1 ? launch_single_populations_out(L, ctx->prec, i, st, ctx->stream)
+                                       : launch_populations_out(L, ctx->prec, k, i, st, ctx->stream),
+                          "pops kernel");
         if (rc) return rc;
         CK(cudaMemcpyAsync(out + (size_t)i * L.N, st, (size_t)L.N * 8, cudaMemcpyDeviceToHost, ctx->stream),
            "copy pops");
@@ -602,6 +646,10 @@ int lb_get_populations(lb_ctx* ctx, int k, double* out) {
 
 int lb_get_owner(lb_ctx* ctx, int* out) {
     if (!ctx || !out) return LB_ERR_ARG;
+    if (ctx->L.ncomp == 1) {  // no particle nodes
+        for (long long s = 0; s < ctx->L.N; s++) out[s] = -1;
+        return LB_OK;
+    }
     CK(cudaMemcpyAsync(out, ctx->L.owner, (size_t)ctx->L.N * 4, cudaMemcpyDeviceToHost, ctx->stream), "copy owner");
     CK(cudaStreamSynchronize(ctx->stream), "owner sync");
     return LB_OK;
@@ -650,6 +698,7 @@ long long lb_pair_list_builds(lb_ctx* ctx) {
 int lb_fused_kernel(const lb_ctx* ctx) {
     if (!ctx) return LB_ERR_ARG;
     const bool unit = ctx->L.P.tau[0] == 1.0 && ctx->L.P.tau[1] == 1.0;
+    if (ctx->L.ncomp == 1) return LB_FUSED_SINGLE;
     if (ctx->L.nc > 0) return unit ? LB_FUSED_MOMENTUM : LB_FUSED_TWO_PASS;
     return LB_FUSED_PLAIN;
 }
@@ -696,6 +745,7 @@ int lb_adjoint_bytes(const lb_ctx* ctx, size_t* field_bytes, size_t* scratch_byt
 
 static int adjoint_ready(lb_ctx* ctx) {
     if (!ctx->have_fields) return set_err(ctx, LB_ERR_STATE, "no fields");
+    if (ctx->L.ncomp == 1) return set_err(ctx, LB_ERR_STATE, "the adjoint is built for the two-component lattice");
     if (ctx->L.sr)
         return set_err(ctx, LB_ERR_STATE, "stochastic rounding: recomputed forward steps would differ from the recorded ones");
     if (!ctx->all_fixed) return set_err(ctx, LB_ERR_STATE, "the adjoint needs immobile particles (infinite mass, at rest)");

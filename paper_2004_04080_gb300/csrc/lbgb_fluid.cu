@@ -1492,7 +1492,11 @@ int launch_fields_out(const Lattice& L, int prec, double* stage, cudaStream_t st
 }
 
 int launch_totals(const Lattice& L, int prec, double* out_dev, cudaStream_t st) {
-    DISPATCH(prec, (k_totals_partial<P><<<L.red_blocks, 256, 0, st>>>(L)));
+    if (L.ncomp == 1) {
+        launch_single_totals_partial(L, prec, st);
+    } else {
+        DISPATCH(prec, (k_totals_partial<P><<<L.red_blocks, 256, 0, st>>>(L)));
+    }
     k_totals_final<<<1, 32, 0, st>>>(L, L.red_blocks, out_dev);
     return 2;
 }

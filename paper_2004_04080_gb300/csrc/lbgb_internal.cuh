@@ -219,6 +219,7 @@ __device__ __forceinline__ float prm<float>(double, float f) { return f; }
 // Device-visible view of one lattice (passed by value to every kernel).
 struct Lattice {
     int nx, ny, nz;
+    int ncomp;         // 2: the two-component lattice; 1: one fluid component, no particles (lbgb_single.cu)
     long long N;       // nx*ny*nz
     long long pstride; // component pairs in a population plane (>= N, padded)
     int per[3];        // periodic flags
@@ -638,6 +639,12 @@ inline int kernel_setup(int threads, size_t smem) {
 // kernel launchers (each returns the number of kernels it launched)
 int launch_init_fields(const Lattice& L, int prec, const double* stage, cudaStream_t st);
 int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st);
+// the one-component fluid (lbgb_single.cu)
+int launch_single_init(const Lattice& L, int prec, const double* stage, cudaStream_t st);
+int launch_single_step(const Lattice& L, int prec, cudaStream_t st);
+int launch_single_fields_out(const Lattice& L, int prec, double* stage, cudaStream_t st);
+int launch_single_totals_partial(const Lattice& L, int prec, cudaStream_t st);
+int launch_single_populations_out(const Lattice& L, int prec, int i, double* stage, cudaStream_t st);
 // the links across the z faces after the lean push (with particles and
 // tau^A = tau^B = 1)
 int launch_wall_bounce(const Lattice& L, int prec, cudaStream_t st);

@@ -21,6 +21,7 @@ from . import build as _build
 LB_OK, LB_ERR_ARG, LB_ERR_STATE, LB_ERR_CUDA, LB_ERR_NOMEM = 0, -1, -2, -3, -4
 LB_ERR_NONFINITE, LB_ERR_OVERLAP, LB_ERR_TIMEOUT = -5, -6, -7
 LB_FP64, LB_FP32, LB_FP16 = 0, 1, 2
+LB_ONE_COMPONENT = 0x100
 PREC = {"fp64": LB_FP64, "fp32": LB_FP32, "fp16": LB_FP16}
 TERMS = {"F_liq": 0, "T_liq": 1, "F_d": 2, "T_d": 3, "F_c": 4, "T_c": 5, "F_s": 6,
          "T_s": 7, "F_pair": 8, "F_total": 9, "T_total": 10}
@@ -179,7 +180,7 @@ def lb_set_params(h, **params):
 
 
 def lb_init_fields(h, rhoA, rhoB, u=None):
-    a, b = _f64(rhoA), _f64(rhoB)
+    a, b = _f64(rhoA), _f64(rhoB)  # rhoB may be None on a one-component lattice
     uu = _f64(u, 3 * a.size)
     return _check(h, load().lb_init_fields(h, _dp(a), _dp(b), _dp(uu)), "lb_init_fields")
 
@@ -334,9 +335,9 @@ def lb_pair_list_builds(h) -> int:
     return n
 
 
-LB_FUSED_MOMENTUM, LB_FUSED_TWO_PASS, LB_FUSED_PLAIN = 1, 2, 3
+LB_FUSED_MOMENTUM, LB_FUSED_TWO_PASS, LB_FUSED_PLAIN, LB_FUSED_SINGLE = 1, 2, 3, 4
 FUSED_KERNEL_NAMES = {LB_FUSED_MOMENTUM: "k_lean", LB_FUSED_TWO_PASS: "k_fused_async",
-                      LB_FUSED_PLAIN: "k_fused"}
+                      LB_FUSED_PLAIN: "k_fused", LB_FUSED_SINGLE: "k1_step"}
 
 
 def lb_fused_kernel(h) -> int:
@@ -354,9 +355,10 @@ def lb_last_error(h) -> str:
 
 # ------------------------------------------------------- convenience
 class LBLattice:
-    """One lattice context with a torch-allocated device workspace."""
+    """One lattice context with a torch-allocated device workspace
+    (components=1: the one-component fluid, LB_ONE_COMPONENT)."""
 
-    def __init__(self, shape, prec="fp32", max_colloids=0, device=None, stream=None):
+    def __init__(self, shape, prec="fp32", max_colloids=0, device=None, stream=None, components=2):
         import torch
 
         if not torch.cuda.is_available():
@@ -364,11 +366,13 @@ class LBLattice:
         self.shape = tuple(int(v) for v in shape)
         self.N = int(np.prod(self.shape))
         self.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        self.components = int(components)
+        flag = LB_ONE_COMPONENT if self.components == 1 else 0
         self.device = torch.device(device or "cuda:0")
-        nbytes = lb_workspace_bytes(*self.shape, self.prec, max_colloids)
+        nbytes = lb_workspace_bytes(*self.shape, self.prec | flag, max_colloids)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self.h = lb_create(*self.shape, self.prec, max_colloids, self.workspace.data_ptr(), nbytes,
+        self.h = lb_create(*self.shape, self.prec | flag, max_colloids, self.workspace.data_ptr(), nbytes,
                            self.stream.cuda_stream)
         self.nc = 0
 
@@ -386,7 +390,7 @@ class LBLattice:
     def set_params(self, **kw):
         lb_set_params(self.h, **kw)
 
-    def init_fields(self, rhoA, rhoB, u=None):
+    def init_fields(self, rhoA, rhoB=None, u=None):
         lb_init_fields(self.h, rhoA, rhoB, u)
         self.nc = 0
 

@@ -69,6 +69,13 @@ def test_workspace_size_host_logic():
     for bad in [(0, 32, 32, 1, 0), (32, 32, 32, 7, 0), (32, 32, 3, 1, 0), (32, 32, 32, 1, -1)]:
         with pytest.raises(lbgb.LBError):
             lbgb.lb_workspace_bytes(*bad)
+    # one component: 19 values per site in each buffer, no per-site coupling
+    # arrays, and no particles
+    one = lbgb.lb_workspace_bytes(32, 32, 32, lbgb.LB_FP32 | lbgb.LB_ONE_COMPONENT, 0)
+    two = lbgb.lb_workspace_bytes(32, 32, 32, lbgb.LB_FP32, 0)
+    assert 2 * 19 * 4 * N < one < 2 * 19 * 4 * N + (1 << 20) and one < two / 2
+    with pytest.raises(lbgb.LBError):
+        lbgb.lb_workspace_bytes(32, 32, 32, lbgb.LB_FP32 | lbgb.LB_ONE_COMPONENT, 1)
 
 
 def test_product_path_has_no_cpu_fallback():

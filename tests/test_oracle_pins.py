@@ -573,3 +573,31 @@ def test_thread_count_gives_the_same_bits():
     b.step(10)
     assert np.array_equal(a.populations(0), b.populations(0))
     assert np.array_equal(a.populations(1), b.populations(1))
+
+
+# ---------------------------------------------------------- one component
+def test_one_component_reduction():
+    """The single-component fluid of the paper's first benchmark (Sec. 5.1,
+    App. D test 1) is the mixture with rho^B = 0: Eq. 14 gives u = j^A/rho^A,
+    Eq. 11 gives no force on A (psi^B = 0) and the mixture viscosity is
+    component A's.  Pinned here by (a) the exact Poiseuille parabola of the
+    halfway bounce-back at tau = 1/2 + sqrt(3/16) with a body force, for
+    component A alone; (b) component B's populations staying exactly zero;
+    (c) G having no effect on the bits."""
+    g, H = 1e-6, 8
+    tau = 0.5 + math.sqrt(3.0 / 16.0)
+    shape = (4, 4, H)
+    N = 16 * H
+    z = zcoord(shape)
+    runs = []
+    for G in (0.0, 0.9):
+        o = make(shape, tau=(tau, tau), bc=(1, 1, 0), body_force=(g, 0, 0), G=G)
+        o.init_fields(np.full(N, 0.7), np.zeros(N))
+        nu = CS2 * (tau - 0.5)
+        o.step(int(34 / (nu * (math.pi / H) ** 2)))
+        a, b, u = o.get_fields()
+        ex = g / (2 * nu) * (z + 0.5) * (H - 0.5 - z)
+        assert np.max(np.abs(u[0] - ex)) / ex.max() < 1e-10
+        assert np.all(b == 0.0) and np.all(o.populations(1) == 0.0)
+        runs.append(o.populations(0))
+    assert np.array_equal(runs[0], runs[1])

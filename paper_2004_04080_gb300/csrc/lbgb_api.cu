@@ -585,10 +585,19 @@ int lb_step(lb_ctx* ctx, int nsteps) {
 }
 
 // density, wetting and wall fields of the current state (no particle terms)
+// the virtual densities find the frontier nodes by the link classes: rebuild
+// them if the node map changed outside lb_step (number of launches)
+static int ensure_link_classes(lb_ctx* ctx, cudaStream_t st) {
+    if (ctx->L.nc <= 0 || ctx->nb_valid) return 0;
+    ctx->nb_valid = 1;
+    return launch_link_classes(ctx->L, true, st);
+}
+
 static int current_forces(lb_ctx* ctx) {
     Lattice& L = ctx->L;
     if (L.ncomp == 1) return LB_OK;  // no Shan-Chen or particle terms
-    int n = launch_density(L, ctx->prec, ctx->stream);
+    int n = ensure_link_classes(ctx, ctx->stream);
+    n += launch_density(L, ctx->prec, ctx->stream);
     n += launch_wall_psi(L, ctx->prec, ctx->stream);
     n += launch_virtual(L, ctx->prec, 0, ctx->stream);
     return launched(ctx, n, "density kernels");
@@ -779,7 +788,8 @@ static int adjoint_step_launch(lb_ctx* ctx, const void* d_state, const void* d_a
     cudaStream_t s = ctx->stream;
     char* head = (char*)d_scratch;
     // forward densities of step t: rho everywhere, wall and virtual densities
-    int n = launch_density(Ls, ctx->prec, s);
+    int n = ensure_link_classes(ctx, s);
+    n += launch_density(Ls, ctx->prec, s);
     n += launch_wall_psi(Ls, ctx->prec, s);
     n += launch_virtual(Ls, ctx->prec, 0, s);
     n += launch_adjoint_step(Ls, ctx->prec, d_adj_in, d_adj_out, head + adj_head_bytes(ctx),

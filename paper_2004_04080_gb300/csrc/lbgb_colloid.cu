@@ -331,6 +331,46 @@ __global__ void __launch_bounds__(PB) k_map_initial(Lattice L, int first) {
 }
 
 // ------------------------------------------------------------- remap
+// The nodes the remap of a step changes are listed (nb_chg, up to
+// NB_CHG_CAP): the refill, the commit and the link classes then visit only
+// them.  When more change, the list is left incomplete and every kernel that
+// uses it falls back to scanning the particles' shells.
+__device__ __forceinline__ void list_changed(const Lattice& L, long long s) {
+    const int q = atomicAdd(L.nb_chg, 1);
+    if (q < NB_CHG_CAP) L.nb_chg[8 + q] = (int)s;
+}
+
+// x_s - r_p (minimum image) and the particle's v, omega, in the compute type:
+// FP32 / FP16 from the snapshot (integer cell + offset), FP64 from the state
+template <typename C>
+__device__ __forceinline__ void particle_frame(const Lattice& L, int p, int x, int y, int z, C (&d)[3], C (&v)[3],
+                                               C (&w)[3]) {
+    const int xs[3] = {x, y, z}, Ls[3] = {L.nx, L.ny, L.nz};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        int ip;
+        C fr;
+        if (sizeof(C) == 8) {
+            const double r = L.pos[3 * p + c];
+            ip = (int)floor(r);
+            fr = C(r - (double)ip);
+            v[c] = C(L.vel[3 * p + c]);
+            w[c] = C(L.omg[3 * p + c]);
+        } else {
+            ip = L.ipos[3 * p + c];
+            fr = C(L.fsnap[9 * p + c]);
+            v[c] = C(L.fsnap[9 * p + 3 + c]);
+            w[c] = C(L.fsnap[9 * p + 6 + c]);
+        }
+        int dd = xs[c] - ip;
+        if (L.per[c]) {
+            if (2 * dd > Ls[c]) dd -= Ls[c];
+            else if (2 * dd < -Ls[c]) dd += Ls[c];
+        }
+        d[c] = C(dd) - fr;
+    }
+}
+
 // The remap kernels work on the points within 0.65 of the surface (a node
 // changes side only within the distance moved, below 1/2 per step); their
 // box reaches 0.75 beyond the sphere.
@@ -355,6 +395,7 @@ __global__ void __launch_bounds__(PB) k_remap_classify(Lattice L) {
                     atomicOr(L.flags, FLAG_OVERLAP);
                     return;
                 }
+                list_changed(L, s);
                 C fv[2][Q], rho[2], j[2][3], u[3], om;
                 load_site<PREC>(L, (const typename Prec<PREC>::S*)L.f_cur, s, fv, rho, j);
                 mixture<C>(L, rho, j, u, om);
@@ -371,6 +412,7 @@ __global__ void __launch_bounds__(PB) k_remap_classify(Lattice L) {
             }
         } else if (o == p) {
             L.evt[s] = 4 * (p + 1) + 2;
+            list_changed(L, s);
         }
     });
     double out[6];
@@ -389,6 +431,7 @@ template <int PREC>
 __global__ void __launch_bounds__(PB) k_remap_create(Lattice L) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
+    if (*L.nb_chg <= NB_CHG_CAP) return;  // the list kernel does it
     int p = blockIdx.x;
     PGeo<C> g = pgeo<C>(L, p, REMAP_PAD);
     CSum<C> acc[6];
@@ -441,6 +484,7 @@ __global__ void __launch_bounds__(PB) k_remap_create(Lattice L) {
 template <int PREC>
 __global__ void __launch_bounds__(PB) k_remap_commit(Lattice L) {
     typedef typename Prec<PREC>::C C;
+    if (*L.nb_chg <= NB_CHG_CAP) return;  // the list kernel does it
     int p = blockIdx.x;
     PGeo<C> g = pgeo<C>(L, p, REMAP_PAD);
     for_band<C>(L, g, -0.65f, 0.65f, [&](int, int, int, long long s, int, int, int, const C (&d)[3]) {
@@ -455,13 +499,77 @@ __global__ void __launch_bounds__(PB) k_remap_commit(Lattice L) {
             L.owner[s] = -1;
             L.mask[s] = 0;
             L.evt[s] = 0;
-        } else {
-            return;
         }
-        // list the node for the link classes around it
-        const int q = atomicAdd(L.nb_chg, 1);
-        if (q < NB_CHG_CAP) L.nb_chg[8 + q] = (int)s;
     });
+}
+
+// The refill (Eq. 25) of the listed nodes a particle released, one thread
+// per listed node (k_remap_create's work when the list is complete): the
+// momentum (rhobar) u_w each one carries off its particle is added to F_c,
+// T_c as its own fixed-point term.
+template <int PREC>
+__global__ void k_remap_create_list(Lattice L) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    const int cnt = *L.nb_chg;
+    if (cnt > NB_CHG_CAP) return;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+        const long long s = L.nb_chg[8 + t];
+        const int code = L.evt[s];
+        if ((code & 3) != 2) continue;
+        const int p = code / 4 - 1;
+        const long long xy = (long long)L.nx * L.ny;
+        const int Z = (int)(s / xy), r = (int)(s - (long long)Z * xy), Y = r / L.nx, X = r - Y * L.nx;
+        SiteNbr n = site_nbr(L, X, Y, Z);
+        C num[2] = {0, 0}, den = 0;
+        for (int i = 1; i < Q; i++) {
+            if (nbr_is_wall(n, i)) continue;
+            long long m = nbr_index(L, n, i);
+            if (L.owner[m] != -1 || L.evt[m] != 0) continue;
+            C w = wgt<C>(i);
+            num[0] += w * site_rho<PREC>(L, m, 0);
+            num[1] += w * site_rho<PREC>(L, m, 1);
+            den += w;
+        }
+        C rb[2];
+        for (int k = 0; k < 2; k++) rb[k] = den > C(0) ? num[k] / den : C(L.P.rho0[k]);
+        C d[3], v[3], w[3], wxd[3], uw[3];
+        particle_frame<C>(L, p, X, Y, Z, d, v, w);
+        crs<C>(w, d, wxd);
+        for (int m = 0; m < 3; m++) uw[m] = v[m] + wxd[m];
+        C uu = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
+        S* f = (S*)L.f_cur;
+        for (int k = 0; k < 2; k++)
+            for (int i = 0; i < Q; i++)
+                st_pop(f + pop_index(k * Q + i, s, L.pstride), feq<C>(i, rb[k], uw[0], uw[1], uw[2], uu),
+                       pop_shift<S, C>(L, k, i));
+        C rt = rb[0] + rb[1];
+        C mom[3] = {-rt * uw[0], -rt * uw[1], -rt * uw[2]}, tq[3];
+        crs<C>(d, mom, tq);
+        for (int m = 0; m < 3; m++) {
+            acc_add(L, acc_slot(L, ACC_FC, p, m), mom[m]);
+            acc_add(L, acc_slot(L, ACC_TC, p, m), tq[m]);
+        }
+    }
+}
+
+// Commit the listed nodes (k_remap_commit's work when the list is complete).
+__global__ void k_remap_commit_list(Lattice L) {
+    const int cnt = *L.nb_chg;
+    if (cnt > NB_CHG_CAP) return;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+        const long long s = L.nb_chg[8 + t];
+        const int e = L.evt[s], p = e / 4 - 1;
+        if ((e & 3) == 1) {
+            int old = atomicCAS(L.owner + s, -1, p);
+            if (old != -1) atomicOr(L.flags, FLAG_OVERLAP);
+            L.mask[s] = 1;
+        } else if ((e & 3) == 2) {
+            L.owner[s] = -1;
+            L.mask[s] = 0;
+        }
+        L.evt[s] = 0;
+    }
 }
 
 // The link-class word of site s = (x, y, z) from the node map (NB_*).
@@ -547,14 +655,15 @@ __device__ __forceinline__ uint32_t nbr_solid(const Lattice& L, const SiteNbr& n
 // neighbours (with the Janus switch s of the node: 1 + s zeta^A, 1 - s zeta^B)
 // neighbours, and Eq. 21 (repulsive sign):
 // F_s = -G sum_k psi^k(s) sum w_i rho^kbar(s + c_i) c_i, added with its torque
-// (x_s - r_p) x F_s to F_s, T_s of the owning particle with FP64 atomics (the
-// step zeroes them in launch_remap).  A block loads psi^k and the owner map
-// of a 32 x 8 tile (+ one-site ring) for all planes of its z chunk (+ one on
-// each side) into shared memory in one batch, 12 bytes per site in coalesced
-// rows; the particle nodes of the chunk are then packed onto consecutive
-// threads, so that the per-node work runs with all lanes busy, and each
-// takes its fluid neighbours from shared memory.  The densities rho^k of the
-// fluid nodes are those of the full density pass of this step (k_density).
+// (x_s - r_p) x F_s to the fixed-point sums F_s, T_s of the owning particle
+// (the step zeroes them in launch_remap).  A block loads psi^k and the owner
+// map of a 32 x 8 tile (+ one-site ring) for all planes of its z chunk (+ one
+// on each side) into shared memory in one batch, 12 bytes per site in
+// coalesced rows; the frontier nodes of the chunk (from the link classes)
+// are then packed onto consecutive threads, so that the per-node work runs
+// with all lanes busy, and each takes its fluid neighbours from shared
+// memory.  The densities rho^k of the fluid nodes are those of the full
+// density pass of this step (k_density).
 constexpr int VTX = 32, VTY = 8, VZC = 8;  // tile and planes per block
 
 template <int PREC>
@@ -568,6 +677,7 @@ __global__ void __launch_bounds__(VTX* VTY) k_virtual(Lattice L, int store_terms
     C (*spb)[VTY + 2][VTX + 2] = spa + NPL;
     __shared__ int cand[NT * VZC];
     __shared__ int wcnt[NT / 32];
+
     const int x0 = blockIdx.x * VTX, y0 = blockIdx.y * VTY;
     const int W = min(VTX, L.nx - x0), H = min(VTY, L.ny - y0);
     const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, L.nz), nz_b = z1 - z0;
@@ -614,13 +724,20 @@ __global__ void __launch_bounds__(VTX* VTY) k_virtual(Lattice L, int store_terms
         if (act) put(ty + 1, tx + 1, zoff + own_xy);
         if (has_ring) put(rly + 1, rlx + 1, zoff + ring_xy);
     }
+    // the frontier nodes of the tile's own column (a particle node with a
+    // fluid neighbour: its link classes), one bit per plane of the chunk
+    unsigned front = 0;
+    if (act)
+        for (int q = 1; q <= nz_b; q++) {
+            const uint32_t c = L.nb[nxy * (z0 + q - 1) + own_xy];
+            front |= (unsigned)((c & NB_SOLID) && (c & NB_LINKS)) << q;
+        }
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
-    // the particle nodes of the chunk, packed onto consecutive threads (in
+    // the frontier nodes of the chunk, packed onto consecutive threads (in
     // plane, warp and lane order: fixed by the geometry)
-    int mine = 0;
-    for (int q = 1; q <= nz_b; q++) mine += act && snd[q][ty + 1][tx + 1] >= 0;
+    const int mine = __popc(front);
     int incl = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -636,69 +753,99 @@ __global__ void __launch_bounds__(VTX* VTY) k_virtual(Lattice L, int store_terms
         tot += wcnt[w];
     }
     for (int q = 1; q <= nz_b; q++)
-        if (act && snd[q][ty + 1][tx + 1] >= 0) cand[off++] = q * NT + tid;
+        if ((front >> q) & 1u) cand[off++] = q * NT + tid;
     __syncthreads();
     const C G = prm<C>(L.P.G, L.PF.G), zA = C(1) + C(L.P.zeta[0]), zB = C(1) + C(L.P.zeta[1]);
-    for (int k = tid; k < tot; k += NT) {
-        const int e = cand[k], q = e / NT, t = e - q * NT, cx0 = t % VTX, cy0 = t / VTX;
-        const int p = snd[q][cy0 + 1][cx0 + 1];
-        C num[2] = {0, 0}, den = 0;
-        C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};
+    // whole warps step through the list together (lanes past its end carry
+    // no term), so that a warp whose nodes all belong to one particle adds
+    // its terms with one set of atomics: the fixed-point words are summed
+    // across the warp first (exact integer sums, so the bits do not depend
+    // on the grouping)
+    for (int base = warp * 32; base < tot; base += NT) {
+        const int k = base + lane;
+        bool has = false;
+        int p = -1;
+        C fs[3] = {0, 0, 0}, tq[3] = {0, 0, 0};
+        if (k < tot) {
+            const int e = cand[k], q = e / NT, t = e - q * NT, cx0 = t % VTX, cy0 = t / VTX;
+            p = snd[q][cy0 + 1][cx0 + 1];
+            C num[2] = {0, 0}, den = 0;
+            C sA[3] = {0, 0, 0}, sB[3] = {0, 0, 0};
 #pragma unroll
-        for (int i = 1; i < Q; i++) {
-            const int a = q + cz(i), yy = cy0 + 1 + cy(i), xx = cx0 + 1 + cx(i);
-            const bool fl = snd[a][yy][xx] == ND_FLUID;
-            C ra = fl ? spa[a][yy][xx] : C(0), rb = fl ? spb[a][yy][xx] : C(0);
-            C w = fl ? wgt<C>(i) : C(0);
-            num[0] += w * ra;
-            num[1] += w * rb;
-            den += w;
-            sA[0] += w * ra * C(cx(i)); sA[1] += w * ra * C(cy(i)); sA[2] += w * ra * C(cz(i));
-            sB[0] += w * rb * C(cx(i)); sB[1] += w * rb * C(cy(i)); sB[2] += w * rb * C(cz(i));
-        }
-        if (!(den > C(0))) continue;
-        const int z = z0 + q - 1;
-        const long long s = nxy * z + (x0 + cx0) + (long long)L.nx * (y0 + cy0);
-        C fs[3], d[3], tq[3];
-        // x_s - r_p (minimum image) from the integer cell and offset of r_p
-        const int xs[3] = {x0 + cx0, y0 + cy0, z}, Ls[3] = {L.nx, L.ny, L.nz};
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            int ip;
-            C fr;
-            if (sizeof(C) == 8) {
-                double r = L.pos[3 * p + c];
-                ip = (int)floor(r);
-                fr = C(r - (double)ip);
-            } else {
-                ip = L.ipos[3 * p + c];
-                fr = C(L.fsnap[9 * p + c]);
+            for (int i = 1; i < Q; i++) {
+                const int a = q + cz(i), yy = cy0 + 1 + cy(i), xx = cx0 + 1 + cx(i);
+                const bool fl = snd[a][yy][xx] == ND_FLUID;
+                C ra = fl ? spa[a][yy][xx] : C(0), rb = fl ? spb[a][yy][xx] : C(0);
+                C w = fl ? wgt<C>(i) : C(0);
+                num[0] += w * ra;
+                num[1] += w * rb;
+                den += w;
+                sA[0] += w * ra * C(cx(i)); sA[1] += w * ra * C(cy(i)); sA[2] += w * ra * C(cz(i));
+                sB[0] += w * rb * C(cx(i)); sB[1] += w * rb * C(cy(i)); sB[2] += w * rb * C(cz(i));
             }
-            int dd = xs[c] - ip;
-            if (L.per[c]) {
-                if (2 * dd > Ls[c]) dd -= Ls[c];
-                else if (2 * dd < -Ls[c]) dd += Ls[c];
+            if (den > C(0)) {
+                const int z = z0 + q - 1;
+                const long long s = nxy * z + (x0 + cx0) + (long long)L.nx * (y0 + cy0);
+                C d[3];
+                // x_s - r_p (minimum image) from the integer cell and offset of r_p
+                const int xs[3] = {x0 + cx0, y0 + cy0, z}, Ls[3] = {L.nx, L.ny, L.nz};
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    int ip;
+                    C fr;
+                    if (sizeof(C) == 8) {
+                        double r = L.pos[3 * p + c];
+                        ip = (int)floor(r);
+                        fr = C(r - (double)ip);
+                    } else {
+                        ip = L.ipos[3 * p + c];
+                        fr = C(L.fsnap[9 * p + c]);
+                    }
+                    int dd = xs[c] - ip;
+                    if (L.per[c]) {
+                        if (2 * dd > Ls[c]) dd -= Ls[c];
+                        else if (2 * dd < -Ls[c]) dd += Ls[c];
+                    }
+                    d[c] = C(dd) - fr;
+                }
+                C fa = zA, fb = zB;
+                if (L.P.janus) {
+                    const C sw = janus_switch<C>(L, p, d);
+                    fa = C(1) + sw * C(L.P.zeta[0]);
+                    fb = C(1) - sw * C(L.P.zeta[1]);
+                }
+                const C pa = fa * num[0] / den;
+                const C pb = fb * num[1] / den;
+                psi[s] = pa;
+                psi[L.N + s] = pb;
+                if (store_terms) {
+#pragma unroll
+                    for (int c = 0; c < 3; c++) fs[c] = -G * pa * sB[c] + -G * pb * sA[c];
+                    crs<C>(d, fs, tq);
+                    has = true;
+                }
             }
-            d[c] = C(dd) - fr;
         }
-        C fa = zA, fb = zB;
-        if (L.P.janus) {
-            const C sw = janus_switch<C>(L, p, d);
-            fa = C(1) + sw * C(L.P.zeta[0]);
-            fb = C(1) - sw * C(L.P.zeta[1]);
-        }
-        const C pa = fa * num[0] / den;
-        const C pb = fb * num[1] / den;
-        psi[s] = pa;
-        psi[L.N + s] = pb;
-        if (!store_terms) continue;
+        if (!store_terms) continue;  // uniform across the block
+        const unsigned any = __ballot_sync(0xffffffffu, has);
+        if (!any) continue;
+        const int p0 = __shfl_sync(0xffffffffu, p, __ffs(any) - 1);
+        const bool one = __all_sync(0xffffffffu, !has || p == p0);
 #pragma unroll
-        for (int c = 0; c < 3; c++) fs[c] = -G * pa * sB[c] + -G * pb * sA[c];
-        crs<C>(d, fs, tq);
+        for (int m = 0; m < 6; m++) {
+            const C v = m < 3 ? fs[m] : tq[m - 3];
+            unsigned long long w[2] = {0ull, 0ull};
+            if (has && !acc_words(L, v, w)) w[0] = w[1] = 0ull;
+            if (!one) {
+                if (has) acc_add_words(L, acc_slot(L, m < 3 ? ACC_FS : ACC_TS, p, m % 3), w);
+                continue;
+            }
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-            acc_add(L, acc_slot(L, ACC_FS, p, c), fs[c]);
-            acc_add(L, acc_slot(L, ACC_TS, p, c), tq[c]);
+            for (int o = 16; o > 0; o >>= 1) {
+                w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
+                w[1] += __shfl_xor_sync(0xffffffffu, w[1], o);
+            }
+            if (lane == 0) acc_add_words(L, acc_slot(L, m < 3 ? ACC_FS : ACC_TS, p0, m % 3), w);
         }
     }
 }
@@ -1045,9 +1192,14 @@ int launch_remap(const Lattice& L, int prec, int maxc, cudaStream_t st) {
     cudaMemsetAsync(L.nb_chg, 0, sizeof(int), st);
     const dim3 grid((unsigned)L.nc, REMAP_GROUPS);
     DISPATCHC(prec, (k_remap_classify<P><<<grid, PBLK, 0, st>>>(L)));
+    // the refill and the commit of the listed nodes; the per-particle shell
+    // scans return at once unless the list overflowed
+    const unsigned lg = (unsigned)(2 * device_sms());
+    DISPATCHC(prec, (k_remap_create_list<P><<<lg, 128, 0, st>>>(L)));
     DISPATCHC(prec, (k_remap_create<P><<<grid, PBLK, 0, st>>>(L)));
+    k_remap_commit_list<<<lg, 128, 0, st>>>(L);
     DISPATCHC(prec, (k_remap_commit<P><<<grid, PBLK, 0, st>>>(L)));
-    return 3;
+    return 5;
 }
 
 int launch_link_classes(const Lattice& L, bool full, cudaStream_t st) {

@@ -533,27 +533,49 @@ __device__ __forceinline__ unsigned long long* acc_slot(const Lattice& L, int te
 // A term outside the range of its format (or not finite) is flagged as a
 // non-finite state and not added.
 // FP32 terms come from FP32 / FP16 contexts only.
-__device__ __forceinline__ void acc_add(const Lattice& L, unsigned long long* a, float v) {
+// The words acc_add adds for v (w[1] = 0 in the one-word format); false
+// (and the flag raised) if v is out of range.
+__device__ __forceinline__ bool acc_words(const Lattice& L, float v, unsigned long long (&w)[2]) {
     if (!(fabsf(v) < 8388608.0f)) {  // 2^23
         atomicOr(L.flags, FLAG_NONFINITE);
-        return;
+        return false;
     }
-    atomicAdd(a, (unsigned long long)__float2ll_rn(v * 1099511627776.0f));  // 2^40
+    w[0] = (unsigned long long)__float2ll_rn(v * 1099511627776.0f);  // 2^40
+    w[1] = 0;
+    return true;
 }
 
-__device__ __forceinline__ void acc_add(const Lattice& L, unsigned long long* a, double v) {
+__device__ __forceinline__ bool acc_words(const Lattice& L, double v, unsigned long long (&w)[2]) {
     if (!(fabs(v) < (L.acc_wide ? 549755813888.0 : 8388608.0))) {  // 2^39 / 2^23
         atomicOr(L.flags, FLAG_NONFINITE);
-        return;
+        return false;
     }
     if (!L.acc_wide) {
-        atomicAdd(a, (unsigned long long)__double2ll_rn(v * 1099511627776.0));
-        return;
+        w[0] = (unsigned long long)__double2ll_rn(v * 1099511627776.0);
+        w[1] = 0;
+        return true;
     }
     const double h = floor(v * 16777216.0);           // 2^24
     const double r = v - h * 5.9604644775390625e-08;  // exact, in [0, 2^-24)
-    atomicAdd(a, (unsigned long long)__double2ll_rn(h));
-    atomicAdd(a + 1, (unsigned long long)__double2ll_rn(r * 18446744073709551616.0));
+    w[0] = (unsigned long long)__double2ll_rn(h);
+    w[1] = (unsigned long long)__double2ll_rn(r * 18446744073709551616.0);
+    return true;
+}
+
+__device__ __forceinline__ void acc_add_words(const Lattice& L, unsigned long long* a,
+                                              const unsigned long long (&w)[2]) {
+    atomicAdd(a, w[0]);
+    if (L.acc_wide) atomicAdd(a + 1, w[1]);
+}
+
+__device__ __forceinline__ void acc_add(const Lattice& L, unsigned long long* a, float v) {
+    unsigned long long w[2];
+    if (acc_words(L, v, w)) atomicAdd(a, w[0]);
+}
+
+__device__ __forceinline__ void acc_add(const Lattice& L, unsigned long long* a, double v) {
+    unsigned long long w[2];
+    if (acc_words(L, v, w)) acc_add_words(L, a, w);
 }
 
 __device__ __forceinline__ double acc_value(const Lattice& L, const unsigned long long* a) {
@@ -627,7 +649,10 @@ inline int kernel_setup(int threads, size_t smem) {
     const int dev = current_device();
     const unsigned long long id = current_context_id();
     if (id && ctx[dev].load(std::memory_order_acquire) == id) return per_sm[dev].load(std::memory_order_relaxed);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(FN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the opt-in beyond 48 KB counts the kernel's static shared memory too
+    cudaFuncAttributes fa;
+    const size_t stat = cudaFuncGetAttributes(&fa, FN) == cudaSuccess ? fa.sharedSizeBytes : 0;
+    if (smem + stat > 48 * 1024) cudaFuncSetAttribute(FN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, FN, threads, smem);
     n = n > 0 ? n : 1;

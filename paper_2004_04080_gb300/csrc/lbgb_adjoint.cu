@@ -139,12 +139,12 @@ __global__ void __launch_bounds__(128) k_adj_local(Lattice L, AdjArgs A) {
                     int Y = cy(i) == 0 ? n.y : (cy(i) > 0 ? n.yp : n.ym);
                     int side = cz(i) < 0 ? 0 : 1;
                     long long w = (long long)X + (long long)L.nx * Y;
-                    pa = pw[(side * 2 + 0) * nxy + w];
-                    pb = pw[(side * 2 + 1) * nxy + w];
+                    pa = pw[2 * (side * nxy + w)];
+                    pb = pw[2 * (side * nxy + w) + 1];
                 } else {
                     long long m = nbr_index(L, n, i);
-                    pa = psi[m];
-                    pb = psi[L.N + m];
+                    pa = psi[2 * m];
+                    pb = psi[2 * m + 1];
                 }
                 C w = wgt<C>(i);
                 SA[0] += C(cx(i)) * w * pa; SA[1] += C(cy(i)) * w * pa; SA[2] += C(cz(i)) * w * pa;
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(128) k_adj_gather(Lattice L, AdjArgs A) {
             for (int k = 0; k < 2; k++) {
                 C zk = C(1) + sk[k] * C(L.P.zeta[k]);
                 cf[k * L.N + s] = W > C(0) ? pb[k] * zk / W : C(0);
-                zp[k] = W > C(0) ? pb[k] * sk[k] * psi[k * L.N + s] / zk : C(0);
+                zp[k] = W > C(0) ? pb[k] * sk[k] * psi[2 * s + k] / zk : C(0);
             }
         }
     }

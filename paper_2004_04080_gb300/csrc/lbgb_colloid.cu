@@ -714,11 +714,11 @@ __global__ void __launch_bounds__(VTX* VTY) k_virtual(Lattice L, int store_terms
             }
             cp_async_4(&snd[q][ly][lx], L.owner + g);
             if (sizeof(C) == 8) {
-                cp_async_8(&spa[q][ly][lx], psi + g);
-                cp_async_8(&spb[q][ly][lx], psi + L.N + g);
+                cp_async_8(&spa[q][ly][lx], psi + 2 * g);
+                cp_async_8(&spb[q][ly][lx], psi + 2 * g + 1);
             } else {
-                cp_async_4(&spa[q][ly][lx], psi + g);
-                cp_async_4(&spb[q][ly][lx], psi + L.N + g);
+                cp_async_4(&spa[q][ly][lx], psi + 2 * g);
+                cp_async_4(&spb[q][ly][lx], psi + 2 * g + 1);
             }
         };
         if (act) put(ty + 1, tx + 1, zoff + own_xy);
@@ -816,8 +816,8 @@ __global__ void __launch_bounds__(VTX* VTY) k_virtual(Lattice L, int store_terms
                 }
                 const C pa = fa * num[0] / den;
                 const C pb = fb * num[1] / den;
-                psi[s] = pa;
-                psi[L.N + s] = pb;
+                psi[2 * s] = pa;
+                psi[2 * s + 1] = pb;
                 if (store_terms) {
 #pragma unroll
                     for (int c = 0; c < 3; c++) fs[c] = -G * pa * sB[c] + -G * pb * sA[c];

@@ -48,8 +48,8 @@ __global__ void k_density(Lattice L) {
     C* psi = (C*)L.psi;
     C* mom = (C*)L.mom;
     if (L.mask[s]) {
-        psi[s] = 0;
-        psi[L.N + s] = 0;
+        psi[2 * s] = 0;
+        psi[2 * s + 1] = 0;
         if (MOM)
 #pragma unroll
             for (int a = 0; a < 3; a++) mom[a * L.pstride + s] = 0;
@@ -71,8 +71,8 @@ __global__ void k_density(Lattice L) {
             }
         }
     }
-    psi[s] = rho[0];
-    psi[L.N + s] = rho[1];
+    psi[2 * s] = rho[0];
+    psi[2 * s + 1] = rho[1];
     if (MOM)
 #pragma unroll
         for (int d = 0; d < 3; d++) mom[d * L.pstride + s] = jt[0][d] + jt[1][d];
@@ -103,14 +103,14 @@ __global__ void k_wall_psi(Lattice L) {
         long long m = (long long)X + (long long)L.nx * ((long long)Y + (long long)L.ny * zf);
         if (L.mask[m]) continue;
         C w = wgt<C>(i);
-        num0 += w * psi[m];
-        num1 += w * psi[L.N + m];
+        num0 += w * psi[2 * m];
+        num1 += w * psi[2 * m + 1];
         den += w;
     }
     long long w = (long long)x + (long long)L.nx * y;
     const bool face = L.P.open[side] == 1 || L.P.open[side] == 3;  // a pressure or equilibrium face
-    pw[(side * 2 + 0) * nxy + w] = face ? C(L.P.open_rho[side][0]) : (den > C(0) ? num0 / den : C(0));
-    pw[(side * 2 + 1) * nxy + w] = face ? C(L.P.open_rho[side][1]) : (den > C(0) ? num1 / den : C(0));
+    pw[2 * (side * nxy + w)] = face ? C(L.P.open_rho[side][0]) : (den > C(0) ? num0 / den : C(0));
+    pw[2 * (side * nxy + w) + 1] = face ? C(L.P.open_rho[side][1]) : (den > C(0) ? num1 / den : C(0));
 }
 
 // Add the link force and torque of one site (Eqs. 22, 23) to the fixed-point
@@ -212,8 +212,8 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
             X = X < 0 ? X + L.nx : (X >= L.nx ? X - L.nx : X);
             Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
             long long w = (long long)X + (long long)L.nx * Y;
-            sh.psi[slot][0][ly + 1][lx + 1] = pw[(side * 2 + 0) * nxy + w];
-            sh.psi[slot][1][ly + 1][lx + 1] = pw[(side * 2 + 1) * nxy + w];
+            sh.psi[slot][0][ly + 1][lx + 1] = pw[2 * (side * nxy + w)];
+            sh.psi[slot][1][ly + 1][lx + 1] = pw[2 * (side * nxy + w) + 1];
             sh.nd[slot][ly + 1][lx + 1] = ND_WALL;
         }
         return false;
@@ -223,8 +223,8 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
     if (tx < W && ty < H) {
         long long s = (long long)(x0 + tx) + (long long)L.nx * (y0 + ty) + zoff;
         if (L.mask[s]) {
-            sh.psi[slot][0][ty + 1][tx + 1] = psi[s];
-            sh.psi[slot][1][ty + 1][tx + 1] = psi[L.N + s];
+            sh.psi[slot][0][ty + 1][tx + 1] = psi[2 * s];
+            sh.psi[slot][1][ty + 1][tx + 1] = psi[2 * s + 1];
             sh.nd[slot][ty + 1][tx + 1] = L.owner[s];
             // a particle node collides on finite placeholder moments (its
             // stores write the rest equilibrium)
@@ -273,12 +273,12 @@ __device__ __forceinline__ bool fill_plane(const Lattice& L, FusedShared<PREC>& 
         C r0, r1;
         int nd;
         if (L.mask[s]) {
-            r0 = psi[s];
-            r1 = psi[L.N + s];
+            r0 = psi[2 * s];
+            r1 = psi[2 * s + 1];
             nd = L.owner[s];
         } else if (L.dense_psi) {
-            r0 = psi[s];
-            r1 = psi[L.N + s];
+            r0 = psi[2 * s];
+            r1 = psi[2 * s + 1];
             nd = ND_FLUID;
         } else {
             r0 = 0;
@@ -689,15 +689,15 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fu
     auto issue_psi = [&](int p) {
         int slot = slot_of(p);
         if ((p < 0 || p >= L.nz) && !L.per[2]) {
-            const C* pw = (const C*)L.psi_wall + (p < 0 ? 0 : 2) * nxy;
+            const C* pw = (const C*)L.psi_wall + 2 * (p < 0 ? 0 : nxy);
             if (act) {
-                sh.psi[slot][0][ty + 1][tx + 1] = pw[own_xy];
-                sh.psi[slot][1][ty + 1][tx + 1] = pw[nxy + own_xy];
+                sh.psi[slot][0][ty + 1][tx + 1] = pw[2 * own_xy];
+                sh.psi[slot][1][ty + 1][tx + 1] = pw[2 * own_xy + 1];
                 sh.nd[slot][ty + 1][tx + 1] = ND_WALL;
             }
             if (has_ring) {
-                sh.psi[slot][0][rly + 1][rlx + 1] = pw[ring_xy];
-                sh.psi[slot][1][rly + 1][rlx + 1] = pw[nxy + ring_xy];
+                sh.psi[slot][0][rly + 1][rlx + 1] = pw[2 * ring_xy];
+                sh.psi[slot][1][rly + 1][rlx + 1] = pw[2 * ring_xy + 1];
                 sh.nd[slot][rly + 1][rlx + 1] = ND_WALL;
             }
             return;
@@ -708,11 +708,11 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fu
         auto put = [&](int ly, int lx, long long g) {
             cp_async_4(&sh.nd[slot][ly][lx], L.owner + g);
             if (sizeof(C) == 8) {
-                cp_async_8(&sh.psi[slot][0][ly][lx], psig + g);
-                cp_async_8(&sh.psi[slot][1][ly][lx], psig + L.N + g);
+                cp_async_8(&sh.psi[slot][0][ly][lx], psig + 2 * g);
+                cp_async_8(&sh.psi[slot][1][ly][lx], psig + 2 * g + 1);
             } else {
-                cp_async_4(&sh.psi[slot][0][ly][lx], psig + g);
-                cp_async_4(&sh.psi[slot][1][ly][lx], psig + L.N + g);
+                cp_async_4(&sh.psi[slot][0][ly][lx], psig + 2 * g);
+                cp_async_4(&sh.psi[slot][1][ly][lx], psig + 2 * g + 1);
             }
         };
         if (act) put(ty + 1, tx + 1, zoff + own_xy);
@@ -808,11 +808,16 @@ constexpr int WPB = 4;     // warps (rows) per block of the lean kernel
 template <int PREC>
 struct alignas(16) LeanShared {
     typedef typename Prec<PREC>::C C;
+    C pad_[2];                   // puts column 1 (the tile's first site) on a 16-byte boundary
     C psi[WNSLOT][3][RW][2];     // psi^A, psi^B side by side: one shared load per neighbour
     alignas(16) C j[2][3][FTX];  // j^A + j^B; 16-byte copies land here
 };
 static_assert(offsetof(LeanShared<LB_FP32>, j) % 16 == 0 && sizeof(LeanShared<LB_FP32>) % 16 == 0, "alignment");
 static_assert(offsetof(LeanShared<LB_FP64>, j) % 16 == 0 && sizeof(LeanShared<LB_FP64>) % 16 == 0, "alignment");
+// 16-byte chunks land on column 1 + k SPC of a row
+static_assert((offsetof(LeanShared<LB_FP32>, psi) + 2 * sizeof(float)) % 16 == 0 && (RW * 2 * sizeof(float)) % 16 == 0,
+              "alignment");
+static_assert((offsetof(LeanShared<LB_FP64>, psi) + 2 * sizeof(double)) % 16 == 0, "alignment");
 
 // The link forces and torques of one lane summed over the planes of its
 // march while they go to one particle p, added to p's fixed-point sums
@@ -1031,43 +1036,43 @@ __global__ void __launch_bounds__(FTX* WPB, (PREC == LB_FP64 ? 1 : (PREC == LB_F
     const long long nxy = (long long)L.nx * L.ny;
     const C* psig = (const C*)L.psi;
     auto slot_of = [&](int p) { return (p - z0 + 1) % WNSLOT; };
-    // the (3 rows) x (W + 2 columns) staged positions, up to 4 per lane
-    int pxy[4], prow[4], pcol[4];
-    bool pon[4];
+    // the psi pairs of the rows y-1, y, y+1 of a plane, as copies of 16-byte
+    // chunks (SPC sites each) of the tile's columns and one pair on each side
+    // (the periodic images at the lattice edges): 3 (W / SPC + 2) copies, at
+    // most two per lane, fixed for the whole march
+    constexpr int SPC = 16 / (2 * (int)sizeof(C));
+    constexpr int NR = (3 * (FTX / SPC + 2) + 31) / 32;  // copies per lane: 2 (FP32, FP16), 4 (FP64)
+    const int nch = W / SPC, per_row = nch + 2;          // W is a multiple of 4 (nx is)
+    int jsm[NR], jxy[NR];
+    bool jon[NR], jck[NR];
 #pragma unroll
-    for (int r = 0; r < 4; r++) {
-        const int q = tx + 32 * r;
-        pon[r] = q < 3 * (W + 2);
-        prow[r] = pon[r] ? q / (W + 2) : 0;
-        pcol[r] = pon[r] ? q % (W + 2) : 0;
-        int X = x0 + pcol[r] - 1, Y = y + prow[r] - 1;
-        X = X < 0 ? X + L.nx : (X >= L.nx ? X - L.nx : X);
+    for (int r = 0; r < NR; r++) {
+        const int j = tx + 32 * r, row = j / per_row, e = j - row * per_row;
+        jon[r] = j < 3 * per_row;
+        jck[r] = e < nch;
+        int Y = y + row - 1;
         Y = Y < 0 ? Y + L.ny : (Y >= L.ny ? Y - L.ny : Y);
-        pxy[r] = X + L.nx * Y;
+        int X = e < nch ? x0 + e * SPC : (e == nch ? x0 - 1 : x0 + W);
+        X = X < 0 ? X + L.nx : (X >= L.nx ? X - L.nx : X);
+        const int col = e < nch ? 1 + e * SPC : (e == nch ? 0 : W + 1);
+        jsm[r] = jon[r] ? (row * RW + col) * 2 : 0;  // element of the slot
+        jxy[r] = X + L.nx * Y;
     }
     auto issue_psi = [&](int p) {
         const int slot = slot_of(p);
         const bool wall = (p < 0 || p >= L.nz) && !L.per[2];
-        const C* pw = (const C*)L.psi_wall + (p < 0 ? 0 : 2) * nxy;
         const int Z = p < 0 ? p + L.nz : (p >= L.nz ? p - L.nz : p);
-        const long long zoff = nxy * Z;
+        // a plane beyond a wall stages the wall densities (pairs as well)
+        const C* base = wall ? (const C*)L.psi_wall + 2 * (p < 0 ? 0 : nxy) : psig + 2 * nxy * Z;
 #pragma unroll
-        for (int r = 0; r < 4; r++) {
-            if (!pon[r]) continue;
-            const int a = prow[r], c = pcol[r];
-            if (wall) {
-                sh.psi[slot][a][c][0] = pw[pxy[r]];
-                sh.psi[slot][a][c][1] = pw[nxy + pxy[r]];
-                continue;
-            }
-            const long long g = zoff + pxy[r];
-            if (sizeof(C) == 8) {
-                cp_async_8(&sh.psi[slot][a][c][0], psig + g);
-                cp_async_8(&sh.psi[slot][a][c][1], psig + L.N + g);
-            } else {
-                cp_async_4(&sh.psi[slot][a][c][0], psig + g);
-                cp_async_4(&sh.psi[slot][a][c][1], psig + L.N + g);
-            }
+        for (int r = 0; r < NR; r++) {
+            if (!jon[r]) continue;
+            C* dst = &sh.psi[slot][0][0][0] + jsm[r];
+            const C* src = base + 2 * (long long)jxy[r];
+            if (SPC == 1 || jck[r])
+                cp_async_16(dst, src);  // a chunk of the tile's columns (FP64: one pair)
+            else
+                cp_async_8(dst, src);   // a pair of the ring (FP32 / FP16)
         }
     };
     // momentum rows of plane p: 16-byte chunks, lane -> chunk tx % LPR of
@@ -1149,7 +1154,7 @@ __device__ __forceinline__ void face_rule(const Lattice& L, int face, int i, con
     const float* uwf = face == 0 ? L.PF.wall_u_lo : L.PF.wall_u_hi;
     const C uw[3] = {prm<C>(uwd[0], uwf[0]), prm<C>(uwd[1], uwf[1]), prm<C>(uwd[2], uwf[2])};
     const int type = L.P.open[face];
-    C rho[2] = {psi[x], psi[L.N + x]};
+    C rho[2] = {psi[2 * x], psi[2 * x + 1]};
     C fb[2];
     if (type == 1) {
         // Eq. 14 at tau_A = tau_B from the total momentum of the density pass
@@ -1238,8 +1243,8 @@ __global__ void k_wall_plane_density(Lattice L) {
         r0 += ld_pop(f + pop_index(i, s, L.pstride), pop_shift<S, C>(L, 0, i));
         r1 += ld_pop(f + pop_index(Q + i, s, L.pstride), pop_shift<S, C>(L, 1, i));
     }
-    psi[s] = r0;
-    psi[L.N + s] = r1;
+    psi[2 * s] = r0;
+    psi[2 * s + 1] = r1;
 }
 
 // rho^A, rho^B and u = sum_k (j^k + F^k/2)/rho into stage [5][N] (FP64)

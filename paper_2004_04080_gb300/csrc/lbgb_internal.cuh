@@ -225,8 +225,8 @@ struct Lattice {
     int per[3];        // periodic flags
     void* f_cur;       // populations at time t: [19][pstride][2] of S (pair_index)
     void* f_nxt;       // populations at time t+1
-    void* psi;         // [2][N] of C: rho^k on fluid, virtual density on frontier
-    void* psi_wall;    // [2 walls][2 comps][nx*ny] of C
+    void* psi;         // [N][2] of C: (psi^A, psi^B) of a site side by side; rho^k on fluid, virtual density on frontier
+    void* psi_wall;    // [2 walls][nx*ny][2 comps] of C (pairs, like psi)
     uint8_t* mask;     // 1 on particle nodes
     int* owner;        // -1 fluid, else particle index
     int* evt;          // remap events: 4 (p+1) + 1 destroy, 4 (p+1) + 2 create
@@ -384,12 +384,12 @@ __device__ __forceinline__ void sc_force(const Lattice& L, const SiteNbr& n, con
             int Y = cy(i) == 0 ? n.y : (cy(i) > 0 ? n.yp : n.ym);
             int side = cz(i) < 0 ? 0 : 1;
             long long w = (long long)X + (long long)L.nx * Y;
-            pa = pw[(side * 2 + 0) * nxy + w];
-            pb = pw[(side * 2 + 1) * nxy + w];
+            pa = pw[2 * (side * nxy + w)];
+            pb = pw[2 * (side * nxy + w) + 1];
         } else {
             long long m = nbr_index(L, n, i);
-            pa = __ldg(psi + m);
-            pb = __ldg(psi + L.N + m);
+            pa = __ldg(psi + 2 * m);
+            pb = __ldg(psi + 2 * m + 1);
         }
         C w = wgt<C>(i);
         if (cx(i)) { sA[0] += C(cx(i)) * w * pa; sB[0] += C(cx(i)) * w * pb; }

@@ -673,8 +673,9 @@ __global__ void __launch_bounds__(VTX* VTY) k_virtual(Lattice L, int store_terms
     extern __shared__ __align__(16) unsigned char vsm[];
     // planes z0-1 .. z0+zc of the tile + ring: node codes, then psi^A, psi^B
     int (*snd)[VTY + 2][VTX + 2] = reinterpret_cast<int (*)[VTY + 2][VTX + 2]>(vsm);
-    C (*spa)[VTY + 2][VTX + 2] = reinterpret_cast<C (*)[VTY + 2][VTX + 2]>(vsm + sizeof(int) * NPL * (VTY + 2) * (VTX + 2));
-    C (*spb)[VTY + 2][VTX + 2] = spa + NPL;
+    // (psi^A, psi^B) pairs after the node codes (whose size is a multiple of 16 bytes)
+    C (*sp)[VTY + 2][VTX + 2][2] =
+        reinterpret_cast<C (*)[VTY + 2][VTX + 2][2]>(vsm + sizeof(int) * NPL * (VTY + 2) * (VTX + 2));
     __shared__ int cand[NT * VZC];
     __shared__ int wcnt[NT / 32];
 
@@ -709,16 +710,14 @@ __global__ void __launch_bounds__(VTX* VTY) k_virtual(Lattice L, int store_terms
         auto put = [&](int ly, int lx, long long g) {
             if (wall) {
                 snd[q][ly][lx] = ND_WALL;
-                spa[q][ly][lx] = spb[q][ly][lx] = C(0);
+                sp[q][ly][lx][0] = sp[q][ly][lx][1] = C(0);
                 return;
             }
             cp_async_4(&snd[q][ly][lx], L.owner + g);
             if (sizeof(C) == 8) {
-                cp_async_8(&spa[q][ly][lx], psi + 2 * g);
-                cp_async_8(&spb[q][ly][lx], psi + 2 * g + 1);
+                cp_async_16(&sp[q][ly][lx][0], psi + 2 * g);
             } else {
-                cp_async_4(&spa[q][ly][lx], psi + 2 * g);
-                cp_async_4(&spb[q][ly][lx], psi + 2 * g + 1);
+                cp_async_8(&sp[q][ly][lx][0], psi + 2 * g);
             }
         };
         if (act) put(ty + 1, tx + 1, zoff + own_xy);
@@ -775,7 +774,7 @@ __global__ void __launch_bounds__(VTX* VTY) k_virtual(Lattice L, int store_terms
             for (int i = 1; i < Q; i++) {
                 const int a = q + cz(i), yy = cy0 + 1 + cy(i), xx = cx0 + 1 + cx(i);
                 const bool fl = snd[a][yy][xx] == ND_FLUID;
-                C ra = fl ? spa[a][yy][xx] : C(0), rb = fl ? spb[a][yy][xx] : C(0);
+                C ra = fl ? sp[a][yy][xx][0] : C(0), rb = fl ? sp[a][yy][xx][1] : C(0);
                 C w = fl ? wgt<C>(i) : C(0);
                 num[0] += w * ra;
                 num[1] += w * rb;

@@ -65,6 +65,13 @@
  *    z = nz - 1/2 moving with a fixed velocity (Eq. 9 with the local density);
  *    for the Shan-Chen force a wall node carries the w_i-weighted mean density
  *    of its fluid neighbours ("wetting mode 0", neutral).
+ *  - Open z faces (Sec. 2.2): a pressure face (Eq. 10) with a given rho_w
+ *    and u_w the velocity of the boundary node (Eq. 14); a velocity face
+ *    (Eq. 9) with the density of the boundary node; an equilibrium face that
+ *    sends in f^eq(rho_w, u_w).  With open_extrap the face values of the
+ *    first two are extrapolated from the boundary node b and the next
+ *    interior node b+1, q_w = q_b + (q_b - q_{b+1})/2 (Sec. 2.2), where b+1
+ *    exists and is fluid.
  *  - Soft harmonic side wall on particles: F_z = k (d - h) away from the wall
  *    when the centre is closer than d to a wall plane (h = distance).
  *  - First step: F_liq(-1/2) := F_liq(+1/2) (Eq. 35).
@@ -143,6 +150,9 @@ typedef struct {
     int open[2];                       /* z faces (lo, hi) with walls: 0 wall,
                                           1 pressure, 2 velocity, 3 equilibrium */
     double open_rho[2][2];             /* face density per component        */
+    int open_extrap;                   /* 1: the face values of pressure and
+                                          velocity faces extrapolated to first
+                                          order from the next interior node   */
 } orc_params;
 
 /* Neumaier compensated sum */
@@ -338,6 +348,8 @@ int orc_set_params(orc_t *o, const orc_params *p)
         return ORC_ERR_ARG;
     if (p->open[0] < 0 || p->open[0] > 3 || p->open[1] < 0 || p->open[1] > 3)
         return ORC_ERR_ARG;
+    if (p->open_extrap != 0 && p->open_extrap != 1)
+        return ORC_ERR_ARG;
     o->P = *p;
     o->have_params = 1;
     return ORC_OK;
@@ -409,6 +421,53 @@ static void mix_velocity(const orc_t *o, long s, double u[3])
     int d;
     for (d = 0; d < 3; d++)
         u[d] = (w0 * o->jm[0][d * N + s] + w1 * o->jm[1][d * N + s]) / den;
+}
+
+/* The next interior node r_{b+1} of the boundary node s on z face `side`
+ * (Sec. 2.2: one site inward along the face normal), or -1 where the face
+ * values are not extrapolated: extrapolation off, no such node (nz < 2), or
+ * a particle node there. */
+static long next_interior(const orc_t *o, long s, int side)
+{
+    int x, y, z, zi;
+    long n;
+    if (!o->P.open_extrap)
+        return -1;
+    coords(o, s, &x, &y, &z);
+    zi = side == 0 ? z + 1 : z - 1;
+    if (zi < 0 || zi >= o->nz)
+        return -1;
+    n = site(o, x, y, zi);
+    return o->owner[n] < 0 ? n : -1;
+}
+
+/* rho_w^k of a velocity face (Eq. 9): the first-order extrapolation of
+ * Sec. 2.2, rho_w = rho(r_b) + [rho(r_b) - rho(r_{b+1})] / 2, else the
+ * density of the boundary node */
+static double face_density(const orc_t *o, long s, int side, int k)
+{
+    long n = next_interior(o, s, side);
+    if (n < 0)
+        return o->rho[k][s];
+    return o->rho[k][s] + 0.5 * (o->rho[k][s] - o->rho[k][n]);
+}
+
+/* u_w of a pressure face (Eq. 10): the same extrapolation of the velocity
+ * of Eq. 14, else the velocity of the boundary node */
+static void face_velocity(const orc_t *o, long s, int side, double u[3])
+{
+    long n = next_interior(o, s, side);
+    double ub[3], ui[3];
+    int d;
+    mix_velocity(o, s, ub);
+    if (n < 0) {
+        for (d = 0; d < 3; d++)
+            u[d] = ub[d];
+        return;
+    }
+    mix_velocity(o, n, ui);
+    for (d = 0; d < 3; d++)
+        u[d] = ub[d] + 0.5 * (ub[d] - ui[d]);
 }
 
 /* position of site s relative to particle p (minimum image), plus offset */
@@ -860,9 +919,10 @@ static void bounce_and_stream(orc_t *o)
                 double cu = CX[i] * uw[0] + CY[i] * uw[1] + CZ[i] * uw[2];
                 if (type == 1) {
                     /* pressure face (Eq. 10, anti-bounce-back): rho_w given,
-                     * u_w the velocity of the boundary node (Eq. 14) */
+                     * u_w the velocity of the boundary node (Eq. 14), or its
+                     * first-order extrapolation to the face */
                     double um[3], cum, uu;
-                    mix_velocity(o, s, um);
+                    face_velocity(o, s, side, um);
                     cum = CX[i] * um[0] + CY[i] * um[1] + CZ[i] * um[2];
                     uu = um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
                     for (k = 0; k < 2; k++)
@@ -876,10 +936,13 @@ static void bounce_and_stream(orc_t *o)
                     for (k = 0; k < 2; k++)
                         o->fnext[k][ib * N + s] = feq_i(ib, o->P.open_rho[side][k], uw);
                 } else {
-                    /* wall or velocity face (Eq. 9) */
-                    for (k = 0; k < 2; k++)
-                        o->fnext[k][ib * N + s] =
-                            o->fpost[k][i * N + s] - 2.0 * WT[i] * o->rho[k][s] * cu / CS2;
+                    /* wall or velocity face (Eq. 9); rho_w the density of
+                     * the boundary node, or on a velocity face its
+                     * first-order extrapolation to the face */
+                    for (k = 0; k < 2; k++) {
+                        double rw = type == 2 ? face_density(o, s, side, k) : o->rho[k][s];
+                        o->fnext[k][ib * N + s] = o->fpost[k][i * N + s] - 2.0 * WT[i] * rw * cu / CS2;
+                    }
                 }
             } else {
                 double off[3], rel[3], uw[3], cu, fl = 0.0, fv[3], tq[3];

@@ -51,6 +51,7 @@ class OrcParams(C.Structure):
         ("janus_width", C.c_double),
         ("open", C.c_int * 2),
         ("open_rho", C.c_double * 4),
+        ("open_extrap", C.c_int),
     ]
 
 
@@ -125,7 +126,9 @@ def _f64(a, shape=None):
 # the benchmark input (App. D) for when it is turned on; rcut and delr (App. A)
 # only size a neighbour list in the GPU library, so the oracle, which
 # evaluates every pair, accepts and ignores them; the z faces are walls unless
-# opened (Sec. 2.2: open=(lo, hi) types, open_rho = (lo A, lo B, hi A, hi B)).
+# opened (Sec. 2.2: open=(lo, hi) types, open_rho = (lo A, lo B, hi A, hi B)),
+# with the face values of pressure and velocity faces taken at the boundary
+# node unless open_extrap = 1 (first-order extrapolation, Sec. 2.2).
 DEFAULTS = dict(
     tau=(1.0, 1.0), G=0.0, zeta=(0.0, 0.0), rho0=(0.5, 0.5), bc=(1, 1, 1),
     wall_u_lo=(0.0, 0.0, 0.0), wall_u_hi=(0.0, 0.0, 0.0), body_force=(0.0, 0.0, 0.0),
@@ -134,7 +137,7 @@ DEFAULTS = dict(
     side_wall_k=0.0, side_wall_d=0.0, rotate=1,
     janus=0, janus_theta0=108.0, janus_width=10.0,
     rcut=0.0, delr=0.0,
-    open=(0, 0), open_rho=(1.0, 1.0, 1.0, 1.0),
+    open=(0, 0), open_rho=(1.0, 1.0, 1.0, 1.0), open_extrap=0,
 )
 
 

@@ -11,12 +11,17 @@ Boltzmann equations fix (CPU only):
   * a density drop between the faces drives fluid out of the dense face and
     into the light one, and leaves the sites beyond the reach of the
     populations exactly at rest;
-  * a velocity face is the moving wall of Eq. 9: bit for bit the wall run.
+  * a velocity face is the moving wall of Eq. 9: bit for bit the wall run;
+  * the first-order face extrapolation of Sec. 2.2 is exact for a linear
+    profile: after one step the populations a velocity face sends in carry
+    the density of a linear rho(z) at the face z = -1/2, and those of a
+    pressure face the velocity of a linear u(z) there; walls and
+    equilibrium faces ignore it (bit for bit).
 """
 import numpy as np
 import pytest
 
-from oracle import Oracle, feq
+from oracle import Oracle, feq, lattice
 
 
 def plug(shape, tau, G, rho0, u0, steps):
@@ -90,6 +95,95 @@ def test_velocity_face_is_the_moving_wall():
                      wall_u_hi=(-0.01, 0.01, 0))
         o.init_fields(a, b)
         o.step(30)
+        runs.append([o.populations(k) for k in range(2)])
+    for k in range(2):
+        assert np.array_equal(runs[0][k], runs[1][k])
+
+
+def _lattice():
+    """Directions in the oracle's numbering; the weights from |c|^2 (1/3,
+    1/18, 1/36 of D3Q19), not from the oracle."""
+    c, _w, opp = lattice()
+    w = np.array([{0: 1 / 3, 1: 1 / 18, 2: 1 / 36}[int(n)] for n in (c * c).sum(axis=1)])
+    return c, w, opp
+
+
+def _feq(i, c, w, rho, u):
+    cu = c[i] @ u
+    return w[i] * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (u @ u))
+
+
+def test_velocity_face_extrapolates_a_linear_density():
+    """rho^A(z) = a + b z, rho^B constant, at rest, tau = 1, G = 0: one step
+    later the population a velocity face (u_w) sends into a node of z = 0 is
+    f*_i - 6 w_i rho_w c_i.u_w with f*_i = w_i rho(0) and rho_w = a - b/2,
+    the profile's value at the face; without the extrapolation rho_w = a."""
+    shape = nx, ny, nz = (4, 3, 8)
+    N = nx * ny * nz
+    a_, b_, rb = 0.55, -0.015, 0.45
+    z = np.repeat(np.arange(nz), nx * ny)
+    uw = np.array([0.03, -0.02, 0.01])
+    c, w, opp = _lattice()
+    got = {}
+    for ex in (0, 1):
+        o = Oracle(*shape)
+        o.set_params(tau=(1.0, 1.0), bc=(1, 1, 0), open=(2, 0), wall_u_lo=tuple(uw), open_extrap=ex)
+        o.init_fields(a_ + b_ * z, np.full(N, rb))
+        o.step(1)
+        got[ex] = [o.populations(k) for k in range(2)]
+    face = z == 0
+    for i in np.nonzero(c[:, 2] == -1)[0]:
+        for ex, rw in ((1, a_ - b_ / 2), (0, a_)):
+            fa = got[ex][0][opp[i], face]
+            assert np.abs(fa - (w[i] * a_ - 6 * w[i] * rw * (c[i] @ uw))).max() < 1e-15
+            fb = got[ex][1][opp[i], face]
+            assert np.abs(fb - (w[i] * rb - 6 * w[i] * rb * (c[i] @ uw))).max() < 1e-15
+    # everything away from the face's incoming links is the same
+    keep = np.ones((19, N), dtype=bool)
+    keep[np.ix_(opp[c[:, 2] == -1], np.nonzero(face)[0])] = False
+    assert np.array_equal(got[0][0][keep], got[1][0][keep])
+
+
+def test_pressure_face_extrapolates_a_linear_velocity():
+    """u(z) = u0 + g z (a shear with a linear profile), uniform densities,
+    tau = 1, G = 0: one step later a pressure face sends into the nodes of
+    z = 0 the anti-bounce-back of Eq. 10, -f^eq_i(rho, u(0)) + 2 w_i rho_w
+    (1 + 9/2 (c_i.u_w)^2 - 3/2 u_w^2), with u_w = u0 - g/2 the profile's
+    velocity at the face; without the extrapolation u_w = u0."""
+    shape = nx, ny, nz = (4, 3, 8)
+    N = nx * ny * nz
+    z = np.repeat(np.arange(nz), nx * ny)
+    u0, g = np.array([0.02, -0.01, 0.015]), np.array([0.004, 0.003, -0.002])
+    u = u0[:, None] + g[:, None] * z[None, :]
+    rho = (0.5, 0.4)
+    rw = (0.6, 0.35)
+    c, w, opp = _lattice()
+    for ex, uw in ((1, u0 - g / 2), (0, u0)):
+        o = Oracle(*shape)
+        o.set_params(tau=(1.0, 1.0), bc=(1, 1, 0), open=(1, 0), open_rho=(rw[0], rw[1], 1.0, 1.0),
+                     open_extrap=ex)
+        o.init_fields(np.full(N, rho[0]), np.full(N, rho[1]), u)
+        o.step(1)
+        for k in range(2):
+            f = o.populations(k)
+            for i in np.nonzero(c[:, 2] == -1)[0]:
+                cu = c[i] @ uw
+                want = -_feq(i, c, w, rho[k], u0) + 2 * w[i] * rw[k] * (1 + 4.5 * cu * cu - 1.5 * (uw @ uw))
+                assert np.abs(f[opp[i], z == 0] - want).max() < 1e-15
+
+
+def test_extrapolation_leaves_walls_and_equilibrium_faces():
+    shape = (5, 4, 9)
+    N = 5 * 4 * 9
+    rng = np.random.default_rng(4)
+    a, b = 0.5 + 0.02 * rng.random(N), 0.5 + 0.02 * rng.random(N)
+    runs = []
+    for ex in (0, 1):
+        o = Oracle(*shape)
+        o.set_params(tau=(0.9, 1.1), G=0.5, bc=(1, 1, 0), open=(0, 3), wall_u_lo=(0.02, 0, 0),
+                     wall_u_hi=(-0.01, 0.01, 0.02), open_rho=(1.0, 1.0, 0.52, 0.49), open_extrap=ex)
+        o.init_fields(a, b)
+        o.step(20)
         runs.append([o.populations(k) for k in range(2)])
     for k in range(2):
         assert np.array_equal(runs[0][k], runs[1][k])

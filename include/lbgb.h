@@ -117,9 +117,16 @@ typedef struct {
      * the boundary node (the wall rule); 3 equilibrium: the incoming
      * populations are f^eq(open_rho[face][k], wall_u).  A pressure or
      * equilibrium face carries open_rho into the Shan-Chen force of Eq. 11.
-     * The adjoint accepts walls and velocity faces only. */
+     * open_extrap = 1 takes u_w of a pressure face and rho_w of a velocity
+     * face at the face itself, extrapolated to first order from the
+     * boundary node b and the next interior node b + 1 along z (Sec. 2.2):
+     * q_w = q_b + (q_b - q_{b+1}) / 2, with q_b alone where b + 1 is a
+     * particle node or nz < 2; 0 (the default) takes q_b.  Walls and
+     * equilibrium faces ignore it.  The adjoint accepts walls and velocity
+     * faces without extrapolation only. */
     int open[2];
     double open_rho[2][2];
+    int open_extrap;
 } lb_params;
 
 /* Device workspace size for a lattice; *bytes receives the size.  prec may

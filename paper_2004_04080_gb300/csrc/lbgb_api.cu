@@ -95,7 +95,7 @@ const int RED_BLOCKS = 1024;
 const int PROF_MAX = 16384;
 
 struct Layout {
-    size_t f0, f1, mom, psi, psi_wall, mask, owner, evt, nb, nb_chg, flags, col, prev, acc, vl, ipos, fsnap, cells,
+    size_t f0, f1, mom, psi, psi_wall, face, mask, owner, evt, nb, nb_chg, flags, col, prev, acc, vl, ipos, fsnap, cells,
         cells_bytes, red, totals, total;
     long long pstride;
 };
@@ -119,6 +119,7 @@ Layout layout(int nx, int ny, int nz, int prec, int maxc, int ncomp) {
     l.mom = off; off = align_up(off + (size_t)3 * (ncomp == 2 ? l.pstride : 0) * compute_bytes(prec));
     l.psi = off; off = align_up(off + (size_t)2 * Np * compute_bytes(prec));
     l.psi_wall = off; off = align_up(off + (size_t)4 * nx * ny * compute_bytes(prec));
+    l.face = off; off = align_up(off + (size_t)10 * nx * ny * compute_bytes(prec));
     l.mask = off; off = align_up(off + (size_t)Np);
     l.owner = off; off = align_up(off + (size_t)Np * 4);
     l.evt = off; off = align_up(off + (size_t)Np * 4);
@@ -258,6 +259,7 @@ int lb_create(int nx, int ny, int nz, int prec, int max_colloids, void* d_worksp
     L.mom = ctx->ws + l.mom;
     L.psi = ctx->ws + l.psi;
     L.psi_wall = ctx->ws + l.psi_wall;
+    L.face = ctx->ws + l.face;
     L.mask = (uint8_t*)(ctx->ws + l.mask);
     L.owner = (int*)(ctx->ws + l.owner);
     L.evt = (int*)(ctx->ws + l.evt);
@@ -348,6 +350,7 @@ int lb_set_params(lb_ctx* ctx, const lb_params* p) {
             if (!(p->open_rho[f][k] >= 0.0 && isfinite(p->open_rho[f][k])))
                 return set_err(ctx, LB_ERR_ARG, "open face densities must be finite and >= 0");
     }
+    if (p->open_extrap != 0 && p->open_extrap != 1) return set_err(ctx, LB_ERR_ARG, "open_extrap is 0 or 1");
     if (ctx->stepped && p->bc[2] != ctx->L.P.bc[2])
         return set_err(ctx, LB_ERR_STATE, "boundary conditions cannot change after stepping");
     ctx->L.P = *p;
@@ -509,8 +512,9 @@ int lb_step(lb_ctx* ctx, int nsteps) {
     for (int t = 0; L.ncomp == 1 && t < nsteps; t++) {
         // the one-component fluid: one kernel per step (Eqs. 5-7, 16, 3, 9)
         if (L.sr) L.sr_key = sr_key(ctx->sr_seed, ctx->sr_step++);
+        const int n0 = launch_single_face_values(L, ctx->prec, s);  // extrapolated face densities
         if (int rc = prof_mark(ctx, LB_KERNEL_FUSED, 0, s)) return rc;
-        const int n = launch_single_step(L, ctx->prec, s);
+        const int n = n0 + launch_single_step(L, ctx->prec, s);
         if (int rc = prof_mark(ctx, LB_KERNEL_FUSED, 1, s)) return rc;
         if (int rc = launched(ctx, n, "step kernel")) return rc;
         void* tmp = L.f_cur;
@@ -554,6 +558,7 @@ int lb_step(lb_ctx* ctx, int nsteps) {
             n += launch_shell_density(L, ctx->prec, s);
         }
         n += launch_wall_psi(L, ctx->prec, s);         // wall densities
+        n += launch_face_values(L, ctx->prec, s);      // extrapolated open-face values (Sec. 2.2)
         n += launch_virtual(L, ctx->prec, 1, s);       // Eqs. 20, 21
         if (int rc = prof_mark(ctx, LB_KERNEL_FUSED, 0, s)) return rc;
         // Eqs. 11, 14, 16, 3, 9, 17; the link forces of Eqs. 19, 22, 23
@@ -759,8 +764,8 @@ static int adjoint_ready(lb_ctx* ctx) {
         return set_err(ctx, LB_ERR_STATE, "stochastic rounding: recomputed forward steps would differ from the recorded ones");
     if (!ctx->all_fixed) return set_err(ctx, LB_ERR_STATE, "the adjoint needs immobile particles (infinite mass, at rest)");
     for (int f = 0; f < 2; f++)
-        if (ctx->L.P.open[f] == 1 || ctx->L.P.open[f] == 3)
-            return set_err(ctx, LB_ERR_STATE, "the adjoint handles walls and velocity faces only");
+        if (ctx->L.P.open[f] == 1 || ctx->L.P.open[f] == 3 || (ctx->L.P.open[f] == 2 && ctx->L.P.open_extrap))
+            return set_err(ctx, LB_ERR_STATE, "the adjoint handles walls and velocity faces without extrapolation only");
     return LB_OK;
 }
 

@@ -113,6 +113,63 @@ __global__ void k_wall_psi(Lattice L) {
     pw[2 * (side * nxy + w) + 1] = face ? C(L.P.open_rho[side][1]) : (den > C(0) ? num1 / den : C(0));
 }
 
+// rho^k and the mixture velocity u (Eqs. 6, 7, 14) of fluid node s from f(t)
+template <int PREC>
+__device__ __forceinline__ void node_values(const Lattice& L, long long s, typename Prec<PREC>::C (&q)[5]) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    const S* f = (const S*)L.f_cur;
+    C rho[2] = {0, 0}, j[2][3] = {{0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        C v[2];
+        ld_pair(f + pair_index(i, s, L.pstride), pop_shift<S, C>(L, 0, i), pop_shift<S, C>(L, 1, i), v[0], v[1]);
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            rho[k] += v[k];
+            j[k][0] += C(cx(i)) * v[k];
+            j[k][1] += C(cy(i)) * v[k];
+            j[k][2] += C(cz(i)) * v[k];
+        }
+    }
+    C u[3], om;
+    mixture<C>(L, rho, j, u, om);
+    q[0] = rho[0];
+    q[1] = rho[1];
+#pragma unroll
+    for (int d = 0; d < 3; d++) q[2 + d] = u[d];
+}
+
+// The face values of the open z faces with extrapolation (Sec. 2.2), one
+// thread per column (x, y) of face blockIdx.z: rho_w^k and u_w at the face
+// plane, q_w = q_b + (q_b - q_{b+1}) / 2 from the boundary node b and the
+// next interior node b + 1 along z; q_b alone where b + 1 is a particle node
+// or nz < 2.  From f(t) after the remap, like every lattice kernel of the
+// step.  The face rules read rho_w of velocity faces (Eq. 9) and u_w of
+// pressure faces (Eq. 10) from here.
+template <int PREC>
+__global__ void k_face_values(Lattice L) {
+    typedef typename Prec<PREC>::C C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, side = blockIdx.z;
+    const int type = L.P.open[side];
+    if (x >= L.nx || (type != 1 && type != 2)) return;
+    const long long nxy = (long long)L.nx * L.ny, col = (long long)x + (long long)L.nx * y;
+    const int zb = side == 0 ? 0 : L.nz - 1, zi = side == 0 ? 1 : L.nz - 2;
+    const long long b = col + nxy * zb;
+    if (L.mask[b]) return;  // a particle node on the face keeps what it holds
+    C q[5];
+    node_values<PREC>(L, b, q);
+    if (zi >= 0 && zi < L.nz && !L.mask[col + nxy * zi]) {
+        C qi[5];
+        node_values<PREC>(L, col + nxy * zi, qi);
+#pragma unroll
+        for (int a = 0; a < 5; a++) q[a] += C(0.5) * (q[a] - qi[a]);
+    }
+    C* fv = (C*)L.face + 5 * (side * nxy + col);
+#pragma unroll
+    for (int a = 0; a < 5; a++) fv[a] = q[a];
+}
+
 // Add the link force and torque of one site (Eqs. 22, 23) to the fixed-point
 // sums of F_liq, T_liq of its particle (p < 0: no link of the site reaches a
 // particle).  Integer atomics: the sums do not depend on the order of the
@@ -498,11 +555,21 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
     Tp[0] = rel[1] * Fl[2] - rel[2] * Fl[1];
     Tp[1] = rel[2] * Fl[0] - rel[0] * Fl[2];
     Tp[2] = rel[0] * Fl[1] - rel[1] * Fl[0];
-    // open z faces of the pressure (Eq. 10) or equilibrium kind: rewrite the
-    // populations the face sends in (the loop above stored the wall rule)
+    // open z faces of the pressure (Eq. 10) or equilibrium kind, and velocity
+    // faces with extrapolated densities: rewrite the populations the face
+    // sends in (the loop above stored the wall rule)
     const int face = wall_lo ? 0 : (wall_hi ? 1 : -1);
-    if (face >= 0 && !solid && (L.P.open[face] == 1 || L.P.open[face] == 3)) {
-        const bool pressure = L.P.open[face] == 1;
+    const int ftype = face >= 0 ? L.P.open[face] : 0;
+    const bool fext = L.P.open_extrap && (ftype == 1 || ftype == 2);
+    if (face >= 0 && !solid && (ftype == 1 || ftype == 3 || fext)) {
+        // u_w of a pressure face: the velocity of this node, or the
+        // extrapolated one (k_face_values), which also holds rho_w^k of a
+        // velocity face
+        const C* fv = (const C*)L.face + 5 * ((long long)face * L.nx * L.ny + x + (long long)L.nx * y);
+        C ue[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) ue[d] = fext ? fv[2 + d] : u[d];
+        const C ueu = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
         const C* uw = V[face == 0 ? 0 : 2];
         const C uwu = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
 #pragma unroll 1
@@ -511,8 +578,7 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
             C fb[2];
             for (int k = 0; k < 2; k++) {
                 const C rw = C(L.P.open_rho[face][k]);
-                if (pressure) {
-                    // -f*_i + 2 w_i rho_w (1 + 9/2 (c_i.u)^2 - 3/2 u.u), u of this node
+                if (ftype != 3) {
                     C fsk;
                     if (UNIT)
                         fsk = feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
@@ -520,8 +586,15 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
                         fsk = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
                                           feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
                               feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
-                    const C cuw = C(cx(i)) * u[0] + C(cy(i)) * u[1] + C(cz(i)) * u[2];
-                    fb[k] = -fsk + C(2) * wgt<C>(i) * rw * (C(1) + C(4.5) * cuw * cuw - C(1.5) * uu);
+                    if (ftype == 1) {
+                        // -f*_i + 2 w_i rho_w (1 + 9/2 (c_i.u_w)^2 - 3/2 u_w.u_w)
+                        const C cuw = C(cx(i)) * ue[0] + C(cy(i)) * ue[1] + C(cz(i)) * ue[2];
+                        fb[k] = -fsk + C(2) * wgt<C>(i) * rw * (C(1) + C(4.5) * cuw * cuw - C(1.5) * ueu);
+                    } else {
+                        // Eq. 9 with the extrapolated rho_w^k: f*_i - 6 w_i rho_w c_i.u_w
+                        const C cw = C(cx(i)) * uw[0] + C(cy(i)) * uw[1] + C(cz(i)) * uw[2];
+                        fb[k] = fsk - C(6) * (wgt<C>(i) * fv[k]) * cw;
+                    }
                 } else {
                     fb[k] = feq<C>(opp(i), rw, uw[0], uw[1], uw[2], uwu);
                 }
@@ -1154,14 +1227,21 @@ __device__ __forceinline__ void face_rule(const Lattice& L, int face, int i, con
     const float* uwf = face == 0 ? L.PF.wall_u_lo : L.PF.wall_u_hi;
     const C uw[3] = {prm<C>(uwd[0], uwf[0]), prm<C>(uwd[1], uwf[1]), prm<C>(uwd[2], uwf[2])};
     const int type = L.P.open[face];
+    // extrapolated face values (k_face_values) of the column of x
+    const C* fv = (const C*)L.face + 5 * (face * (long long)L.nx * L.ny + x % ((long long)L.nx * L.ny));
+    const bool ext = L.P.open_extrap && (type == 1 || type == 2);
     C rho[2] = {psi[2 * x], psi[2 * x + 1]};
+    if (ext && type == 2) {
+        rho[0] = fv[0];
+        rho[1] = fv[1];
+    }
     C fb[2];
     if (type == 1) {
         // Eq. 14 at tau_A = tau_B from the total momentum of the density pass
         C u[3];
         const C ir = C(1) / (rho[0] + rho[1]);
 #pragma unroll
-        for (int d = 0; d < 3; d++) u[d] = mom[d * L.pstride + x] * ir;
+        for (int d = 0; d < 3; d++) u[d] = ext ? fv[2 + d] : mom[d * L.pstride + x] * ir;
         const C uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         const C cuw = C(cx(i)) * u[0] + C(cy(i)) * u[1] + C(cz(i)) * u[2];
 #pragma unroll
@@ -1379,6 +1459,14 @@ int launch_wall_bounce(const Lattice& L, int prec, cudaStream_t st) {
         return 1;
     }
     DISPATCH(prec, (k_wall_bounce<P, false><<<g, 128, 0, st>>>(L)));
+    return 1;
+}
+
+int launch_face_values(const Lattice& L, int prec, cudaStream_t st) {
+    if (L.per[2] || !L.P.open_extrap) return 0;
+    if (L.P.open[0] != 1 && L.P.open[0] != 2 && L.P.open[1] != 1 && L.P.open[1] != 2) return 0;
+    dim3 g((unsigned)((L.nx + 127) / 128), (unsigned)L.ny, 2);
+    DISPATCH(prec, (k_face_values<P><<<g, 128, 0, st>>>(L)));
     return 1;
 }
 

@@ -227,6 +227,8 @@ struct Lattice {
     void* f_nxt;       // populations at time t+1
     void* psi;         // [N][2] of C: (psi^A, psi^B) of a site side by side; rho^k on fluid, virtual density on frontier
     void* psi_wall;    // [2 walls][nx*ny][2 comps] of C (pairs, like psi)
+    void* face;        // [2 faces][nx*ny][5] of C: rho_w^A, rho_w^B, u_w of the open faces
+                       // extrapolated to first order (k_face_values; with P.open_extrap)
     uint8_t* mask;     // 1 on particle nodes
     int* owner;        // -1 fluid, else particle index
     int* evt;          // remap events: 4 (p+1) + 1 destroy, 4 (p+1) + 2 create
@@ -667,6 +669,7 @@ int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st);
 // the one-component fluid (lbgb_single.cu)
 int launch_single_init(const Lattice& L, int prec, const double* stage, cudaStream_t st);
 int launch_single_step(const Lattice& L, int prec, cudaStream_t st);
+int launch_single_face_values(const Lattice& L, int prec, cudaStream_t st);
 int launch_single_fields_out(const Lattice& L, int prec, double* stage, cudaStream_t st);
 int launch_single_totals_partial(const Lattice& L, int prec, cudaStream_t st);
 int launch_single_populations_out(const Lattice& L, int prec, int i, double* stage, cudaStream_t st);
@@ -676,6 +679,7 @@ int launch_wall_bounce(const Lattice& L, int prec, cudaStream_t st);
 int launch_shell_density(const Lattice& L, int prec, cudaStream_t st);
 int launch_density(const Lattice& L, int prec, cudaStream_t st);
 int launch_wall_psi(const Lattice& L, int prec, cudaStream_t st);
+int launch_face_values(const Lattice& L, int prec, cudaStream_t st);
 int launch_fields_out(const Lattice& L, int prec, double* stage, cudaStream_t st);
 int launch_totals(const Lattice& L, int prec, double* out_dev, cudaStream_t st);
 int launch_populations_out(const Lattice& L, int prec, int k, int i, double* stage, cudaStream_t st);

@@ -33,6 +33,34 @@ __global__ void k1_init(Lattice L, const double* __restrict__ stage) {
     for (int i = 0; i < Q; i++) st_pop(f + pop1_index(i, s, L.pstride), feq<C>(i, r, ux, uy, uz, uu), pop_shift<S, C>(L, 0, i));
 }
 
+// rho of node s from f(t)
+template <int PREC>
+__device__ __forceinline__ typename Prec<PREC>::C node_rho1(const Lattice& L, long long s) {
+    typedef typename Prec<PREC>::S S;
+    typedef typename Prec<PREC>::C C;
+    const S* f = (const S*)L.f_cur;
+    C r = 0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) r += ld_pop(f + pop1_index(i, s, L.pstride), pop_shift<S, C>(L, 0, i));
+    return r;
+}
+
+// rho_w of the velocity faces (Eq. 9) extrapolated to first order from the
+// boundary node b and the next interior node b + 1 along z (Sec. 2.2),
+// rho_w = rho_b + (rho_b - rho_{b+1}) / 2 (rho_b alone for nz < 2), one
+// thread per column of face blockIdx.z, into element 0 of the face record
+template <int PREC>
+__global__ void k1_face_values(Lattice L) {
+    typedef typename Prec<PREC>::C C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, side = blockIdx.z;
+    if (x >= L.nx || L.P.open[side] != 2) return;
+    const long long nxy = (long long)L.nx * L.ny, col = (long long)x + (long long)L.nx * y;
+    const int zb = side == 0 ? 0 : L.nz - 1, zi = side == 0 ? 1 : L.nz - 2;
+    C r = node_rho1<PREC>(L, col + nxy * zb);
+    if (zi >= 0 && zi < L.nz) r += C(0.5) * (r - node_rho1<PREC>(L, col + nxy * zi));
+    ((C*)L.face)[5 * (side * nxy + col)] = r;
+}
+
 // One time step of every site (grid: x chunks, y, z).  UNIT: omega = 1, so
 // Eq. 16 is f* = f^eq(rho, u + g) and the populations enter only through
 // their moments.
@@ -100,7 +128,13 @@ __global__ void __launch_bounds__(128) k1_step(Lattice L) {
             const float* uwf = cz(i) < 0 ? L.PF.wall_u_lo : L.PF.wall_u_hi;
             const C cw = C(cx(i)) * prm<C>(uwd[0], uwf[0]) + C(cy(i)) * prm<C>(uwd[1], uwf[1]) +
                          C(cz(i)) * prm<C>(uwd[2], uwf[2]);
-            v = fs[i] - C(6) * wgt<C>(i) * rho * cw;
+            // rho_w: rho of this node, or on a velocity face with
+            // extrapolation the face value of the column (k1_face_values)
+            const int h = cz(i) < 0 ? 0 : 1;
+            C rw = rho;
+            if (L.P.open_extrap && L.P.open[h] == 2)
+                rw = ((const C*)L.face)[5 * ((long long)h * nxy + x + (long long)nx * y)];
+            v = fs[i] - C(6) * wgt<C>(i) * rw * cw;
             e = (long long)opp(i) * ps + SKEW + (long long)s + cx(i);
         }
         val[i] = v;
@@ -212,6 +246,13 @@ static inline unsigned nblk1(long long n, int b) { return (unsigned)((n + b - 1)
 
 int launch_single_init(const Lattice& L, int prec, const double* stage, cudaStream_t st) {
     DISPATCH1(prec, (k1_init<P><<<nblk1(L.N, 256), 256, 0, st>>>(L, stage)));
+    return 1;
+}
+
+int launch_single_face_values(const Lattice& L, int prec, cudaStream_t st) {
+    if (L.per[2] || !L.P.open_extrap || (L.P.open[0] != 2 && L.P.open[1] != 2)) return 0;
+    dim3 g((unsigned)((L.nx + 127) / 128), (unsigned)L.ny, 2);
+    DISPATCH1(prec, (k1_face_values<P><<<g, 128, 0, st>>>(L)));
     return 1;
 }
 

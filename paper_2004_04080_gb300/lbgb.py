@@ -49,7 +49,7 @@ class LbParams(C.Structure):
         ("side_wall_k", C.c_double), ("side_wall_d", C.c_double), ("rotate", C.c_int),
         ("janus", C.c_int), ("janus_theta0", C.c_double), ("janus_width", C.c_double),
         ("rcut", C.c_double), ("delr", C.c_double),
-        ("open", C.c_int * 2), ("open_rho", C.c_double * 4),
+        ("open", C.c_int * 2), ("open_rho", C.c_double * 4), ("open_extrap", C.c_int),
     ]
 
 

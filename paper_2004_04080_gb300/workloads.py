@@ -129,7 +129,7 @@ def default_params() -> dict:
         side_wall_k=0.0, side_wall_d=0.0, rotate=1,
         janus=0, janus_theta0=108.0, janus_width=10.0,
         rcut=0.0, delr=0.0,
-        open=(0, 0), open_rho=(1.0, 1.0, 1.0, 1.0),
+        open=(0, 0), open_rho=(1.0, 1.0, 1.0, 1.0), open_extrap=0,
     )
 
 

@@ -41,7 +41,7 @@ def test_params_struct_layout_matches_c():
 int main(void) { printf("size %zu\n", sizeof(lb_params));
 O(tau) O(G) O(zeta) O(rho0) O(bc) O(wall_u_lo) O(wall_u_hi) O(body_force) O(hertz_K)
 O(hertz_sigma) O(hertz_rcap) O(lub_on) O(lub_hn) O(lub_hmin) O(lub_scale) O(side_wall_k)
-O(side_wall_d) O(rotate) O(janus) O(janus_theta0) O(janus_width) O(rcut) O(delr) O(open) O(open_rho) return 0; }
+O(side_wall_d) O(rotate) O(janus) O(janus_theta0) O(janus_width) O(rcut) O(delr) O(open) O(open_rho) O(open_extrap) return 0; }
 '''
     tmp = os.path.join(ROOT, "paper_2004_04080_gb300", "_build")
     os.makedirs(tmp, exist_ok=True)

@@ -545,3 +545,55 @@ def test_open_faces_with_particles(prec, tol, tau):
     g, o = run_both(shape, params, 40, prec, col, mixture_densities(shape, seed=43, amp=0.05))
     compare_fields(g, o, tol)
     compare_colloids(g, o, tol)
+
+
+def _away_from(g, o_plain, tol):
+    """The run differs from the oracle's run without extrapolation by more
+    than the tolerance: the extrapolated face values reached the result."""
+    ga, _, gu = g.get_fields()
+    ra, _, ru = o_plain.get_fields()
+    assert max(rel(ga, ra), rel(gu, ru, floor=1.0)) > 10 * tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("fp16", 1e-3)])
+@pytest.mark.parametrize("tau", [(1.0, 1.0), (0.8, 1.2)])
+def test_open_faces_extrapolated(prec, tol, tau):
+    """Open z faces with the first-order extrapolation of Sec. 2.2: a
+    velocity face (Eq. 9 with rho_w extrapolated) below, a pressure face
+    (Eq. 10 with u_w extrapolated) above, without particles (the plain fused
+    kernel), 40 steps."""
+    shape = (24, 13, 17)
+    params = dict(G=0.6, tau=tau, bc=(1, 1, 0), open=(2, 1), wall_u_lo=(0.01, -0.02, 0.03),
+                  open_rho=(0.5, 0.5, 0.47, 0.5), open_extrap=1)
+    dens = mixture_densities(shape, seed=45, amp=0.05)
+    g, o = run_both(shape, params, 40, prec, dens=dens)
+    assert g.fused_kernel() == "k_fused"
+    compare_fields(g, o, tol)
+    if prec != "fp16":
+        o0 = Oracle(*shape)
+        o0.set_params(**dict(params, open_extrap=0))
+        o0.init_fields(*dens)
+        o0.step(40)
+        _away_from(g, o0, tol)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("tau", [(1.0, 1.0), (0.8, 1.2)])
+def test_open_faces_extrapolated_with_particles(prec, tol, tau):
+    """The extrapolated faces with particles (the lean kernel and its wall
+    kernel at tau = 1, the copy-pipelined kernel otherwise): a pressure face
+    below, a velocity face above; the first particle covers nodes of the
+    plane next to the lower face, where the face values fall back to those
+    of the boundary node, 40 steps."""
+    shape = (32, 21, 23)
+    params = dict(G=0.5, tau=tau, bc=(1, 1, 0), open=(1, 2), wall_u_hi=(0.02, 0.0, -0.01),
+                  open_rho=(0.52, 0.5, 0.5, 0.5), hertz_K=20, hertz_sigma=8.0, hertz_rcap=7.0,
+                  open_extrap=1)
+    col = dict(pos=[[8.2, 5.3, 3.2], [22.6, 14.1, 12.4]], radius=[2.6, 3.2], mass=[400.0, 350.0],
+               vel=[[0.01, 0.01, 0.0], [-0.01, 0.0, 0.02]], omega=[[0.0, 0.01, 0.0], [0.01, 0.0, 0.0]])
+    g, o = run_both(shape, params, 40, prec, col, mixture_densities(shape, seed=47, amp=0.05))
+    assert g.fused_kernel() == ("k_lean" if tau == (1.0, 1.0) else "k_fused_async")
+    own = o.owner().reshape(shape[2], shape[1], shape[0])
+    assert (own[1] == 0).any() and (own[0] < 0).all()
+    compare_fields(g, o, tol)
+    compare_colloids(g, o, tol)

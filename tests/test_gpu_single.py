@@ -75,3 +75,25 @@ def test_one_component_periodic_mass_and_momentum():
         g.populations(1)
     with pytest.raises(lbgb.LBError):
         g.add_colloids([[5.0, 5.0, 5.0]], 2.0, 100.0)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("fp16", 1e-3)])
+def test_one_component_extrapolated_velocity_faces(prec, tol):
+    """Velocity faces (Eq. 9) on both z faces with rho_w extrapolated to
+    first order (Sec. 2.2), a body force along z that stratifies the
+    density, 60 steps; and the run differs from the one without the
+    extrapolation."""
+    shape = (20, 9, 12)
+    params = dict(tau=(0.9, 0.9), bc=(1, 1, 0), open=(2, 2), wall_u_lo=(0.02, 0.0, 0.01),
+                  wall_u_hi=(-0.01, 0.01, -0.01), body_force=(0, 0, -2e-4), rho0=(1.0, 0.0),
+                  open_extrap=1)
+    g, o = _run(shape, params, 60, prec)
+    ga, _, gu = g.get_fields()
+    ra, _, ru = o.get_fields()
+    assert rel(ga, ra) < tol
+    assert rel(gu, ru, floor=1.0 if prec == "fp16" else 0.03) < tol
+    if prec != "fp16":
+        _, o0 = _run(shape, dict(params, open_extrap=0), 0, "fp64")
+        o0.step(60)
+        a0, _, u0 = o0.get_fields()
+        assert max(rel(ga, a0), rel(gu, u0, floor=0.03)) > 10 * tol

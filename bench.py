@@ -353,7 +353,8 @@ def case0_throughput(dev, torch, n=1024, steps=10):
     out = {"workload": "%d^3 periodic, two components, G = 0.65, rho = 1.0 + 1.0 (std 0.004), tau = 1, "
                        "no particles, FP16 storage (stochastic rounding)" % n,
            "steps": steps, "ms_per_step": round(ms / steps, 3), "glups": round(N * steps / (ms / 1e3) / 1e9, 3),
-           "kernel": lat.fused_kernel(),
+           "kernel": lat.fused_kernel(), "bytes_per_site": alg_bytes("fp16"),
+           "hbm_frac": round(N * steps / (ms / 1e3) * alg_bytes("fp16") / 1e9 / peaks()[0], 4),
            "paper_glups": 1.37, "paper_case": "1024^3 case 0 on 1024 cores (Sec. 5.1 two-component table)"}
     del lat
     torch.cuda.empty_cache()

@@ -324,17 +324,18 @@ long long lb_pair_list_builds(lb_ctx *ctx);
 /* Which fused lattice kernel lb_step launches in the context's present state
  * (the sequence of Sec. 3.1 is the same for all; they differ in how the
  * moments and the Shan-Chen halo densities of Eq. 11 reach the collision):
- *  LB_FUSED_MOMENTUM  particles present, tau_A = tau_B = 1: a density pass
- *      writes rho^k and j^k of every node (Eqs. 6-7) and the class of every
- *      link (fluid-fluid, fluid-particle); the lean lattice kernel collides
- *      every node from the moments (Eq. 16 at omega = 1), staging the halo
- *      of rho^k in shared memory with asynchronous copies, pushes the links
- *      and bounces those into particle nodes (Eqs. 17-19, 22, 23); a small
- *      kernel then applies the rules of the z faces (Eqs. 9, 10);
+ *  LB_FUSED_MOMENTUM  tau_A = tau_B = 1, with or without particles: a
+ *      density pass writes rho^k and j^k of every node (Eqs. 6-7), the
+ *      class of every link (fluid-fluid, fluid-particle) is kept with the
+ *      node map; the lean lattice kernel collides every node from the
+ *      moments (Eq. 16 at omega = 1), staging the halo of rho^k in shared
+ *      memory with asynchronous copies, pushes the links and bounces those
+ *      into particle nodes (Eqs. 17-19, 22, 23); a small kernel then applies
+ *      the rules of the z faces (Eqs. 9, 10);
  *  LB_FUSED_TWO_PASS  particles, other tau: a density pass writes rho^k, the
  *      fused kernel re-reads the populations;
- *  LB_FUSED_PLAIN     no particles: one pass, halo densities formed from the
- *      neighbours' populations;
+ *  LB_FUSED_PLAIN     no particles, other tau: one pass, halo densities
+ *      formed from the neighbours' populations;
  *  LB_FUSED_SINGLE    a one-component lattice (LB_ONE_COMPONENT): one pass,
  *      one thread per site.
  * Returns the code, or LB_ERR_ARG for a NULL context. */

@@ -503,6 +503,13 @@ int lb_set_rounding(lb_ctx* ctx, int mode, unsigned long long seed) {
     return LB_OK;
 }
 
+// the link classes (NB_*) of every site, when they are not kept up to date
+static int ensure_link_classes(lb_ctx* ctx, cudaStream_t st) {
+    if (ctx->nb_valid) return 0;
+    ctx->nb_valid = 1;
+    return launch_link_classes(ctx->L, true, st);
+}
+
 int lb_step(lb_ctx* ctx, int nsteps) {
     if (!ctx || nsteps < 0) return LB_ERR_ARG;
     if (!ctx->have_fields) return set_err(ctx, LB_ERR_STATE, "lb_init_fields must come first");
@@ -538,17 +545,20 @@ int lb_step(lb_ctx* ctx, int nsteps) {
         }
         if (L.sr) L.sr_key = sr_key(ctx->sr_seed, ctx->sr_step++);
         n += launch_remap(L, ctx->prec, ctx->maxc, s);  // destroy / create (Eqs. 24, 25)
+        const bool unit = L.P.tau[0] == 1.0 && L.P.tau[1] == 1.0;
         if (L.nc > 0) {
             n += launch_link_classes(L, !ctx->nb_valid, s);
             ctx->nb_valid = 1;
+        } else if (unit) {
+            n += ensure_link_classes(ctx, s);  // no particles: every word 0, once
         }
         // rho^k (Eq. 6) of every fluid node when particles need virtual
-        // densities (Eq. 20); with omega = 1 the pass also writes j^k, and
-        // the fused kernel collides from the moments instead of re-reading the
-        // populations.  Without particles only the planes next to the walls
-        // (the fused kernel then forms its halo densities itself).
-        const bool unit = L.P.tau[0] == 1.0 && L.P.tau[1] == 1.0;
-        L.dense_psi = L.nc > 0;
+        // densities (Eq. 20) or omega = 1; with omega = 1 the pass also
+        // writes j^k, and the lean kernel collides from the moments instead of
+        // re-reading the populations.  Otherwise (no particles, other tau)
+        // only the planes next to the walls (the plain fused kernel then forms
+        // its halo densities itself).
+        L.dense_psi = L.nc > 0 || unit;
         L.dense_mom = L.dense_psi && unit;
         if (L.dense_psi) {
             if (int rc = prof_mark(ctx, LB_KERNEL_DENSITY, 0, s)) return rc;
@@ -592,11 +602,6 @@ int lb_step(lb_ctx* ctx, int nsteps) {
 // density, wetting and wall fields of the current state (no particle terms)
 // the virtual densities find the frontier nodes by the link classes: rebuild
 // them if the node map changed outside lb_step (number of launches)
-static int ensure_link_classes(lb_ctx* ctx, cudaStream_t st) {
-    if (ctx->L.nc <= 0 || ctx->nb_valid) return 0;
-    ctx->nb_valid = 1;
-    return launch_link_classes(ctx->L, true, st);
-}
 
 static int current_forces(lb_ctx* ctx) {
     Lattice& L = ctx->L;
@@ -713,8 +718,8 @@ int lb_fused_kernel(const lb_ctx* ctx) {
     if (!ctx) return LB_ERR_ARG;
     const bool unit = ctx->L.P.tau[0] == 1.0 && ctx->L.P.tau[1] == 1.0;
     if (ctx->L.ncomp == 1) return LB_FUSED_SINGLE;
-    if (ctx->L.nc > 0) return unit ? LB_FUSED_MOMENTUM : LB_FUSED_TWO_PASS;
-    return LB_FUSED_PLAIN;
+    if (unit) return LB_FUSED_MOMENTUM;
+    return ctx->L.nc > 0 ? LB_FUSED_TWO_PASS : LB_FUSED_PLAIN;
 }
 
 

@@ -1553,18 +1553,10 @@ int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st) {
     zc = zc < 4 ? 4 : zc;
     zc = zc > L.nz ? L.nz : zc;
     dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + FTY - 1) / FTY, (L.nz + zc - 1) / zc);
-    // relaxation frequency exactly 1 (tau_A = tau_B = 1): the collision needs
-    // no non-equilibrium part, a separate instantiation keeps the code small
-    bool unit = L.P.tau[0] == 1.0 && L.P.tau[1] == 1.0;
-    if (prec == LB_FP16 && L.sr) {
-        if (unit) return launch_fused_plain<LB_FP16, true, true>(L, zc, grid, st);
-        return launch_fused_plain<LB_FP16, false, true>(L, zc, grid, st);
-    }
-    if (unit) {
-        DISPATCH(prec, (launch_fused_plain<P, true, false>(L, zc, grid, st)));
-    } else {
-        DISPATCH(prec, (launch_fused_plain<P, false, false>(L, zc, grid, st)));
-    }
+    // no particles and tau_A, tau_B not both 1 (at omega = 1 lb_step runs the
+    // density pass and the lean kernel, particles or not)
+    if (prec == LB_FP16 && L.sr) return launch_fused_plain<LB_FP16, false, true>(L, zc, grid, st);
+    DISPATCH(prec, (launch_fused_plain<P, false, false>(L, zc, grid, st)));
     return 1;
 }
 

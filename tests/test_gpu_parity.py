@@ -235,10 +235,13 @@ def test_reduced_precision_ragged_walls_moving_particles(prec, tol, nx):
     compare_colloids(g, o, tol)
 
 
-def test_fp64_fluid_only_populations_exact():
-    """No particles: every population matches the oracle to 1e-13."""
+@pytest.mark.parametrize("tau", [(0.7, 0.9), (1.0, 1.0)])
+def test_fp64_fluid_only_populations_exact(tau):
+    """No particles (the plain fused kernel, and the lean kernel at tau = 1):
+    every population matches the oracle to 1e-13."""
     shape = (16, 9, 7)
-    g, o = run_both(shape, dict(G=0.9, tau=(0.7, 0.9)), 25, "fp64")
+    g, o = run_both(shape, dict(G=0.9, tau=tau), 25, "fp64")
+    assert g.fused_kernel() == ("k_lean" if tau == (1.0, 1.0) else "k_fused")
     for k in (0, 1):
         assert rel(g.populations(k), o.populations(k)) < 1e-13
 
@@ -319,14 +322,19 @@ def event_mask(g, o, shape, radius):
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_momentum_kernel_runs_the_particle_workloads(prec):
-    """The tau = 1 particle workloads (bijel, Pickering, confined shear) take
-    the momentum kernel after the full density pass; other tau the two-pass one."""
+    """Every tau = 1 lattice (the particle workloads: bijel, Pickering,
+    confined shear; and the fluid alone) takes the lean kernel after the full
+    density pass; other tau the two-pass kernel with particles, the plain
+    fused kernel without."""
     w = workload("small_fp64")
     g = _lattice(w.shape, prec, w.n_colloids)
     g.set_params(**w.params)
     a, b = w.densities()
     g.init_fields(a, b)
+    assert g.fused_kernel() == "k_lean"
+    g.set_params(**dict(w.params, tau=(0.8, 1.2)))
     assert g.fused_kernel() == "k_fused"
+    g.set_params(**w.params)
     c = w.colloids()
     g.add_colloids(c["pos"], c["radius"], c["mass"])
     assert g.fused_kernel() == "k_lean"
@@ -522,7 +530,8 @@ def test_janus_lubrication_benchmark_physics(prec, tol):
 def test_open_faces(prec, tol, tau):
     """Open z faces (Sec. 2.2): an equilibrium inlet (rho_w, u_w) at z = -1/2
     and a pressure outlet (Eq. 10) at z = nz - 1/2 on the demixing-capable
-    mixture, without particles (the plain fused kernel), 40 steps."""
+    mixture, without particles (the lean kernel at tau = 1, the plain fused
+    kernel otherwise), 40 steps."""
     shape = (24, 13, 17)
     params = dict(G=0.6, tau=tau, bc=(1, 1, 0), open=(3, 1), wall_u_lo=(0.01, 0.0, 0.03),
                   open_rho=(0.56, 0.46, 0.5, 0.5))
@@ -560,14 +569,14 @@ def _away_from(g, o_plain, tol):
 def test_open_faces_extrapolated(prec, tol, tau):
     """Open z faces with the first-order extrapolation of Sec. 2.2: a
     velocity face (Eq. 9 with rho_w extrapolated) below, a pressure face
-    (Eq. 10 with u_w extrapolated) above, without particles (the plain fused
-    kernel), 40 steps."""
+    (Eq. 10 with u_w extrapolated) above, without particles (the lean kernel
+    at tau = 1, the plain fused kernel otherwise), 40 steps."""
     shape = (24, 13, 17)
     params = dict(G=0.6, tau=tau, bc=(1, 1, 0), open=(2, 1), wall_u_lo=(0.01, -0.02, 0.03),
                   open_rho=(0.5, 0.5, 0.47, 0.5), open_extrap=1)
     dens = mixture_densities(shape, seed=45, amp=0.05)
     g, o = run_both(shape, params, 40, prec, dens=dens)
-    assert g.fused_kernel() == "k_fused"
+    assert g.fused_kernel() == ("k_lean" if tau == (1.0, 1.0) else "k_fused")
     compare_fields(g, o, tol)
     if prec != "fp16":
         o0 = Oracle(*shape)

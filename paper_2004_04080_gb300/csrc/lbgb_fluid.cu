@@ -397,7 +397,7 @@ __device__ __forceinline__ LinkInfo link_info(const SH& sh, const int (&sl)[3], 
 // Nearly every warp holds a bounce-back site, so the store of each link
 // selects its destination (the neighbour's slot i, or the own slot opp(i)
 // with the wall-velocity term) instead of branching.
-template <int PREC, bool UNIT, bool SR, typename SH, typename PopFn>
+template <int PREC, bool SR, typename SH, typename PopFn>
 __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int (&sl)[3], int x, int y, int z,
                                              int ty, const OwnSite<PREC>& m, bool solid, PopFn pop,
                                              const LinkInfo& li, const ParticleRef<typename Prec<PREC>::C>& pref,
@@ -445,20 +445,13 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
     C uus[2] = {us[0][0] * us[0][0] + us[0][1] * us[0][1] + us[0][2] * us[0][2],
                 us[1][0] * us[1][0] + us[1][1] * us[1][1] + us[1][2] * us[1][2]};
     C one_m_om = C(1) - om;
-    // Eq. 5 factored per weight class c (0 rest, 1 axis, 2 diagonal):
-    // f^eq_i = A_c + c_i.v (B_c + H_c c_i.v) with A_c = w_c rho (1 - 3/2 v.v),
-    // B_c = 3 w_c rho, H_c = 9/2 w_c rho; v = us^k (the shifted velocity of
-    // Eq. 16) and, for omega != 1, v = u.
-    C A[2][3], B[2][3], H[2][3];
+    // 3 w_c rho^k per weight class c (1 axis, 2 diagonal): the wall term of
+    // the bounce-back (Eqs. 9, 17) is 3 w_c rho^k (-2 c_i.u_w)
+    C B[2][3];
 #pragma unroll
     for (int k = 0; k < 2; k++)
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-            C wr = wgt<C>(c == 0 ? 0 : (c == 1 ? 1 : 7)) * m.rho[k];
-            A[k][c] = wr * (C(1) - C(1.5) * uus[k]);
-            B[k][c] = C(3) * wr;
-            H[k][c] = C(4.5) * wr;
-        }
+        for (int c = 0; c < 3; c++) B[k][c] = C(3) * (wgt<C>(c == 0 ? 0 : (c == 1 ? 1 : 7)) * m.rho[k]);
     // site-index steps to the neighbours, periodic wrap folded in (32-bit:
     // a lattice holds fewer than 2^31 sites)
     const unsigned ps = (unsigned)L.pstride;
@@ -501,18 +494,11 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         C fs[2];
-        C cu[2];
 #pragma unroll
         for (int k = 0; k < 2; k++) {
-            const int c = i == 0 ? 0 : (i <= 6 ? 1 : 2);
-            if (UNIT) {  // omega = 1 exactly: Eq. 16 is f* = f^eq(rho^k, us^k)
-                cu[k] = C(cx(i)) * us[k][0] + C(cy(i)) * us[k][1] + C(cz(i)) * us[k][2];
-                fs[k] = i == 0 ? A[k][0] : A[k][c] + cu[k] * (B[k][c] + H[k][c] * cu[k]);
-            } else {
-                fs[k] = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
-                                    feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
-                        feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
-            }
+            fs[k] = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
+                                feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
+                    feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
         }
         if (i == 0) {
             put2(pair_at(0, (unsigned)SKEW + s), solid ? wgt<C>(0) * prm<C>(L.P.rho0[0], L.PF.rho0[0]) : fs[0],
@@ -579,13 +565,9 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
             for (int k = 0; k < 2; k++) {
                 const C rw = C(L.P.open_rho[face][k]);
                 if (ftype != 3) {
-                    C fsk;
-                    if (UNIT)
-                        fsk = feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
-                    else
-                        fsk = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
-                                          feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
-                              feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
+                    const C fsk = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
+                                              feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
+                                  feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
                     if (ftype == 1) {
                         // -f*_i + 2 w_i rho_w (1 + 9/2 (c_i.u_w)^2 - 3/2 u_w.u_w)
                         const C cuw = C(cx(i)) * ue[0] + C(cy(i)) * ue[1] + C(cz(i)) * ue[2];
@@ -614,12 +596,9 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
             C cw = C(cx(i)) * U[0] + C(cy(i)) * U[1] + C(cz(i)) * U[2];
             C fsv[2], fbv[2];
             for (int k = 0; k < 2; k++) {
-                if (UNIT)
-                    fsv[k] = feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
-                else
-                    fsv[k] = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
-                                         feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
-                             feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
+                fsv[k] = one_m_om * (ld_pop(pop(k * Q + i), pop_shift<S, C>(L, k, i)) -
+                                     feq<C>(i, m.rho[k], u[0], u[1], u[2], uu)) +
+                         feq<C>(i, m.rho[k], us[k][0], us[k][1], us[k][2], uus[k]);
                 fbv[k] = fsv[k] - C(6) * wgt<C>(i) * m.rho[k] * cw;
             }
             const unsigned own = (unsigned)(SKEW + cx(i)) + s;  // pair of s in plane opp(i)
@@ -637,8 +616,8 @@ __device__ __forceinline__ void collide_site(const Lattice& L, SH& sh, const int
     }
 }
 
-template <int PREC, bool UNIT, bool SR>
-__global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k_fused(Lattice L, int zc) {
+template <int PREC, bool SR>
+__global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : 2)) k_fused(Lattice L, int zc) {
     typedef typename Prec<PREC>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FusedShared<PREC>& sh = *reinterpret_cast<FusedShared<PREC>*>(smem_raw);
@@ -651,8 +630,8 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k
     // prologue: plane z0-1 into slot 0, plane z0 into slot 1 (own site staged)
     fill_plane<PREC>(L, sh, 0, z0 - 1, x0, y0, W, H, false, nxt);
     bool have = fill_plane<PREC>(L, sh, 1, z0, x0, y0, W, H, true, nxt);
-    // the populations themselves are needed again only for omega != 1
-    if (!UNIT && have)
+    // the populations themselves are needed again for the collision
+    if (have)
 #pragma unroll
         for (int q = 0; q < 2 * Q; q++) sh.stage[q][tid] = nxt.raw[q];
     cur.rho[0] = nxt.rho[0]; cur.rho[1] = nxt.rho[1];
@@ -672,12 +651,12 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k
             // (particle 0 stands in when no link reaches a particle: its
             // record exists whenever the lattice has room for particles)
             const ParticleRef<C> pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
-            collide_site<PREC, UNIT, SR>(L, sh, sl, x0 + tx, y0 + ty, z, ty, cur, solid,
+            collide_site<PREC, SR>(L, sh, sl, x0 + tx, y0 + ty, z, ty, cur, solid,
                                      [&](int q) { return &sh.stage[q][tid]; }, li, pref, pf, Fp, Tp);
         }
         commit_link_forces<C>(L, pf, Fp, Tp);
         __syncthreads();
-        if (!UNIT && have_n)
+        if (have_n)
 #pragma unroll
             for (int q = 0; q < 2 * Q; q++) sh.stage[q][tid] = nxt.raw[q];
         cur.rho[0] = nxt.rho[0]; cur.rho[1] = nxt.rho[1];
@@ -690,7 +669,7 @@ __global__ void __launch_bounds__(FNT, (PREC == LB_FP64 ? 1 : (UNIT ? 3 : 2))) k
 
 // ------------------------------------------ copy-pipelined fused step
 // The fused step for a lattice with particles at tau != 1 (tau = 1: the
-// warp-independent momentum kernel below), where a full density pass
+// lean momentum kernel below), where a full density pass
 // (k_density) and the virtual densities (Eq. 20) have filled psi before the
 // step: the halo of the Shan-Chen sum then needs no populations, and the
 // block streams each plane through shared memory with asynchronous copies
@@ -725,7 +704,7 @@ constexpr int async_x_multiple() {
     return 16 / (int)sizeof(typename Prec<PREC>::S) < 4 ? 4 : 16 / (int)sizeof(typename Prec<PREC>::S);
 }
 
-template <int PREC, bool UNIT, int TY, bool SR>
+template <int PREC, int TY, bool SR>
 __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fused_async(Lattice L, int zc) {
     typedef typename Prec<PREC>::S S;
     typedef typename Prec<PREC>::C C;
@@ -840,7 +819,7 @@ __global__ void __launch_bounds__(FTX* TY, (PREC == LB_FP64 ? 1 : 16 / TY)) k_fu
             const bool solid = sh.nd[mid][ty + 1][tx + 1] != ND_FLUID;
             const LinkInfo li = link_info(sh, sl, tx, ty, solid);
             const ParticleRef<C> pref = particle_load<C>(L, li.p0 >= 0 ? li.p0 : 0);
-            collide_site<PREC, UNIT, SR>(L, sh, sl, x0 + tx, y0 + ty, z, ty, m, solid,
+            collide_site<PREC, SR>(L, sh, sl, x0 + tx, y0 + ty, z, ty, m, solid,
                                      [&](int q) { return &sh.stage[b][q % Q][ty][2 * (MS + tx - cx(q % Q)) + q / Q]; },
                                      li, pref,
                                      pf, Fp, Tp);
@@ -856,7 +835,7 @@ constexpr int WNSLOT = 5;  // psi planes a lean warp holds: z-1 .. z+3
 constexpr int WPB = 4;     // warps (rows) per block of the lean kernel
 
 // ------------------------------------------------------- lean momentum kernel
-// With particles present and omega = 1 (tau^A = tau^B = 1), and the class of
+// At omega = 1 (tau^A = tau^B = 1), with or without particles, and the class of
 // every link kept with the node map (nb, NB_*), this kernel collides every
 // site from its moments (Eq. 16 at omega = 1, with the force of Eq. 11) and
 // pushes its links (Eq. 3) with no per-link decisions beyond a predicate:
@@ -1499,37 +1478,35 @@ static int z_chunks(const Lattice& L, int tiles, int per_sm, int zmin) {
     return best;
 }
 
-template <int P, bool UNIT, bool SR>
+template <int P, bool SR>
 static int launch_fused_async_t(const Lattice& L, cudaStream_t st) {
     constexpr int TY = ASYNC_TY, NT = FTX * TY;
     typedef AsyncShared<P, TY> SH;
     const size_t smem = sizeof(SH);
-    const int per_sm = kernel_setup<k_fused_async<P, UNIT, TY, SR>>(NT, smem);
+    const int per_sm = kernel_setup<k_fused_async<P, TY, SR>>(NT, smem);
     int tiles = ((L.nx + FTX - 1) / FTX) * ((L.ny + TY - 1) / TY);
     int zc = z_chunks(L, tiles, per_sm, 8);
     dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
-    k_fused_async<P, UNIT, TY, SR><<<grid, dim3(FTX, TY), smem, st>>>(L, zc);
+    k_fused_async<P, TY, SR><<<grid, dim3(FTX, TY), smem, st>>>(L, zc);
     return 1;
 }
 
 template <int P>
 static int launch_fused_async(const Lattice& L, bool unit, cudaStream_t st) {
     // omega = 1: lb_step has the density pass write the momenta, and the
-    // warp kernel collides from them; otherwise the general collision (exact
-    // at omega = 1 as well: the non-equilibrium part is multiplied by 0)
+    // lean kernel collides from them; otherwise the general collision
     if (unit && L.dense_mom) return launch_lean<P>(L, st) + launch_wall_bounce(L, P, st);
     if constexpr (P == LB_FP16)
-        if (L.sr) return launch_fused_async_t<P, false, true>(L, st);
-    return launch_fused_async_t<P, false, false>(L, st);
+        if (L.sr) return launch_fused_async_t<P, true>(L, st);
+    return launch_fused_async_t<P, false>(L, st);
 }
 
-// the plain fused kernel (no particles): shared memory without the
-// population stage at omega = 1
-template <int P, bool UNIT, bool SR>
+// the plain fused kernel (no particles, tau != 1)
+template <int P, bool SR>
 static int launch_fused_plain(const Lattice& L, int zc, dim3 grid, cudaStream_t st) {
-    const size_t smem = UNIT ? offsetof(FusedShared<P>, stage) : sizeof(FusedShared<P>);
-    kernel_setup<k_fused<P, UNIT, SR>>(FTX * FTY, smem);
-    k_fused<P, UNIT, SR><<<grid, dim3(FTX, FTY), smem, st>>>(L, zc);
+    const size_t smem = sizeof(FusedShared<P>);
+    kernel_setup<k_fused<P, SR>>(FTX * FTY, smem);
+    k_fused<P, SR><<<grid, dim3(FTX, FTY), smem, st>>>(L, zc);
     return 1;
 }
 
@@ -1555,8 +1532,8 @@ int launch_fluid_step(const Lattice& L, int prec, cudaStream_t st) {
     dim3 grid((L.nx + FTX - 1) / FTX, (L.ny + FTY - 1) / FTY, (L.nz + zc - 1) / zc);
     // no particles and tau_A, tau_B not both 1 (at omega = 1 lb_step runs the
     // density pass and the lean kernel, particles or not)
-    if (prec == LB_FP16 && L.sr) return launch_fused_plain<LB_FP16, false, true>(L, zc, grid, st);
-    DISPATCH(prec, (launch_fused_plain<P, false, false>(L, zc, grid, st)));
+    if (prec == LB_FP16 && L.sr) return launch_fused_plain<LB_FP16, true>(L, zc, grid, st);
+    DISPATCH(prec, (launch_fused_plain<P, false>(L, zc, grid, st)));
     return 1;
 }
 

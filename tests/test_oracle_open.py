@@ -187,3 +187,10 @@ def test_extrapolation_leaves_walls_and_equilibrium_faces():
         runs.append([o.populations(k) for k in range(2)])
     for k in range(2):
         assert np.array_equal(runs[0][k], runs[1][k])
+
+
+def test_extrapolation_flag_is_checked():
+    o = Oracle(4, 4, 6)
+    with pytest.raises(RuntimeError):
+        o.set_params(bc=(1, 1, 0), open=(2, 0), open_extrap=2)
+    o.set_params(bc=(1, 1, 0), open=(2, 0), open_extrap=1)

@@ -194,3 +194,33 @@ def test_extrapolation_flag_is_checked():
     with pytest.raises(RuntimeError):
         o.set_params(bc=(1, 1, 0), open=(2, 0), open_extrap=2)
     o.set_params(bc=(1, 1, 0), open=(2, 0), open_extrap=1)
+
+
+def test_extrapolation_falls_back_under_a_particle():
+    """Where the next interior node b + 1 is a particle node the velocity
+    face takes the density of the boundary node itself: the populations the
+    face sends into that column are those of the run without extrapolation,
+    while a column with fluid at b + 1 differs by -3 w_i (rho_b - rho_{b+1})
+    c_i.u_w, half the density step in the wall term of Eq. 9."""
+    shape = nx, ny, nz = (8, 8, 8)
+    N = nx * ny * nz
+    a_, b_ = 0.55, -0.02
+    z = np.repeat(np.arange(nz), nx * ny)
+    uw = np.array([0.03, -0.02, 0.01])
+    c, w, opp = _lattice()
+    got = {}
+    for ex in (0, 1):
+        o = Oracle(*shape, 1)
+        o.set_params(tau=(1.0, 1.0), bc=(1, 1, 0), open=(2, 0), wall_u_lo=tuple(uw), open_extrap=ex)
+        o.init_fields(a_ + b_ * z, np.full(N, 0.45))
+        o.add_colloids([[2.0, 2.0, 2.2]], [1.5], [1e30])
+        own = o.owner()
+        o.step(1)
+        got[ex] = o.populations(0)
+    site = lambda x, y, zz: x + nx * (y + ny * zz)
+    assert own[site(2, 2, 1)] == 0 and own[site(2, 2, 0)] < 0 and own[site(0, 0, 1)] < 0
+    for i in np.nonzero(c[:, 2] == -1)[0]:
+        under, free = site(2, 2, 0), site(0, 0, 0)
+        assert got[1][opp[i], under] == got[0][opp[i], under]
+        d = got[1][opp[i], free] - got[0][opp[i], free]
+        assert abs(d - 3 * w[i] * b_ * (c[i] @ uw)) < 1e-15

@@ -1,9 +1,9 @@
 // lbgb_fluid.cu -- lattice kernels: initialisation, densities, the fused
 // collide + Shan-Chen + bounce-back + push-stream step, and read-outs.
 //
-// Populations are stored structure-of-arrays, f[k][i][s] (component k, link
-// i, site s = x + nx (y + ny z)), with the population planes padded to a
-// multiple of 64 sites.  The state between time steps is the post-streaming
+// Populations are stored per link plane as component pairs: link i of site
+// s = x + nx (y + ny z) is the pair SKEW + s - c_ix of plane i (pair_index),
+// both components side by side.  The state between time steps is the post-streaming
 // population f(t) (the paper's step starts from it, Sec. 3.1); one step
 // reads f(t) at each site, collides locally and pushes f*(t) to the
 // neighbours, writing f(t+1) into the second buffer.

@@ -224,3 +224,47 @@ def test_extrapolation_falls_back_under_a_particle():
         assert got[1][opp[i], under] == got[0][opp[i], under]
         d = got[1][opp[i], free] - got[0][opp[i], free]
         assert abs(d - 3 * w[i] * b_ * (c[i] @ uw)) < 1e-15
+
+
+def test_pressure_face_extrapolates_the_weighted_mixture_velocity():
+    """Unequal tau, G = 0: component k starts at f^eq(rho^k, u^k(z)) with
+    linear u^k(z).  The boundary velocity of Eq. 10 is the mixture velocity
+    of Eq. 14, u = sum_k omega_k rho^k u^k / sum_k omega_k rho^k, so the
+    face sends in -f*_i + 2 w_i rho_w (1 + 9/2 (c_i.u_w)^2 - 3/2 u_w^2)
+    with f*_i = (1 - omega) f^eq(rho^k, u^k(0)) + omega f^eq(rho^k, u(0)),
+    omega the mixture frequency of Eq. 13 (1/omega = 3 nubar + 1/2,
+    1/nubar = sum_k (rho^k / rho) / nu_k), and u_w = u(0) + (u(0) - u(1))/2;
+    an unweighted mixture velocity fails this."""
+    shape = nx, ny, nz = (4, 3, 8)
+    N = nx * ny * nz
+    z = np.repeat(np.arange(nz), nx * ny)
+    tau = (0.7, 1.4)
+    om = [1 / t for t in tau]
+    rho = (0.6, 0.3)
+    ua0, ga = np.array([0.02, 0.0, 0.01]), np.array([0.003, 0.001, -0.002])
+    ub0, gb = np.array([-0.01, 0.015, 0.0]), np.array([-0.002, 0.002, 0.001])
+    c, w, opp = _lattice()
+    mix = lambda ua, ub: (om[0] * rho[0] * ua + om[1] * rho[1] * ub) / (om[0] * rho[0] + om[1] * rho[1])
+    u0, u1 = mix(ua0, ub0), mix(ua0 + ga, ub0 + gb)
+    nu = [(t - 0.5) / 3 for t in tau]
+    nubar = 1 / sum(r / sum(rho) / n for r, n in zip(rho, nu))
+    omega = 1 / (3 * nubar + 0.5)
+    uw = u0 + 0.5 * (u0 - u1)
+    rw = (0.62, 0.28)
+    o = Oracle(*shape)
+    o.set_params(tau=tau, bc=(1, 1, 0), open=(1, 0), open_rho=(rw[0], rw[1], 1.0, 1.0), open_extrap=1)
+    o.init_fields(np.full(N, rho[0]), np.full(N, rho[1]))
+    for k, (u_0, g_) in enumerate(((ua0, ga), (ub0, gb))):
+        f = np.empty((19, N))
+        for s in range(N):
+            u = u_0 + g_ * z[s]
+            f[:, s] = [_feq(i, c, w, rho[k], u) for i in range(19)]
+        o.set_populations(k, f)
+    o.step(1)
+    for k, u_k in enumerate((ua0, ub0)):
+        f = o.populations(k)
+        for i in np.nonzero(c[:, 2] == -1)[0]:
+            fs = (1 - omega) * _feq(i, c, w, rho[k], u_k) + omega * _feq(i, c, w, rho[k], u0)
+            cu = c[i] @ uw
+            want = -fs + 2 * w[i] * rw[k] * (1 + 4.5 * cu * cu - 1.5 * (uw @ uw))
+            assert np.abs(f[opp[i], z == 0] - want).max() < 1e-15
